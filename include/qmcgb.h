@@ -1,0 +1,175 @@
+/*
+ * qmcgb.h - C ABI of the GB300 particle-by-particle QMC library (libqmcgb.so).
+ *
+ * What the library computes (citations are to the QMCPACK paper, arXiv 1802.06922):
+ *   Many independent walkers (Markov chains, Sec. "Variational Monte Carlo") move their
+ *   electrons one at a time (Sec. "Trial Moves", particle-by-particle transition density)
+ *   through a trial wavefunction Psi = D_up D_dn e^J (Eq. msdj with one determinant):
+ *     - orbitals phi_j are periodic tricubic B-splines; one evaluation of value, gradient
+ *       and Laplacian gathers the 64 coefficient rows around the point
+ *       (Sec. "B-spline basis sets");
+ *     - the determinant ratio of a move of electron e is phi(r') . column e of A^-1, and an
+ *       accepted move updates A^-1 by Sherman-Morrison or by the delayed rank-k scheme
+ *       (Sec. "Multi-Determinant Slater-Jastrow Form");
+ *     - J holds one- and two-body terms built from 1D cubic B-spline radial functors
+ *       with minimum-image distances (Sec. "Jastrow factor");
+ *     - a move is accepted with min(1, |Psi'/Psi|^2 T'/T) (Eq. accept_reject); DMC steps
+ *       use drift-diffusion proposals (Eq. pmc:driftdiffusion_step), the fixed-node
+ *       rule, weights (Eq. pmc:walker_weight) and branching (Sec. "Diffusion Monte Carlo");
+ *     - the local energy E_L = Psi^-1 H Psi (Sec. "Hamiltonian") is kinetic plus a
+ *       short-range Yukawa potential standing in for the Coulomb terms.
+ *
+ * Conventions for every call:
+ *   - Units are Hartree atomic units; the cell is the cube [0, L)^3, periodic.
+ *   - Electrons 0..n_up-1 are spin up, n_up..n_up+n_dn-1 spin down.
+ *   - Every function returns a qmc_status; nothing throws across the ABI. On failure the
+ *     message of the calling thread is available from qmc_last_error().
+ *   - Host arrays passed in are copied before the call returns; the caller keeps them.
+ *   - Device buffers created by the library are owned by it and released by the
+ *     matching destroy call. Device pointers passed in by the caller (trace buffers,
+ *     outputs) are borrowed: the library never frees them, and they must stay valid
+ *     until the work queued on the given stream has finished.
+ *   - Calls that take a `stream` (a cudaStream_t, NULL = the legacy default stream)
+ *     only enqueue work and return; device-side failures (a singular matrix, a bounded
+ *     wait that timed out) are recorded in a device flag and reported by the next
+ *     synchronising call (qmc_measure, qmc_accumulate_energy, qmc_get_state,
+ *     qmc_check_errors).
+ *   - Output pointers of qmc_measure and qmc_accumulate_energy may be host or device
+ *     memory; the library looks at the pointer and copies accordingly.
+ *   - destroy functions accept NULL.
+ */
+#ifndef QMCGB_H
+#define QMCGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qmc_system_s* qmc_system_t;
+typedef struct qmc_walkers_s* qmc_walkers_t;
+
+typedef enum {
+  QMC_OK = 0,
+  QMC_EINVAL = -1,     /* a bad argument: NULL handle, size out of range, wrong order of calls */
+  QMC_ENOMEM = -2,     /* a device or host allocation failed */
+  QMC_ECUDA = -3,      /* a CUDA runtime call failed */
+  QMC_ESINGULAR = -4,  /* a Slater matrix had an exactly zero pivot at (re-)inversion */
+  QMC_ETIMEOUT = -5,   /* a bounded device-side wait ran out */
+  QMC_ESTATE = -6      /* a serialized state does not match the walker set */
+} qmc_status;
+
+typedef enum {
+  QMC_FP64 = 0,          /* table, orbital values, inverse and ratios in double */
+  QMC_FP32 = 1,          /* FP32 table and inverse; FP64 re-inversion and reductions */
+  QMC_FP32_BF16TAB = 2   /* BF16 coefficient table, FP32 accumulation, else as QMC_FP32 */
+} qmc_precision;
+
+typedef enum {
+  QMC_MOVE_METROPOLIS = 0,  /* r' = r + step * xi (Gaussian xi) */
+  QMC_MOVE_DRIFT = 1        /* r' = r + step * grad ln|Psi| + sqrt(step) * xi */
+} qmc_move;
+
+/* Description of one system (Sec. "Hamiltonian", Sec. "Trial Moves"). */
+typedef struct {
+  int n_up, n_dn;          /* electrons per spin; each determinant is N_s x N_s */
+  double L;                /* side of the periodic cubic cell (bohr) */
+  int n_ion;               /* number of ions (may be 0) */
+  const double* ion_pos;   /* host [n_ion][3], copied */
+  double ion_Z;            /* ion charge in the potential */
+  double kappa;            /* Yukawa screening (1/bohr); v(r) = exp(-kappa r)/r, r < L/2 */
+  int with_potential;      /* 0: E_L is the kinetic energy only */
+  qmc_precision prec;
+  qmc_move move;
+  double step;             /* sigma (Metropolis) or tau (drift), bohr or 1/Ha */
+  int delay_k;             /* 1 = Sherman-Morrison rank-1; 2..64 = delayed rank-k */
+  int reinv_period;        /* re-invert each Slater matrix in FP64 every this many moves (0 = never) */
+  int reinv_on_accepted;   /* 1: count accepted moves of the determinant; 0: proposed moves */
+  uint64_t seed;           /* Philox4x32-10 key of every draw */
+} qmc_system_desc;
+
+/* Creates a system. Fails with QMC_EINVAL for n_up or n_dn outside [0, 1024], n_up+n_dn
+ * = 0, L <= 0, step < 0, delay_k outside [1, 64] or an unknown precision/move. */
+qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out);
+
+/* Sets the B-spline orbital table (Sec. "B-spline basis sets"). coef is host memory
+ * [nx][ny][nz][n_orb] in double, row (ix,iy,iz) holding the n_orb orbital coefficients of
+ * node (ix,iy,iz) at position (ix*L/nx, iy*L/ny, iz*L/nz). It is copied to the device and
+ * cast to the system's table precision. Requires n_orb >= max(n_up, n_dn) and each of
+ * nx, ny, nz >= 4. Both spins use orbitals 0..N_s-1. */
+qmc_status qmc_system_set_spline(qmc_system_t sys, int nx, int ny, int nz, int n_orb,
+                                 const double* coef);
+
+/* Sets one radial Jastrow functor u(r) = sum_{m=0}^{M} p_m B3(r M / rcut - m), u = 0 for
+ * r >= rcut (Sec. "Jastrow factor"). which: 0 = electron-ion, 1 = same-spin pair,
+ * 2 = opposite-spin pair. p: host [M+1]. If cusp_set, p[0] is replaced by
+ * p[2] - (2 rcut / M) cusp so that u'(0) = cusp. 1 <= M <= 32, 0 < rcut <= L/2.
+ * A functor that is never set is zero. */
+qmc_status qmc_system_set_jastrow(qmc_system_t sys, int which, int M, double rcut,
+                                  const double* p, int cusp_set, double cusp);
+
+/* Creates n_walkers walkers with IDs 0..n_walkers-1 at positions pos (host
+ * [n_walkers][n_up+n_dn][3], wrapped into the cell). Evaluates the orbitals at every
+ * electron, inverts each Slater matrix in FP64 and records ln|det| and its sign.
+ * Synchronous. QMC_ESINGULAR if a Slater matrix is singular. */
+qmc_status qmc_walkers_create(qmc_system_t sys, int n_walkers, const double* pos,
+                              qmc_walkers_t* out);
+
+/* Advances every walker by n_sweeps sweeps; a sweep proposes one move for each electron
+ * in index order. Uses (and then advances) the walker set's sweep counter, which is part
+ * of every Philox counter, so the result depends only on the seed, the walker IDs, the
+ * positions and the counter. Asynchronous on `stream`. */
+qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream);
+
+/* Local energy and ln|Psi| of every walker's current configuration
+ * (E_L = Psi^-1 H Psi, Sec. "Hamiltonian"). e_local and log_psi: [n_walkers] doubles,
+ * host or device (either may be NULL). Synchronises `stream` when an output is host
+ * memory; reports deferred device errors. */
+qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_psi, void* stream);
+
+/* FP64 sums over walkers of the last measurement (Sec. "Variational Monte Carlo" and
+ * Eq. pmc:weighted_average): out[0] = sum W, out[1] = sum W E_L, out[2] = sum W E_L^2,
+ * out[3] = accepted / proposed moves since the previous call. W = 1 in VMC. out: host or
+ * device [4]. Measures first if the walkers moved since the last measurement. */
+qmc_status qmc_accumulate_energy(qmc_walkers_t w, double* out, void* stream);
+
+/* Enables a per-move trace of the next sweeps: dev_buf (device, borrowed) receives, for
+ * each traced sweep, [n_walkers][n_up+n_dn][8] doubles = (ratio R_det, dJ,
+ * grad_e ln|Psi(R')| x,y,z, u, A, accepted). bytes bounds how many sweeps are traced;
+ * NULL / 0 disables. */
+qmc_status qmc_trace_enable(qmc_walkers_t w, void* dev_buf, size_t bytes);
+
+/* Lockstep replay: the next qmc_sweep call of n sweeps takes its accept decisions from
+ * accept_bits (host or device, [n][n_walkers][n_up+n_dn] bytes, 0 or 1) instead of
+ * u < A. Used to compare reduced-precision runs move by move with a reference run.
+ * The array is copied; NULL clears a pending replay. */
+qmc_status qmc_replay_decisions(qmc_walkers_t w, const uint8_t* accept_bits, int n_sweeps);
+
+/* Positions [n_walkers][n_e][3] of every walker, copied to host or device memory. */
+qmc_status qmc_get_positions(qmc_walkers_t w, double* pos, void* stream);
+
+/* Serialised walker state (positions, walker IDs, weights, sweep counter, seed) for
+ * checkpoint/resume. qmc_get_state with buf = NULL stores the needed size in *len.
+ * qmc_set_state rebuilds the inverses by FP64 re-inversion; QMC_ESTATE if the buffer does
+ * not match this walker set's sizes. Synchronous. */
+qmc_status qmc_get_state(qmc_walkers_t w, void* buf, size_t* len);
+qmc_status qmc_set_state(qmc_walkers_t w, const void* buf, size_t len);
+
+/* Waits for the walkers' queued work on `stream` and reports deferred device errors. */
+qmc_status qmc_check_errors(qmc_walkers_t w, void* stream);
+
+/* Number of kernel launches the library enqueued since the walker set was created. */
+int64_t qmc_launch_count(qmc_walkers_t w);
+
+void qmc_walkers_destroy(qmc_walkers_t w);
+void qmc_system_destroy(qmc_system_t sys);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* qmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCGB_H */

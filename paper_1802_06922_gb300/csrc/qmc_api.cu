@@ -1,0 +1,571 @@
+// C-ABI runtime of libqmcgb: object lifetimes, argument checks, host<->device copies and
+// the order of kernel launches of a sweep.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qmcgb.h"
+#include "qmc_internal.h"
+#include "qmc_launch.h"
+
+using namespace qmcgb;
+
+namespace {
+thread_local std::string g_err;
+
+qmc_status fail(qmc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define QMC_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? QMC_ENOMEM : QMC_ECUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+double host_min_image(double d, double L) { return d - L * std::nearbyint(d / L); }
+
+double host_wrap(double x, double L) {
+  double m = std::fmod(x, L);
+  if (m != 0.0 && m < 0.0) m += L;
+  return m;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// IEEE round-to-nearest-even of a float to bfloat16 (stored as the upper 16 bits).
+uint16_t f32_to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);   // NaN
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+}  // namespace
+
+struct qmc_system_s {
+  qmc_system_desc d{};
+  SysParams P{};
+  void* d_table = nullptr;
+  double* d_ions = nullptr;
+  float* d_ionsf = nullptr;
+  bool has_spline = false;
+  const TwLaunch* tw = nullptr;
+  const TtLaunch* tt = nullptr;
+};
+
+struct qmc_walkers_s {
+  qmc_system_s* sys = nullptr;
+  WalkParams W{};
+  uint32_t sweep = 0;
+  int chunk = 0;               // moves per launch of a spin block
+  void* d_P = nullptr;         // proposal orbital values [W][chunk][5][ld_v]
+  Prop* d_prop = nullptr;      // [W][chunk]
+  double* d_out = nullptr;     // [8] accumulate output
+  long long* d_nacc = nullptr;
+  long long proposed = 0;      // since the last accumulate
+  double* trace = nullptr;     // borrowed
+  size_t trace_sweeps = 0;     // capacity in sweeps
+  size_t traced = 0;
+  uint8_t* d_forced = nullptr;
+  int forced_sweeps = 0;
+  int64_t launches = 0;
+  bool energy_valid = false;
+};
+
+// ------------------------------------------------------------------------ errors
+extern "C" const char* qmc_last_error(void) { return g_err.c_str(); }
+
+// ------------------------------------------------------------------------ system
+extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out) {
+  if (!desc || !out) return fail(QMC_EINVAL, "qmc_system_create: NULL argument");
+  *out = nullptr;
+  const qmc_system_desc& d = *desc;
+  if (d.n_up < 0 || d.n_dn < 0 || d.n_up > 1024 || d.n_dn > 1024 || d.n_up + d.n_dn == 0)
+    return fail(QMC_EINVAL, "electron counts must be in [0, 1024] with at least one electron");
+  if (!(d.L > 0.0) || !std::isfinite(d.L)) return fail(QMC_EINVAL, "L must be positive");
+  if (d.n_ion < 0 || (d.n_ion > 0 && !d.ion_pos)) return fail(QMC_EINVAL, "bad ion list");
+  if (!(d.step >= 0.0)) return fail(QMC_EINVAL, "step must be >= 0");
+  if (d.delay_k < 1 || d.delay_k > kMaxDelay) return fail(QMC_EINVAL, "delay_k must be in [1, %d]", kMaxDelay);
+  if (d.prec < QMC_FP64 || d.prec > QMC_FP32_BF16TAB) return fail(QMC_EINVAL, "unknown precision");
+  if (d.move != QMC_MOVE_METROPOLIS && d.move != QMC_MOVE_DRIFT) return fail(QMC_EINVAL, "unknown move");
+  if (d.reinv_period < 0) return fail(QMC_EINVAL, "reinv_period must be >= 0");
+  qmc_system_s* s = new qmc_system_s;
+  s->d = d;
+  s->d.ion_pos = nullptr;
+  SysParams& P = s->P;
+  P.n_up = d.n_up;
+  P.n_dn = d.n_dn;
+  P.n_e = d.n_up + d.n_dn;
+  P.n_ion = d.n_ion;
+  P.L = d.L;
+  P.Lf = (float)d.L;
+  P.ion_Z = d.ion_Z;
+  P.ion_Zf = (float)d.ion_Z;
+  P.kappa = d.kappa;
+  P.kappaf = (float)d.kappa;
+  P.with_potential = d.with_potential;
+  P.move = d.move;
+  P.step = d.step;
+  P.seed_lo = (uint32_t)(d.seed & 0xffffffffu);
+  P.seed_hi = (uint32_t)(d.seed >> 32);
+  // ions: wrapped, device copies in [3][n_ion] layout; ion-ion constant on the host
+  std::vector<double> ion((size_t)3 * std::max(d.n_ion, 1));
+  std::vector<float> ionf(ion.size());
+  for (int I = 0; I < d.n_ion; ++I)
+    for (int c = 0; c < 3; ++c) {
+      ion[(size_t)c * d.n_ion + I] = host_wrap(d.ion_pos[3 * I + c], d.L);
+      ionf[(size_t)c * d.n_ion + I] = (float)ion[(size_t)c * d.n_ion + I];
+    }
+  double vii = 0.0;
+  for (int I = 0; I < d.n_ion; ++I)
+    for (int J = I + 1; J < d.n_ion; ++J) {
+      double r2 = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        const double dd = host_min_image(ion[(size_t)c * d.n_ion + I] - ion[(size_t)c * d.n_ion + J], d.L);
+        r2 += dd * dd;
+      }
+      const double r = std::sqrt(r2);
+      if (r < 0.5 * d.L) vii += d.ion_Z * d.ion_Z * std::exp(-d.kappa * r) / r;
+    }
+  P.v_ion_ion = vii;
+  cudaError_t e = cudaMalloc(&s->d_ions, ion.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_ionsf, ionf.size() * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_ions, ion.data(), ion.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_ionsf, ionf.data(), ionf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    qmc_system_destroy(s);
+    return fail(QMC_ECUDA, "qmc_system_create: %s", cudaGetErrorString(e));
+  }
+  P.ions = s->d_ions;
+  P.ionsf = s->d_ionsf;
+  s->tw = d.prec == QMC_FP64 ? &tw_launch_f64() : &tw_launch_f32();
+  s->tt = d.prec == QMC_FP64 ? &tt_launch_f64()
+                             : (d.prec == QMC_FP32 ? &tt_launch_f32() : &tt_launch_bf16());
+  *out = s;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_system_set_spline(qmc_system_t s, int nx, int ny, int nz, int n_orb,
+                                            const double* coef) {
+  if (!s || !coef) return fail(QMC_EINVAL, "qmc_system_set_spline: NULL argument");
+  if (nx < 4 || ny < 4 || nz < 4 || nx > 4096 || ny > 4096 || nz > 4096)
+    return fail(QMC_EINVAL, "grid sizes must be in [4, 4096]");
+  if (n_orb < std::max(s->P.n_up, s->P.n_dn) || n_orb > 4096)
+    return fail(QMC_EINVAL, "n_orb must be >= max(n_up, n_dn) and <= 4096");
+  const int ld = round_up(n_orb, 8);
+  const size_t rows = (size_t)nx * ny * nz;
+  const size_t esz = s->d.prec == QMC_FP64 ? 8 : (s->d.prec == QMC_FP32 ? 4 : 2);
+  void* dt = nullptr;
+  QMC_CUDA(cudaMalloc(&dt, rows * ld * esz));
+  // convert and upload in slabs of rows
+  const size_t slab = std::max<size_t>(1, (64u << 20) / (ld * esz));
+  std::vector<unsigned char> host(std::min(rows, slab) * ld * esz);
+  for (size_t r0 = 0; r0 < rows; r0 += slab) {
+    const size_t nr = std::min(slab, rows - r0);
+    std::memset(host.data(), 0, nr * ld * esz);
+    for (size_t r = 0; r < nr; ++r) {
+      const double* src = coef + (r0 + r) * n_orb;
+      if (esz == 8) {
+        std::memcpy(host.data() + r * ld * 8, src, sizeof(double) * n_orb);
+      } else if (esz == 4) {
+        float* dst = reinterpret_cast<float*>(host.data()) + r * ld;
+        for (int o = 0; o < n_orb; ++o) dst[o] = (float)src[o];
+      } else {
+        uint16_t* dst = reinterpret_cast<uint16_t*>(host.data()) + r * ld;
+        for (int o = 0; o < n_orb; ++o) dst[o] = f32_to_bf16((float)src[o]);
+      }
+    }
+    cudaError_t e = cudaMemcpy(static_cast<unsigned char*>(dt) + r0 * ld * esz, host.data(),
+                               nr * ld * esz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(dt);
+      return fail(QMC_ECUDA, "qmc_system_set_spline: %s", cudaGetErrorString(e));
+    }
+  }
+  if (s->d_table) cudaFree(s->d_table);
+  s->d_table = dt;
+  SysParams& P = s->P;
+  P.table = dt;
+  P.nx = nx; P.ny = ny; P.nz = nz; P.ld = ld; P.n_orb = n_orb;
+  const int nn[3] = {nx, ny, nz};
+  for (int c = 0; c < 3; ++c) {
+    P.inv_delta[c] = (double)nn[c] / s->d.L;
+    P.inv_deltaf[c] = (float)P.inv_delta[c];
+  }
+  s->has_spline = true;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_system_set_jastrow(qmc_system_t s, int which, int M, double rcut,
+                                             const double* p, int cusp_set, double cusp) {
+  if (!s || !p) return fail(QMC_EINVAL, "qmc_system_set_jastrow: NULL argument");
+  if (which < 0 || which > 2) return fail(QMC_EINVAL, "which must be 0, 1 or 2");
+  if (M < 1 || M > kMaxKnots) return fail(QMC_EINVAL, "M must be in [1, %d]", kMaxKnots);
+  if (!(rcut > 0.0) || rcut > 0.5 * s->d.L * (1 + 1e-12))
+    return fail(QMC_EINVAL, "rcut must be in (0, L/2]");
+  if (cusp_set && M < 2) return fail(QMC_EINVAL, "a cusp needs M >= 2");
+  SysParams& P = s->P;
+  P.jM[which] = M;
+  P.jrc[which] = rcut;
+  P.jrcf[which] = (float)rcut;
+  for (int m = 0; m <= kMaxKnots; ++m) P.jp[which][m] = m <= M ? p[m] : 0.0;
+  if (cusp_set) P.jp[which][0] = P.jp[which][2] - (2.0 * rcut / M) * cusp;
+  for (int m = 0; m <= kMaxKnots; ++m) P.jpf[which][m] = (float)P.jp[which][m];
+  return QMC_OK;
+}
+
+extern "C" void qmc_system_destroy(qmc_system_t s) {
+  if (!s) return;
+  cudaFree(s->d_table);
+  cudaFree(s->d_ions);
+  cudaFree(s->d_ionsf);
+  delete s;
+}
+
+// ------------------------------------------------------------------------ walkers
+namespace {
+
+qmc_status check_err(qmc_walkers_s* w, cudaStream_t st) {
+  QMC_CUDA(cudaStreamSynchronize(st));
+  int err = 0;
+  QMC_CUDA(cudaMemcpy(&err, w->W.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    QMC_CUDA(cudaMemset(w->W.err, 0, sizeof(int)));
+    if (err & kErrSingular) return fail(QMC_ESINGULAR, "a Slater matrix was singular at (re-)inversion");
+    if (err & kErrTimeout) return fail(QMC_ETIMEOUT, "a bounded device wait timed out");
+    return fail(QMC_ECUDA, "device error flag 0x%x", err);
+  }
+  return QMC_OK;
+}
+
+qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
+  qmc_system_s* s = w->sys;
+  QMC_CUDA(s->tt->vgl_current(s->P, w->W, st));
+  QMC_CUDA(s->tw->reinvert(s->P, w->W, st));
+  QMC_CUDA(s->tw->local_energy(s->P, w->W, st));
+  w->launches += 3;
+  QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
+  w->energy_valid = true;
+  return check_err(w, st);
+}
+
+void free_walkers(qmc_walkers_s* w) {
+  WalkParams& W = w->W;
+  void* ptrs[] = {W.pos, W.binv, W.vgl, W.logdet, W.sgn, W.wid, W.weight, W.e_loc, W.log_psi,
+                  W.n_acc, W.acc_since, W.scratch64, W.err, w->d_P, w->d_prop, w->d_out,
+                  w->d_nacc, w->d_forced};
+  for (void* p : ptrs) cudaFree(p);
+}
+
+qmc_status upload_positions(qmc_walkers_s* w, const double* pos, bool pos_on_device) {
+  const SysParams& P = w->sys->P;
+  const int nw = w->W.n_w, ne = P.n_e;
+  std::vector<double> h((size_t)nw * ne * 3);
+  std::vector<double> src;
+  if (pos_on_device) {
+    src.resize(h.size());
+    QMC_CUDA(cudaMemcpy(src.data(), pos, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    pos = src.data();
+  }
+  for (int a = 0; a < nw; ++a)
+    for (int e = 0; e < ne; ++e)
+      for (int c = 0; c < 3; ++c) {
+        const double v = pos[((size_t)a * ne + e) * 3 + c];
+        if (!std::isfinite(v)) return fail(QMC_EINVAL, "non-finite electron position");
+        h[((size_t)a * 3 + c) * ne + e] = host_wrap(v, P.L);
+      }
+  QMC_CUDA(cudaMemcpy(w->W.pos, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return QMC_OK;
+}
+}  // namespace
+
+extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const double* pos,
+                                         qmc_walkers_t* out) {
+  if (!s || !out || !pos) return fail(QMC_EINVAL, "qmc_walkers_create: NULL argument");
+  *out = nullptr;
+  if (!s->has_spline) return fail(QMC_EINVAL, "qmc_walkers_create: set the spline table first");
+  if (n_walkers < 1 || n_walkers > (1 << 20)) return fail(QMC_EINVAL, "n_walkers must be in [1, 2^20]");
+  const SysParams& P = s->P;
+  qmc_walkers_s* w = new qmc_walkers_s;
+  w->sys = s;
+  WalkParams& W = w->W;
+  W.n_w = n_walkers;
+  const int ns_max = std::max(P.n_up, P.n_dn);
+  W.ld_v = round_up(std::max(ns_max, 1), 8);
+  const size_t tw = s->tw->tw_size;
+  const size_t nw = n_walkers, ne = P.n_e;
+  w->chunk = ns_max;
+  // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
+  while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
+  const size_t nbinv = (size_t)P.n_up * P.n_up + (size_t)P.n_dn * P.n_dn;
+  struct A { void** p; size_t bytes; } allocs[] = {
+      {(void**)&W.pos, nw * 3 * ne * sizeof(double)},
+      {(void**)&W.binv, nw * nbinv * tw},
+      {(void**)&W.vgl, nw * ne * 5 * W.ld_v * tw},
+      {(void**)&W.logdet, nw * 2 * sizeof(double)},
+      {(void**)&W.sgn, nw * 2 * sizeof(double)},
+      {(void**)&W.wid, nw * sizeof(uint32_t)},
+      {(void**)&W.weight, nw * sizeof(double)},
+      {(void**)&W.e_loc, nw * sizeof(double)},
+      {(void**)&W.log_psi, nw * sizeof(double)},
+      {(void**)&W.n_acc, nw * sizeof(long long)},
+      {(void**)&W.acc_since, nw * 2 * sizeof(int)},
+      {(void**)&W.scratch64, nw * (size_t)W.ld_v * W.ld_v * sizeof(double)},
+      {(void**)&W.err, sizeof(int)},
+      {(void**)&w->d_P, nw * (size_t)w->chunk * 5 * W.ld_v * tw},
+      {(void**)&w->d_prop, nw * (size_t)w->chunk * sizeof(Prop)},
+      {(void**)&w->d_out, 8 * sizeof(double)},
+      {(void**)&w->d_nacc, sizeof(long long)},
+  };
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      free_walkers(w);
+      delete w;
+      return fail(QMC_ENOMEM, "qmc_walkers_create: cannot allocate %zu bytes: %s", a.bytes,
+                  cudaGetErrorString(e));
+    }
+  }
+  // zero the orbital rows so padded columns never hold garbage
+  cudaMemset(W.vgl, 0, nw * ne * 5 * W.ld_v * tw);
+  cudaMemset(W.err, 0, sizeof(int));
+  cudaMemset(W.n_acc, 0, nw * sizeof(long long));
+  std::vector<uint32_t> ids(nw);
+  std::vector<double> ones(nw, 1.0);
+  for (size_t i = 0; i < nw; ++i) ids[i] = (uint32_t)i;
+  cudaMemcpy(W.wid, ids.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(W.weight, ones.data(), nw * sizeof(double), cudaMemcpyHostToDevice);
+  qmc_status st = upload_positions(w, pos, is_device_ptr(pos));
+  if (st == QMC_OK) st = setup_state(w, 0);
+  if (st != QMC_OK) {
+    const std::string msg = g_err;
+    free_walkers(w);
+    delete w;
+    g_err = msg;
+    return st;
+  }
+  *out = w;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
+  if (!w) return fail(QMC_EINVAL, "qmc_sweep: NULL walkers");
+  if (n_sweeps < 0) return fail(QMC_EINVAL, "qmc_sweep: n_sweeps < 0");
+  qmc_system_s* s = w->sys;
+  if (s->d.move != QMC_MOVE_METROPOLIS)
+    return fail(QMC_EINVAL, "qmc_sweep: drift moves are taken by the DMC step");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SysParams& P = s->P;
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    WalkParams W = w->W;
+    W.trace = nullptr;
+    W.forced = nullptr;
+    if (w->trace && w->traced < w->trace_sweeps)
+      W.trace = w->trace + w->traced * (size_t)W.n_w * P.n_e * 8;
+    if (w->d_forced && sw < w->forced_sweeps)
+      W.forced = w->d_forced + (size_t)sw * W.n_w * P.n_e;
+    for (int spin = 0; spin < 2; ++spin) {
+      const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
+      for (int e0 = b0; e0 < b1; e0 += w->chunk) {
+        const int e1 = std::min(b1, e0 + w->chunk);
+        QMC_CUDA(launch_proposals(P, W, w->sweep, e0, e1, w->d_prop, st));
+        QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, w->d_prop, w->d_P, st));
+        QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, s->d.delay_k, w->d_P, w->d_prop,
+                              s->d.reinv_period, s->d.reinv_on_accepted, false, st));
+        w->launches += 3;
+      }
+    }
+    QMC_CUDA(s->tw->local_energy(P, W, st));
+    w->launches += 1;
+    if (W.trace) ++w->traced;
+    ++w->sweep;
+    w->proposed += (long long)W.n_w * P.n_e;
+  }
+  if (w->d_forced) {
+    QMC_CUDA(cudaStreamSynchronize(st));
+    cudaFree(w->d_forced);
+    w->d_forced = nullptr;
+    w->forced_sweeps = 0;
+  }
+  w->energy_valid = true;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_psi, void* stream) {
+  if (!w) return fail(QMC_EINVAL, "qmc_measure: NULL walkers");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!w->energy_valid) {
+    QMC_CUDA(w->sys->tw->local_energy(w->sys->P, w->W, st));
+    w->launches += 1;
+    w->energy_valid = true;
+  }
+  const size_t b = sizeof(double) * w->W.n_w;
+  if (e_local) QMC_CUDA(cudaMemcpyAsync(e_local, w->W.e_loc, b, cudaMemcpyDefault, st));
+  if (log_psi) QMC_CUDA(cudaMemcpyAsync(log_psi, w->W.log_psi, b, cudaMemcpyDefault, st));
+  const bool host = (e_local && !is_device_ptr(e_local)) || (log_psi && !is_device_ptr(log_psi));
+  if (host) return check_err(w, st);
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_accumulate_energy(qmc_walkers_t w, double* out, void* stream) {
+  if (!w || !out) return fail(QMC_EINVAL, "qmc_accumulate_energy: NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  QMC_CUDA(launch_accumulate(w->W, w->d_out, w->d_nacc, st));
+  w->launches += 1;
+  double h[4];
+  long long nacc = 0;
+  QMC_CUDA(cudaMemcpyAsync(h, w->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  QMC_CUDA(cudaMemcpyAsync(&nacc, w->d_nacc, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  qmc_status r = check_err(w, st);
+  if (r != QMC_OK) return r;
+  h[3] = w->proposed > 0 ? (double)nacc / (double)w->proposed : 0.0;
+  w->proposed = 0;
+  QMC_CUDA(cudaMemcpy(out, h, sizeof h, cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_trace_enable(qmc_walkers_t w, void* dev_buf, size_t bytes) {
+  if (!w) return fail(QMC_EINVAL, "qmc_trace_enable: NULL walkers");
+  if (!dev_buf || bytes == 0) {
+    w->trace = nullptr;
+    w->trace_sweeps = 0;
+    w->traced = 0;
+    return QMC_OK;
+  }
+  if (!is_device_ptr(dev_buf)) return fail(QMC_EINVAL, "qmc_trace_enable: the buffer must be device memory");
+  const size_t per = (size_t)w->W.n_w * w->sys->P.n_e * 8 * sizeof(double);
+  if (bytes < per) return fail(QMC_EINVAL, "qmc_trace_enable: buffer smaller than one sweep (%zu bytes)", per);
+  w->trace = static_cast<double*>(dev_buf);
+  w->trace_sweeps = bytes / per;
+  w->traced = 0;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_replay_decisions(qmc_walkers_t w, const uint8_t* bits, int n_sweeps) {
+  if (!w) return fail(QMC_EINVAL, "qmc_replay_decisions: NULL walkers");
+  if (w->d_forced) {
+    cudaFree(w->d_forced);
+    w->d_forced = nullptr;
+    w->forced_sweeps = 0;
+  }
+  if (!bits || n_sweeps <= 0) return QMC_OK;
+  const size_t n = (size_t)n_sweeps * w->W.n_w * w->sys->P.n_e;
+  QMC_CUDA(cudaMalloc(&w->d_forced, n));
+  QMC_CUDA(cudaMemcpy(w->d_forced, bits, n, cudaMemcpyDefault));
+  w->forced_sweeps = n_sweeps;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_get_positions(qmc_walkers_t w, double* pos, void* stream) {
+  if (!w || !pos) return fail(QMC_EINVAL, "qmc_get_positions: NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  qmc_status r = check_err(w, st);
+  if (r != QMC_OK) return r;
+  const int nw = w->W.n_w, ne = w->sys->P.n_e;
+  std::vector<double> h((size_t)nw * ne * 3), o(h.size());
+  QMC_CUDA(cudaMemcpy(h.data(), w->W.pos, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (int a = 0; a < nw; ++a)
+    for (int c = 0; c < 3; ++c)
+      for (int e = 0; e < ne; ++e) o[((size_t)a * ne + e) * 3 + c] = h[((size_t)a * 3 + c) * ne + e];
+  QMC_CUDA(cudaMemcpy(pos, o.data(), o.size() * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+namespace {
+struct StateHeader {
+  uint64_t magic, seed;
+  int32_t n_w, n_e, n_up, pad;
+  uint32_t sweep, pad2;
+};
+constexpr uint64_t kMagic = 0x31305f4354415453ull;   // "STATE_01"
+}  // namespace
+
+extern "C" qmc_status qmc_get_state(qmc_walkers_t w, void* buf, size_t* len) {
+  if (!w || !len) return fail(QMC_EINVAL, "qmc_get_state: NULL argument");
+  const int nw = w->W.n_w, ne = w->sys->P.n_e;
+  const size_t need = sizeof(StateHeader) + (size_t)nw * ne * 3 * sizeof(double) +
+                      (size_t)nw * (sizeof(uint32_t) + sizeof(double));
+  if (!buf) {
+    *len = need;
+    return QMC_OK;
+  }
+  if (*len < need) return fail(QMC_EINVAL, "qmc_get_state: buffer too small (%zu < %zu)", *len, need);
+  qmc_status r = check_err(w, 0);
+  if (r != QMC_OK) return r;
+  StateHeader h{kMagic, w->sys->d.seed, nw, ne, w->sys->P.n_up, 0, w->sweep, 0};
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  r = qmc_get_positions(w, reinterpret_cast<double*>(p), nullptr);
+  if (r != QMC_OK) return r;
+  p += (size_t)nw * ne * 3 * sizeof(double);
+  QMC_CUDA(cudaMemcpy(p, w->W.wid, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  p += nw * sizeof(uint32_t);
+  QMC_CUDA(cudaMemcpy(p, w->W.weight, nw * sizeof(double), cudaMemcpyDeviceToHost));
+  *len = need;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_set_state(qmc_walkers_t w, const void* buf, size_t len) {
+  if (!w || !buf) return fail(QMC_EINVAL, "qmc_set_state: NULL argument");
+  StateHeader h;
+  if (len < sizeof h) return fail(QMC_ESTATE, "qmc_set_state: truncated state");
+  std::memcpy(&h, buf, sizeof h);
+  const int nw = w->W.n_w, ne = w->sys->P.n_e;
+  const size_t need = sizeof(StateHeader) + (size_t)nw * ne * 3 * sizeof(double) +
+                      (size_t)nw * (sizeof(uint32_t) + sizeof(double));
+  if (h.magic != kMagic || h.n_w != nw || h.n_e != ne || h.n_up != w->sys->P.n_up ||
+      h.seed != w->sys->d.seed || len != need)
+    return fail(QMC_ESTATE, "qmc_set_state: state does not match this walker set");
+  const char* p = static_cast<const char*>(buf) + sizeof h;
+  qmc_status r = upload_positions(w, reinterpret_cast<const double*>(p), false);
+  if (r != QMC_OK) return r;
+  p += (size_t)nw * ne * 3 * sizeof(double);
+  QMC_CUDA(cudaMemcpy(w->W.wid, p, nw * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  p += nw * sizeof(uint32_t);
+  QMC_CUDA(cudaMemcpy(w->W.weight, p, nw * sizeof(double), cudaMemcpyHostToDevice));
+  w->sweep = h.sweep;
+  return setup_state(w, 0);
+}
+
+extern "C" qmc_status qmc_check_errors(qmc_walkers_t w, void* stream) {
+  if (!w) return fail(QMC_EINVAL, "qmc_check_errors: NULL walkers");
+  return check_err(w, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int64_t qmc_launch_count(qmc_walkers_t w) { return w ? w->launches : 0; }
+
+extern "C" void qmc_walkers_destroy(qmc_walkers_t w) {
+  if (!w) return;
+  cudaDeviceSynchronize();
+  free_walkers(w);
+  delete w;
+}

@@ -1,0 +1,205 @@
+// Device building blocks: counter-based draws, periodic geometry, B-spline weights,
+// Jastrow functors and block reductions.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qmc_internal.h"
+
+namespace qmcgb {
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Counter-based generator of Salmon et al. (SC'11): ten rounds of two 32x32->64-bit
+// multiplications whose halves are XOR-mixed with the other two words and the key; the
+// key is bumped by the two Weyl constants between rounds.
+struct U32x4 { uint32_t v[4]; };
+
+__device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                               uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  U32x4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+// Word -> open interval (0, 1): (w + 0.5) 2^-32, exact in double.
+__device__ __forceinline__ double unit_open(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+// Gaussian displacement (Box-Muller on word pairs (0,1) and (2,3)) and acceptance
+// variate of the move of electron e of walker `wid` in sweep t (trial move of
+// Sec. "Trial Moves"; counter layout (t, e, wid, 0|1)).
+__device__ __forceinline__ void move_draws(const SysParams& S, uint32_t t, uint32_t e,
+                                           uint32_t wid, double xi[3], double& u) {
+  const U32x4 a = philox4x32_10(t, e, wid, 0u, S.seed_lo, S.seed_hi);
+  const double r1 = sqrt(-2.0 * log(unit_open(a.v[0])));
+  const double g1 = 2.0 * M_PI * unit_open(a.v[1]);
+  xi[0] = r1 * cos(g1);
+  xi[1] = r1 * sin(g1);
+  const double r2 = sqrt(-2.0 * log(unit_open(a.v[2])));
+  xi[2] = r2 * cos(2.0 * M_PI * unit_open(a.v[3]));
+  const U32x4 b = philox4x32_10(t, e, wid, 1u, S.seed_lo, S.seed_hi);
+  u = unit_open(b.v[0]);
+}
+
+// ------------------------------------------------------------------ geometry
+// Wrap into [0, L): the sign-corrected remainder.
+__device__ __forceinline__ double wrap_box(double x, double L) {
+  double m = fmod(x, L);
+  if (m != 0.0 && m < 0.0) m += L;
+  return m;
+}
+__device__ __forceinline__ double tfloor(double x) { return floor(x); }
+__device__ __forceinline__ float tfloor(float x) { return floorf(x); }
+__device__ __forceinline__ double trint(double x) { return rint(x); }
+__device__ __forceinline__ float trint(float x) { return rintf(x); }
+template <class T>
+__device__ __forceinline__ T min_image(T d, T L) { return d - L * trint(d / L); }
+
+// ------------------------------------------------------------------ B-spline weights
+// Uniform cubic B-spline weights of the nodes i-1..i+2 at fractional position t, and
+// their first and second derivatives (Sec. "B-spline basis sets").
+template <class T>
+__device__ __forceinline__ void bspline_w(T t, T b[4], T db[4], T d2b[4]) {
+  const T t2 = t * t, t3 = t2 * t, omt = T(1) - t;
+  b[0] = omt * omt * omt * T(1.0 / 6.0);
+  b[1] = (T(3) * t3 - T(6) * t2 + T(4)) * T(1.0 / 6.0);
+  b[2] = (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) * T(1.0 / 6.0);
+  b[3] = t3 * T(1.0 / 6.0);
+  db[0] = T(-0.5) * omt * omt;
+  db[1] = T(1.5) * t2 - T(2) * t;
+  db[2] = T(-1.5) * t2 + t + T(0.5);
+  db[3] = T(0.5) * t2;
+  d2b[0] = omt;
+  d2b[1] = T(3) * t - T(2);
+  d2b[2] = T(1) - T(3) * t;
+  d2b[3] = t;
+}
+
+// One radial Jastrow functor u(r), u'(r), u''(r): the four control points p_i..p_{i+3}
+// with i = floor(r M / rc) weighted by the cubic B-spline basis at t = r M / rc - i
+// (p_m = 0 for m > M; u = 0 for r >= rc). Sec. "Jastrow factor".
+// Precision-matched views of the system constants (no double<->float conversion in the
+// single-precision kernels: on this GPU those run on the slow FP64 pipe).
+template <class T> struct Cst;
+template <> struct Cst<double> {
+  __device__ static __forceinline__ double knot(const SysParams& S, int f, int m) { return S.jp[f][m]; }
+  __device__ static __forceinline__ double rc(const SysParams& S, int f) { return S.jrc[f]; }
+  __device__ static __forceinline__ double L(const SysParams& S) { return S.L; }
+  __device__ static __forceinline__ const double* ions(const SysParams& S) { return S.ions; }
+  __device__ static __forceinline__ double invd(const SysParams& S, int d) { return S.inv_delta[d]; }
+  __device__ static __forceinline__ double Z(const SysParams& S) { return S.ion_Z; }
+  __device__ static __forceinline__ double kappa(const SysParams& S) { return S.kappa; }
+};
+template <> struct Cst<float> {
+  __device__ static __forceinline__ float knot(const SysParams& S, int f, int m) { return S.jpf[f][m]; }
+  __device__ static __forceinline__ float rc(const SysParams& S, int f) { return S.jrcf[f]; }
+  __device__ static __forceinline__ float L(const SysParams& S) { return S.Lf; }
+  __device__ static __forceinline__ const float* ions(const SysParams& S) { return S.ionsf; }
+  __device__ static __forceinline__ float invd(const SysParams& S, int d) { return S.inv_deltaf[d]; }
+  __device__ static __forceinline__ float Z(const SysParams& S) { return S.ion_Zf; }
+  __device__ static __forceinline__ float kappa(const SysParams& S) { return S.kappaf; }
+};
+
+template <class T>
+__device__ __forceinline__ void jastrow_u(const SysParams& S, int f, T r, T& u, T& du, T& d2u) {
+  u = du = d2u = T(0);
+  const int M = S.jM[f];
+  const T rc = Cst<T>::rc(S, f);
+  if (M == 0 || !(r < rc)) return;
+  const T scale = T(M) / rc;
+  const T s = r * scale;
+  int i = (int)tfloor(s);
+  if (i < 0) i = 0;
+  const T t = s - T(i);
+  T b[4], db[4], d2b[4];
+  bspline_w<T>(t, b, db, d2b);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int m = i + q;
+    const T p = (m <= M) ? Cst<T>::knot(S, f, m) : T(0);
+    u += p * b[q];
+    du += p * db[q];
+    d2u += p * d2b[q];
+  }
+  du *= scale;
+  d2u *= scale * scale;
+}
+
+// Yukawa pair potential exp(-kappa r)/r for r < L/2 (stand-in for v_ee, v_eI).
+template <class T>
+__device__ __forceinline__ T yukawa(T r, T kappa, T L) {
+  return (r < T(0.5) * L) ? exp(-kappa * r) / r : T(0);
+}
+
+// ------------------------------------------------------------------ reductions
+template <int N, class T>
+__device__ __forceinline__ void warp_sum(T (&v)[N]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+// Sum N values over the block: warp sums in T, then thread 0 adds the warp partials in
+// double and stores the totals in out[0..N) (shared memory). Ends with a barrier, so
+// every thread may read out[] afterwards. red: shared [32 * N] of T.
+template <int N, class T>
+__device__ __forceinline__ void block_sum(T (&v)[N], T* red, double* out) {
+  warp_sum<N, T>(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) red[warp * N + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += (double)red[w * N + k];
+      out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ table loads
+template <class TT> struct TabVec;
+template <> struct TabVec<double> {
+  static constexpr int V = 2;
+  __device__ static __forceinline__ void load(const double* p, float (&)[2], double (&o)[2]) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = q.x; o[1] = q.y;
+  }
+};
+template <> struct TabVec<float> {
+  static constexpr int V = 4;
+  __device__ static __forceinline__ void load(const float* p, float (&o)[4], double (&)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  }
+};
+template <> struct TabVec<__nv_bfloat16> {
+  static constexpr int V = 8;
+  __device__ static __forceinline__ void load(const __nv_bfloat16* p, float (&o)[8], double (&)[8]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+    }
+  }
+};
+
+// Working-precision accumulator type of a table type.
+template <class TT> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+}  // namespace qmcgb

@@ -1,0 +1,67 @@
+// Internal structures shared by the C-ABI runtime and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qmcgb {
+
+constexpr int kMaxKnots = 32;       // largest Jastrow M
+constexpr int kMaxDelay = 64;       // largest delay rank k
+constexpr int kThreads = 256;       // threads of the per-walker kernels
+
+// One proposed move: new position and acceptance variate.
+struct alignas(32) Prop {
+  double x, y, z, u;
+};
+
+// Device error flags (bitwise OR into WalkParams::err).
+enum : int { kErrSingular = 1, kErrNonFinite = 2, kErrTimeout = 4 };
+
+// Read-only description of a system, passed to kernels by value.
+struct SysParams {
+  int n_up, n_dn, n_e, n_ion;
+  double L;
+  // tricubic B-spline table [nx][ny][nz][ld] (table precision)
+  const void* table;
+  int nx, ny, nz, ld, n_orb;
+  // Jastrow functors: 0 electron-ion, 1 same-spin pair, 2 opposite-spin pair
+  int jM[3];
+  double jrc[3];
+  double jp[3][kMaxKnots + 1];
+  float jpf[3][kMaxKnots + 1];   // single-precision copies for the mixed forms
+  float jrcf[3];
+  const double* ions;  // device [3][n_ion] (x block, y block, z block)
+  const float* ionsf;  // the same in single precision
+  double inv_delta[3]; // grid points per bohr along x, y, z (n / L)
+  float inv_deltaf[3];
+  float Lf, ion_Zf, kappaf;
+  double ion_Z, kappa;
+  int with_potential;
+  double v_ion_ion;    // Z^2 sum_{I<J} v(R_IJ), a constant
+  int move;            // 0 Metropolis, 1 drift
+  double step;
+  uint32_t seed_lo, seed_hi;
+};
+
+// Mutable walker arrays, passed to kernels by value (pointers to device memory).
+struct WalkParams {
+  int n_w;
+  int ld_v;            // row length of per-electron orbital vectors (>= max N_s, multiple of 8)
+  double* pos;         // [W][3][n_e]
+  void* binv;          // working precision [W][n_up*n_up + n_dn*n_dn]; Binv[e][j] = (A^-1)[j][e]
+  void* vgl;           // working precision [W][n_e][5][ld_v]: value, gx, gy, gz, lap at r_e
+  double* logdet;      // [W][2]
+  double* sgn;         // [W][2]
+  uint32_t* wid;       // [W]
+  double* weight;      // [W]
+  double* e_loc;       // [W]
+  double* log_psi;     // [W]
+  long long* n_acc;    // [W] accepted moves since the last accumulate
+  int* acc_since;      // [W][2] accepted (or proposed) moves since the last re-inversion
+  double* trace;       // optional [W][n_e][8] for the current sweep
+  const uint8_t* forced;  // optional [W][n_e] decisions
+  double* scratch64;   // [W][max N_s]^2 FP64 work matrices for re-inversion
+  int* err;            // device error flags
+};
+
+}  // namespace qmcgb

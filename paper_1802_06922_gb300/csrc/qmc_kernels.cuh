@@ -1,0 +1,774 @@
+// Kernels of the particle-by-particle sweep. Templated on the coefficient-table type TT
+// (double, float, bf16) and the working type TW (double, or float for the mixed forms).
+//
+// Precision discipline of the mixed forms (TW = float): on this GPU FP64 arithmetic and
+// double<->float conversions run at a small fraction of the FP32 rate, so per-element
+// work stays in single precision; double is used by one thread per move (the proposal,
+// ln|det| accumulation, the final sum of warp partials) and in the periodic FP64
+// re-inversion.
+#pragma once
+#include "qmc_device.cuh"
+
+namespace qmcgb {
+
+// =============================================================================
+// Orbital evaluation: value, gradient and Laplacian of orbitals [o_begin, o_begin+32V)
+// at point r, by one warp (Sec. "B-spline basis sets": 64 coefficient rows per point,
+// each a contiguous run of orbital coefficients). Lane l owns V consecutive orbitals and
+// reads them with one 16-byte load per row. r must be the same in every lane.
+// =============================================================================
+template <class TT, class TW>
+__device__ __forceinline__ void vgl_warp(const SysParams& S, const double r[3], int o_begin,
+                                         int n_eval, TW* __restrict__ out, int ld_out) {
+  using A = typename AccOf<TT>::type;
+  constexpr int V = TabVec<TT>::V;
+  const int lane = threadIdx.x & 31;
+  // grid cell and fractional offset per axis, computed in double by lanes 0..2
+  A tl = A(0);
+  int il = 0;
+  if (lane < 3) {
+    const double s = r[lane] * S.inv_delta[lane];
+    const double fi = floor(s);
+    tl = (A)(s - fi);
+    il = (int)fi;
+  }
+  const int o0 = o_begin + lane * V;
+  const int nn[3] = {S.nx, S.ny, S.nz};
+  A w[3][3][4];
+  int idx[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const A t = __shfl_sync(0xffffffffu, tl, d);
+    const int i = __shfl_sync(0xffffffffu, il, d);
+    bspline_w<A>(t, w[d][0], w[d][1], w[d][2]);
+    const A inv = Cst<A>::invd(S, d), inv2 = inv * inv;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      w[d][1][q] *= inv;
+      w[d][2][q] *= inv2;
+      idx[d][q] = (((i - 1 + q) % nn[d]) + nn[d]) % nn[d];   // always in [0, n)
+    }
+  }
+  if (o0 >= n_eval) return;
+  A acc[5][V];
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[k][v] = A(0);
+  const TT* __restrict__ tab = static_cast<const TT*>(S.table);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const A wxy = w[0][0][a] * w[1][0][b];
+      const A dxy = w[0][1][a] * w[1][0][b];
+      const A xdy = w[0][0][a] * w[1][1][b];
+      const A lxy = w[0][2][a] * w[1][0][b] + w[0][0][a] * w[1][2][b];
+      const size_t base = ((size_t)idx[0][a] * S.ny + idx[1][b]) * S.nz;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float cf[V];
+        double cd[V];
+        TabVec<TT>::load(tab + (base + idx[2][c]) * S.ld + o0, cf, cd);
+        const A wv = wxy * w[2][0][c], wgx = dxy * w[2][0][c], wgy = xdy * w[2][0][c];
+        const A wgz = wxy * w[2][1][c], wl = lxy * w[2][0][c] + wxy * w[2][2][c];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          A cv;
+          if constexpr (sizeof(A) == 8) cv = cd[v]; else cv = cf[v];
+          acc[0][v] += wv * cv;
+          acc[1][v] += wgx * cv;
+          acc[2][v] += wgy * cv;
+          acc[3][v] += wgz * cv;
+          acc[4][v] += wl * cv;
+        }
+      }
+    }
+  }
+  if (o0 + V <= n_eval) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      TW* p = out + k * ld_out + o0;
+      if constexpr (sizeof(A) == 8) {
+        *reinterpret_cast<double2*>(p) = make_double2(acc[k][0], acc[k][1]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; v += 4)
+          *reinterpret_cast<float4*>(p + v) =
+              make_float4(acc[k][v], acc[k][v + 1], acc[k][v + 2], acc[k][v + 3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (o0 + v < n_eval) out[k * ld_out + o0 + v] = (TW)acc[k][v];
+  }
+}
+
+// VGL of every electron of every walker at its current position (walker set-up and
+// re-inversion): one warp per (walker, electron, 32V-orbital chunk).
+template <class TT, class TW>
+__global__ void __launch_bounds__(256) k_vgl_current(SysParams S, WalkParams Wk) {
+  constexpr int V = TabVec<TT>::V;
+  const int chunks = (Wk.ld_v + 32 * V - 1) / (32 * V);
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long total = (long long)Wk.n_w * S.n_e * chunks;
+  if (gw >= total) return;
+  const int ch = (int)(gw % chunks);
+  const long long pe = gw / chunks;
+  const int e = (int)(pe % S.n_e);
+  const int w = (int)(pe / S.n_e);
+  const double* P = Wk.pos + (size_t)w * 3 * S.n_e;
+  const double r[3] = {P[e], P[S.n_e + e], P[2 * S.n_e + e]};
+  const int ns = e < S.n_up ? S.n_up : S.n_dn;
+  TW* out = static_cast<TW*>(Wk.vgl) + ((size_t)w * S.n_e + e) * 5 * Wk.ld_v;
+  vgl_warp<TT, TW>(S, r, ch * 32 * V, ns, out, Wk.ld_v);
+}
+
+// Metropolis proposals of electrons [e0, e1) of every walker in sweep t:
+// r' = wrap(r + step xi); prop[w][e-e0] = (x', y', z', u). One thread per move.
+static __global__ void k_proposals(SysParams S, WalkParams Wk, uint32_t t, int e0, int e1,
+                            Prop* __restrict__ prop) {
+  const int ne = e1 - e0;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)Wk.n_w * ne) return;
+  const int w = (int)(i / ne), e = e0 + (int)(i % ne);
+  double xi[3], u;
+  move_draws(S, t, (uint32_t)e, Wk.wid[w], xi, u);
+  const double* P = Wk.pos + (size_t)w * 3 * S.n_e;
+  Prop o;
+  o.x = wrap_box(P[e] + S.step * xi[0], S.L);
+  o.y = wrap_box(P[S.n_e + e] + S.step * xi[1], S.L);
+  o.z = wrap_box(P[2 * S.n_e + e] + S.step * xi[2], S.L);
+  o.u = u;
+  prop[i] = o;
+}
+
+// VGL at every proposed position of a chunk: out[w][e-e0][5][ld_v].
+template <class TT, class TW>
+__global__ void __launch_bounds__(256) k_vgl_proposals(SysParams S, WalkParams Wk, int e0, int e1,
+                                                      const Prop* __restrict__ prop,
+                                                      TW* __restrict__ out) {
+  constexpr int V = TabVec<TT>::V;
+  const int ns = e0 < S.n_up ? S.n_up : S.n_dn;
+  const int chunks = (ns + 32 * V - 1) / (32 * V);
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nmov = (long long)Wk.n_w * (e1 - e0);
+  if (gw >= nmov * chunks) return;
+  const int ch = (int)(gw % chunks);
+  const long long mv = gw / chunks;
+  const Prop p = prop[mv];
+  const double r[3] = {p.x, p.y, p.z};
+  vgl_warp<TT, TW>(S, r, ch * 32 * V, ns, out + (size_t)mv * 5 * Wk.ld_v, Wk.ld_v);
+}
+
+// =============================================================================
+// FP64 Gauss-Jordan inversion with partial pivoting of M (n x n, row-major, global),
+// in place, by one thread block. Returns false on an exactly zero or non-finite pivot.
+// ln|det M| and its sign are accumulated from the pivots and row interchanges.
+// =============================================================================
+static __device__ bool gj_invert_fp64(double* __restrict__ M, int n, double* colk, int* perm,
+                               double* redv, int* redi, double& logdet, double& sign) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double ld = 0.0, sg = 1.0;
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < n; i += nt) {
+      const double a = fabs(M[(size_t)i * n + k]);
+      if (a > best) { best = a; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    best = redv[0];
+    bi = redi[0];
+    for (int w = 1; w < nw; ++w)
+      if (redv[w] > best || (redv[w] == best && redi[w] < bi)) { best = redv[w]; bi = redi[w]; }
+    const double pv = M[(size_t)bi * n + k];
+    __syncthreads();
+    if (!(pv != 0.0) || !isfinite(pv)) { ok = false; break; }   // uniform across the block
+    if (bi != k) {
+      for (int j = tid; j < n; j += nt) {
+        const double a = M[(size_t)k * n + j];
+        M[(size_t)k * n + j] = M[(size_t)bi * n + j];
+        M[(size_t)bi * n + j] = a;
+      }
+      sg = -sg;
+    }
+    if (tid == 0) perm[k] = bi;
+    if (tid == 0) ld += log(fabs(pv));
+    if (pv < 0) sg = -sg;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) colk[i] = M[(size_t)i * n + k];
+    __syncthreads();
+    const double pinv = 1.0 / pv;
+    for (int j = tid; j < n; j += nt) {
+      const double pr = (j == k) ? pinv : M[(size_t)k * n + j] * pinv;
+      M[(size_t)k * n + j] = pr;
+      if (j == k) {
+        for (int i = 0; i < n; ++i)
+          if (i != k) M[(size_t)i * n + j] = -colk[i] * pinv;
+      } else {
+        for (int i = 0; i < n; ++i)
+          if (i != k) M[(size_t)i * n + j] -= colk[i] * pr;
+      }
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = perm[k];
+      if (p != k)
+        for (int i = tid; i < n; i += nt) {
+          const double a = M[(size_t)i * n + k];
+          M[(size_t)i * n + k] = M[(size_t)i * n + p];
+          M[(size_t)i * n + p] = a;
+        }
+      __syncthreads();
+    }
+  }
+  logdet = ld;   // valid in thread 0
+  sign = sg;
+  return ok;
+}
+
+// Re-inversion of one spin block of walker w from the orbital values at the current
+// positions: M = A^T (M[j][e] = phi_j(r_e)), so M^-1 = (A^-1)^T = Binv. Writes Binv in
+// working precision, ln|det A| and its sign. Called by one whole block.
+template <class TW>
+__device__ void reinvert_block(const SysParams& S, const WalkParams& Wk, int w, int spin,
+                               double* colk, int* perm, double* redv, int* redi) {
+  const int ns = spin ? S.n_dn : S.n_up;
+  if (ns == 0) return;
+  const int first = spin ? S.n_up : 0;
+  const size_t msz = (size_t)Wk.ld_v * Wk.ld_v;
+  double* M = Wk.scratch64 + (size_t)w * msz;
+  const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * S.n_e * 5 * Wk.ld_v;
+  for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) {
+    const int j = i / ns, e = i % ns;
+    M[i] = (double)VG[(size_t)(first + e) * 5 * Wk.ld_v + j];
+  }
+  __syncthreads();
+  double ld, sg;
+  const bool ok = gj_invert_fp64(M, ns, colk, perm, redv, redi, ld, sg);
+  TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+          (spin ? S.n_up * S.n_up : 0);
+  if (ok)
+    for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) B[i] = (TW)M[i];
+  if (threadIdx.x == 0) {
+    if (ok) {
+      Wk.logdet[2 * w + spin] = ld;
+      Wk.sgn[2 * w + spin] = sg;
+    } else {
+      atomicOr(Wk.err, kErrSingular);
+    }
+  }
+  __syncthreads();
+}
+
+__host__ __device__ inline size_t reinvert_smem_bytes(int ld_v) {
+  return sizeof(double) * (ld_v + 32) + sizeof(int) * (ld_v + 32);
+}
+
+template <class TW>
+__global__ void __launch_bounds__(256) k_reinvert(SysParams S, WalkParams Wk) {
+  extern __shared__ __align__(16) char smem_r[];
+  const int w = blockIdx.x >> 1, spin = blockIdx.x & 1;
+  double* colk = reinterpret_cast<double*>(smem_r);
+  double* redv = colk + Wk.ld_v;
+  int* perm = reinterpret_cast<int*>(redv + 32);
+  int* redi = perm + Wk.ld_v;
+  reinvert_block<TW>(S, Wk, w, spin, colk, perm, redv, redi);
+}
+
+// =============================================================================
+// The sequential sweep of electrons [e0, e1) (one spin block) of every walker: one
+// thread block per walker. Per move (Sec. "Trial Moves", Eq. accept_reject):
+//   x  = column e of the current inverse = Binv0[e] - sum_l z_l U_l   (delayed window)
+//   R  = phi(r') . x,   G = grad phi(r') . x / R
+//   dJ = sum over electrons and ions of u(|r' - r_j|) - u(|r_e - r_j|), grad J at r'
+//   A  = min(1, R^2 exp(2 dJ)), accept iff u < A.
+// Accepted moves enter a delayed-update window (rank-k, Sec. "Multi-Determinant
+// Slater-Jastrow Form"; k = 1 is Sherman-Morrison). With U_l = Binv0[e_l] (rows of the
+// inverse at the window's electrons), Phi_l their new orbital rows and
+// C[l][l'] = Phi_l . U_l', the current inverse is Binv[n] = Binv0[n] - sum_l (C^-1 d_n)_l U_l
+// with d_n[l] = Phi_l . Binv0[n] - delta(n, e_l); a full window is applied to every row
+// of Binv0 (the flush) and emptied.
+// =============================================================================
+template <class TW>
+struct SweepSmem {
+  double* posd;  // [3][n_e] exact positions
+  double* outd;  // [16] block sums and per-move scalars
+  double* colk;  // [ld_v]  re-inversion
+  double* redv;  // [32]
+  TW* posw;      // [3][n_e] positions in working precision
+  TW* phi;       // [4][ld_v]   proposal value and gradient
+  TW* row0;      // [ld_v]      Binv0[e]
+  TW* wphi;      // [k][ld_v]   window: new orbital rows
+  TW* wu;        // [k][ld_v]   window: Binv0 rows of the moved electrons
+  TW* rowbuf;    // [nwarps][ld_v]
+  TW* cinv;      // [k][k]
+  TW* dvec;      // [k]
+  TW* zvec;      // [k]
+  TW* crow;      // [k]
+  TW* yvec;      // [k]
+  TW* dz;        // [nwarps][2k]  flush: per-warp d and z
+  TW* red;       // [32][12]
+  TW* rnew;      // [4]
+  int* wrow;     // [k]
+  int* perm;     // [ld_v]
+  int* redi;     // [32]
+  int* flag;     // [4]
+};
+
+template <class TW>
+__host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int nwarps) {
+  size_t b = sizeof(double) * (3 * (size_t)n_e + 16 + ld_v + 32);
+  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (5 + 2 * k + nwarps) + (size_t)k * k +
+                     4 * k + 2 * k * nwarps + 32 * 12 + 4);
+  b += sizeof(int) * (k + ld_v + 32 + 4);
+  return (b + 15) & ~size_t(15);
+}
+
+template <class TW>
+__device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, int k, int nwarps) {
+  SweepSmem<TW> s;
+  double* d = reinterpret_cast<double*>(base);
+  s.posd = d; d += 3 * n_e;
+  s.outd = d; d += 16;
+  s.colk = d; d += ld_v;
+  s.redv = d; d += 32;
+  TW* t = reinterpret_cast<TW*>(d);
+  s.posw = t; t += 3 * n_e;
+  s.phi = t; t += 4 * ld_v;
+  s.row0 = t; t += ld_v;
+  s.wphi = t; t += (size_t)k * ld_v;
+  s.wu = t; t += (size_t)k * ld_v;
+  s.rowbuf = t; t += (size_t)nwarps * ld_v;
+  s.cinv = t; t += k * k;
+  s.dvec = t; t += k;
+  s.zvec = t; t += k;
+  s.crow = t; t += k;
+  s.yvec = t; t += k;
+  s.dz = t; t += 2 * k * nwarps;
+  s.red = t; t += 32 * 12;
+  s.rnew = t; t += 4;
+  int* ip = reinterpret_cast<int*>(t);
+  s.wrow = ip; ip += k;
+  s.perm = ip; ip += ld_v;
+  s.redi = ip; ip += 32;
+  s.flag = ip;
+  return s;
+}
+
+// Apply the window (m rows) to every row of Binv0 (B, ns x ns) and empty it:
+// Binv0[n] -= sum_l z_l U_l with z = C^-1 d_n, d_n[l] = Phi_l . Binv0[n] - delta(n, e_l).
+template <class TW>
+__device__ void flush_window(TW* __restrict__ B, int ns, int m, int kc,
+                             const SweepSmem<TW>& sm, int ld_v) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  TW* rb = sm.rowbuf + (size_t)warp * ld_v;
+  TW* dw = sm.dz + (size_t)warp * 2 * kc;
+  TW* zw = dw + kc;
+  for (int n = warp; n < ns; n += nw) {
+    for (int j = lane; j < ns; j += 32) rb[j] = B[(size_t)n * ns + j];
+    __syncwarp();
+    for (int l = 0; l < m; ++l) {
+      TW s = TW(0);
+      const TW* ph = sm.wphi + (size_t)l * ld_v;
+      for (int j = lane; j < ns; j += 32) s += ph[j] * rb[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) dw[l] = s - (sm.wrow[l] == n ? TW(1) : TW(0));
+    }
+    __syncwarp();
+    for (int l = lane; l < m; l += 32) {
+      TW z = TW(0);
+      for (int lp = 0; lp < m; ++lp) z += sm.cinv[l * kc + lp] * dw[lp];
+      zw[l] = z;
+    }
+    __syncwarp();
+    for (int j = lane; j < ns; j += 32) {
+      TW v = rb[j];
+      for (int l = 0; l < m; ++l) v -= zw[l] * sm.wu[(size_t)l * ld_v + j];
+      B[(size_t)n * ns + j] = v;
+    }
+    __syncwarp();
+  }
+}
+
+template <class TW, bool kFixedNode>
+__global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint32_t t, int e0,
+                                              int e1, int kc, const TW* __restrict__ Pv,
+                                              const Prop* __restrict__ prop, int reinv_period,
+                                              int reinv_on_acc) {
+  extern __shared__ __align__(16) char smem_s[];
+  const int w = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = nt >> 5;
+  const int n_e = S.n_e, ld_v = Wk.ld_v;
+  SweepSmem<TW> sm = carve<TW>(smem_s, n_e, ld_v, kc, nw);
+  const int spin = e0 >= S.n_up ? 1 : 0;
+  const int first = spin ? S.n_up : 0;
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int nmov = e1 - e0;
+  const TW Lw = Cst<TW>::L(S);
+  const TW* ionw = Cst<TW>::ions(S);
+  TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+          (spin ? S.n_up * S.n_up : 0);
+  TW* VG = static_cast<TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
+  double* gpos = Wk.pos + (size_t)w * 3 * n_e;
+  for (int i = tid; i < 3 * n_e; i += nt) {
+    const double p = gpos[i];
+    sm.posd[i] = p;
+    sm.posw[i] = (TW)p;
+  }
+  // per-walker scalars live in thread 0
+  double logdet = 0.0, sgn = 1.0;
+  long long nacc = 0;
+  if (tid == 0) {
+    logdet = Wk.logdet[2 * w + spin];
+    sgn = Wk.sgn[2 * w + spin];
+  }
+  int since = Wk.acc_since[2 * w + spin];
+  int m = 0;
+  __syncthreads();
+  for (int e = e0; e < e1; ++e) {
+    const int row = e - first;
+    const size_t mv = (size_t)w * nmov + (e - e0);
+    const TW* Pe = Pv + mv * 5 * ld_v;
+    if (tid == 0) {
+      const Prop pr = prop[mv];
+      sm.outd[10] = pr.x; sm.outd[11] = pr.y; sm.outd[12] = pr.z; sm.outd[13] = pr.u;
+      sm.rnew[0] = (TW)pr.x; sm.rnew[1] = (TW)pr.y; sm.rnew[2] = (TW)pr.z;
+    }
+    for (int j = tid; j < ns; j += nt) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sm.phi[c * ld_v + j] = Pe[c * ld_v + j];
+      sm.row0[j] = B[(size_t)row * ns + j];
+    }
+    __syncthreads();
+    // d_l = Phi_l . Binv0[e]
+    for (int l = warp; l < m; l += nw) {
+      TW s = TW(0);
+      for (int j = lane; j < ns; j += 32) s += sm.wphi[(size_t)l * ld_v + j] * sm.row0[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) sm.dvec[l] = s;
+    }
+    __syncthreads();
+    if (tid < m) {
+      TW z = TW(0);
+      for (int lp = 0; lp < m; ++lp) z += sm.cinv[tid * kc + lp] * sm.dvec[lp];
+      sm.zvec[tid] = z;
+    }
+    __syncthreads();
+    // x = Binv0[e] - sum_l z_l U_l; ratio and gradient partial sums
+    TW acc[9];
+    {
+      TW a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+      for (int j = tid; j < ns; j += nt) {
+        const TW r0 = sm.row0[j];
+        TW xv = r0;
+        for (int l = 0; l < m; ++l) xv -= sm.zvec[l] * sm.wu[(size_t)l * ld_v + j];
+        a0 += sm.phi[j] * xv;
+        a1 += sm.phi[ld_v + j] * xv;
+        a2 += sm.phi[2 * ld_v + j] * xv;
+        a3 += sm.phi[3 * ld_v + j] * xv;
+        a4 += sm.phi[j] * r0;
+      }
+      acc[0] = a0; acc[1] = a1; acc[2] = a2; acc[3] = a3; acc[4] = a4;
+    }
+    // Jastrow difference and gradient at r'
+    {
+      const TW rn[3] = {sm.rnew[0], sm.rnew[1], sm.rnew[2]};
+      const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+      TW dj = 0, gx = 0, gy = 0, gz = 0;
+      const int ntot = n_e + S.n_ion;
+      for (int j = tid; j < ntot; j += nt) {
+        if (j == e) continue;
+        TW q[3];
+        int f;
+        if (j < n_e) {
+          q[0] = sm.posw[j]; q[1] = sm.posw[n_e + j]; q[2] = sm.posw[2 * n_e + j];
+          f = ((j >= S.n_up) == (e >= S.n_up)) ? 1 : 2;
+        } else {
+          const int I = j - n_e;
+          q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
+          f = 0;
+        }
+        if (S.jM[f] == 0) continue;
+        TW dn[3], dq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dn[c] = min_image<TW>(rn[c] - q[c], Lw);
+          dq[c] = min_image<TW>(ro[c] - q[c], Lw);
+        }
+        const TW rnn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
+        const TW roo = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
+        TW un, dun, d2n, uo, duo, d2o;
+        jastrow_u<TW>(S, f, rnn, un, dun, d2n);
+        jastrow_u<TW>(S, f, roo, uo, duo, d2o);
+        dj += un - uo;
+        if (rnn > TW(0)) {
+          const TW g = dun / rnn;
+          gx += g * dn[0]; gy += g * dn[1]; gz += g * dn[2];
+        }
+      }
+      acc[5] = dj; acc[6] = gx; acc[7] = gy; acc[8] = gz;
+    }
+    block_sum<9, TW>(acc, sm.red, sm.outd);
+    // decision by thread 0 (double), broadcast through shared memory
+    if (tid == 0) {
+      const double R = sm.outd[0], dJ = sm.outd[5], u = sm.outd[13];
+      const bool ok = (R != 0.0) && isfinite(R);
+      const double A = ok ? fmin(1.0, R * R * exp(2.0 * dJ)) : 0.0;
+      bool accept = u < A;
+      if (kFixedNode && R < 0.0) accept = false;
+      if (Wk.forced) accept = Wk.forced[(size_t)w * n_e + e] != 0;
+      if (Wk.trace) {
+        double* tr = Wk.trace + ((size_t)w * n_e + e) * 8;
+        tr[0] = R;
+        tr[1] = dJ;
+        tr[2] = (ok ? sm.outd[1] / R : 0.0) + sm.outd[6];
+        tr[3] = (ok ? sm.outd[2] / R : 0.0) + sm.outd[7];
+        tr[4] = (ok ? sm.outd[3] / R : 0.0) + sm.outd[8];
+        tr[5] = u;
+        tr[6] = A;
+        tr[7] = accept ? 1.0 : 0.0;
+      }
+      sm.flag[0] = accept;
+      if (accept) {
+        ++nacc;
+        logdet += log(fabs(R));
+        if (R < 0) sgn = -sgn;
+        sm.posd[e] = sm.outd[10]; sm.posd[n_e + e] = sm.outd[11]; sm.posd[2 * n_e + e] = sm.outd[12];
+        sm.posw[e] = sm.rnew[0]; sm.posw[n_e + e] = sm.rnew[1]; sm.posw[2 * n_e + e] = sm.rnew[2];
+        sm.wrow[m] = row;
+        sm.rnew[3] = (TW)R;
+      }
+    }
+    __syncthreads();
+    const bool accept = sm.flag[0] != 0;
+    if (accept) {
+      TW* dst = VG + (size_t)e * 5 * ld_v;
+      for (int j = tid; j < ns; j += nt) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) dst[c * ld_v + j] = Pe[c * ld_v + j];
+        sm.wphi[(size_t)m * ld_v + j] = sm.phi[j];
+        sm.wu[(size_t)m * ld_v + j] = sm.row0[j];
+      }
+      // border of C: crow[l'] = phi' . U_l'
+      for (int l = warp; l < m; l += nw) {
+        TW s = TW(0);
+        for (int j = lane; j < ns; j += 32) s += sm.phi[j] * sm.wu[(size_t)l * ld_v + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sm.crow[l] = s;
+      }
+      __syncthreads();
+      if (tid < m) {
+        TW y = TW(0);
+        for (int l = 0; l < m; ++l) y += sm.crow[l] * sm.cinv[l * kc + tid];
+        sm.yvec[tid] = y;
+      }
+      __syncthreads();
+      // C^-1 of the bordered matrix (Schur complement s = R)
+      const TW sinv = TW(1) / sm.rnew[3];
+      for (int i = tid; i < (m + 1) * (m + 1); i += nt) {
+        const int a = i / (m + 1), b = i % (m + 1);
+        TW v;
+        if (a < m && b < m)
+          v = sm.cinv[a * kc + b] + sm.zvec[a] * sm.yvec[b] * sinv;
+        else if (a < m)
+          v = -sm.zvec[a] * sinv;
+        else if (b < m)
+          v = -sm.yvec[b] * sinv;
+        else
+          v = sinv;
+        sm.cinv[a * kc + b] = v;
+      }
+      ++m;
+      __syncthreads();
+      if (m == kc) {
+        flush_window<TW>(B, ns, m, kc, sm, ld_v);
+        m = 0;
+        __syncthreads();
+      }
+    }
+    if (reinv_period > 0) {
+      if (accept || !reinv_on_acc) ++since;
+      if (since >= reinv_period) {
+        if (m > 0) {
+          flush_window<TW>(B, ns, m, kc, sm, ld_v);
+          m = 0;
+        }
+        __syncthreads();
+        reinvert_block<TW>(S, Wk, w, spin, sm.colk, sm.perm, sm.redv, sm.redi);
+        if (tid == 0) {
+          logdet = Wk.logdet[2 * w + spin];
+          sgn = Wk.sgn[2 * w + spin];
+        }
+        since = 0;
+      }
+    }
+    __syncthreads();
+  }
+  if (m > 0) flush_window<TW>(B, ns, m, kc, sm, ld_v);
+  __syncthreads();
+  for (int i = tid; i < 3 * n_e; i += nt) gpos[i] = sm.posd[i];
+  if (tid == 0) {
+    Wk.logdet[2 * w + spin] = logdet;
+    Wk.sgn[2 * w + spin] = sgn;
+    Wk.n_acc[w] += nacc;
+    Wk.acc_since[2 * w + spin] = since;
+  }
+}
+
+// =============================================================================
+// Local energy (Sec. "Hamiltonian", E_L = Psi^-1 H Psi) and ln|Psi| of every walker.
+// Per electron i, with g_D = grad phi(r_i) . Binv[i] and l_D = lap phi(r_i) . Binv[i]:
+//   T_i = -1/2 [ l_D - |g_D|^2 + lap_i J + |g_D + grad_i J|^2 ],
+//   V = sum_{i<j} v(r_ij) - Z sum_{i,I} v(r_iI) + Z^2 sum_{I<J} v(R_IJ).
+// One block per walker, one warp per electron; per-electron terms summed in FP64.
+// =============================================================================
+template <class TW>
+__global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk) {
+  extern __shared__ __align__(16) char smem_e[];
+  TW* posw = reinterpret_cast<TW*>(smem_e);                  // [3][n_e]
+  const int w = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n_e = S.n_e, ld_v = Wk.ld_v;
+  const double* P = Wk.pos + (size_t)w * 3 * n_e;
+  for (int i = threadIdx.x; i < 3 * n_e; i += blockDim.x) posw[i] = (TW)P[i];
+  __syncthreads();
+  const TW Lw = Cst<TW>::L(S), kap = Cst<TW>::kappa(S), Zw = Cst<TW>::Z(S);
+  const TW* ionw = Cst<TW>::ions(S);
+  const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
+  const TW* Bw = static_cast<const TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn);
+  double kin = 0.0, pot = 0.0, jas = 0.0;   // lane 0 of each warp
+  for (int i = warp; i < n_e; i += nw) {
+    const int spin = i >= S.n_up;
+    const int ns = spin ? S.n_dn : S.n_up;
+    const int row = i - (spin ? S.n_up : 0);
+    const TW* Bi = Bw + (spin ? S.n_up * S.n_up : 0) + (size_t)row * ns;
+    const TW* v = VG + (size_t)i * 5 * ld_v;
+    TW s[10];
+    {
+      TW g0 = 0, g1 = 0, g2 = 0, l0 = 0;
+      for (int j = lane; j < ns; j += 32) {
+        const TW b = Bi[j];
+        g0 += v[ld_v + j] * b;
+        g1 += v[2 * ld_v + j] * b;
+        g2 += v[3 * ld_v + j] * b;
+        l0 += v[4 * ld_v + j] * b;
+      }
+      s[0] = g0; s[1] = g1; s[2] = g2; s[3] = l0;
+    }
+    const TW ri[3] = {posw[i], posw[n_e + i], posw[2 * n_e + i]};
+    {
+      TW gx = 0, gy = 0, gz = 0, lj = 0, jj = 0, pv = 0;
+      const int ntot = n_e + S.n_ion;
+      for (int j = lane; j < ntot; j += 32) {
+        if (j == i) continue;
+        TW q[3];
+        int f;
+        if (j < n_e) {
+          q[0] = posw[j]; q[1] = posw[n_e + j]; q[2] = posw[2 * n_e + j];
+          f = ((j >= S.n_up) == (i >= S.n_up)) ? 1 : 2;
+        } else {
+          const int I = j - n_e;
+          q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
+          f = 0;
+        }
+        TW dd[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dd[c] = min_image<TW>(ri[c] - q[c], Lw);
+        const TW r = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const bool once = (j >= n_e) || (j > i);
+        if (S.with_potential && once) {
+          const TW y = yukawa<TW>(r, kap, Lw);
+          pv += (j < n_e) ? y : -Zw * y;
+        }
+        if (S.jM[f] == 0) continue;
+        TW u, du, d2u;
+        jastrow_u<TW>(S, f, r, u, du, d2u);
+        if (once) jj += u;
+        if (r > TW(0)) {
+          const TW g = du / r;
+          gx += g * dd[0]; gy += g * dd[1]; gz += g * dd[2];
+          lj += d2u + TW(2) * g;
+        }
+      }
+      s[4] = gx; s[5] = gy; s[6] = gz; s[7] = lj; s[8] = pv; s[9] = jj;
+    }
+    warp_sum<10, TW>(s);
+    if (lane == 0) {
+      const double g0 = s[0], g1 = s[1], g2 = s[2];
+      const double lapD = (double)s[3] - (g0 * g0 + g1 * g1 + g2 * g2);
+      const double gx = g0 + (double)s[4], gy = g1 + (double)s[5], gz = g2 + (double)s[6];
+      kin += -0.5 * (lapD + (double)s[7] + gx * gx + gy * gy + gz * gz);
+      pot += (double)s[8];
+      jas += (double)s[9];
+    }
+  }
+  // sum the warp totals (lane 0 of each warp) in double
+  double* part = reinterpret_cast<double*>(posw);   // reuse after the barrier
+  __syncthreads();
+  if (lane == 0) { part[3 * warp] = kin; part[3 * warp + 1] = pot; part[3 * warp + 2] = jas; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double k = 0, p = 0, j = 0;
+    for (int q = 0; q < nw; ++q) { k += part[3 * q]; p += part[3 * q + 1]; j += part[3 * q + 2]; }
+    const double vii = S.with_potential ? S.v_ion_ion : 0.0;
+    Wk.e_loc[w] = k + p + vii;
+    Wk.log_psi[w] = Wk.logdet[2 * w] + Wk.logdet[2 * w + 1] + j;
+  }
+}
+
+inline size_t energy_smem_bytes(int n_e, size_t tw) {
+  const size_t b = tw * 3 * (size_t)n_e;
+  const size_t need = sizeof(double) * 3 * 32;   // warp partials, after the positions
+  return b > need ? b : need;
+}
+
+// FP64 sums over walkers: (sum w, sum w E, sum w E^2, accepted) and reset of n_acc.
+static __global__ void k_accumulate(WalkParams Wk, double* out, long long* nacc_total) {
+  __shared__ double red[32 * 3];
+  __shared__ long long redl[32];
+  double a[3] = {0, 0, 0};
+  long long acc = 0;
+  for (int w = threadIdx.x; w < Wk.n_w; w += blockDim.x) {
+    const double wt = Wk.weight[w], e = Wk.e_loc[w];
+    a[0] += wt; a[1] += wt * e; a[2] += wt * e * e;
+    acc += Wk.n_acc[w];
+    Wk.n_acc[w] = 0;
+  }
+  warp_sum<3, double>(a);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[3 * warp] = a[0]; red[3 * warp + 1] = a[1]; red[3 * warp + 2] = a[2]; redl[warp] = acc; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[3] = {0, 0, 0};
+    long long t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      s[0] += red[3 * q]; s[1] += red[3 * q + 1]; s[2] += red[3 * q + 2]; t += redl[q];
+    }
+    out[0] = s[0]; out[1] = s[1]; out[2] = s[2];
+    *nacc_total = t;
+  }
+}
+
+}  // namespace qmcgb

@@ -1,0 +1,48 @@
+// Instantiations of the orbital-evaluation kernels per coefficient-table type.
+#include "qmc_kernels.cuh"
+#include "qmc_launch.h"
+
+namespace qmcgb {
+namespace {
+
+template <class TT, class TW>
+cudaError_t vgl_current(const SysParams& S, const WalkParams& W, cudaStream_t st) {
+  constexpr int V = TabVec<TT>::V;
+  const long long chunks = (W.ld_v + 32 * V - 1) / (32 * V);
+  const long long warps = (long long)W.n_w * S.n_e * chunks;
+  const long long blocks = (warps * 32 + 255) / 256;
+  k_vgl_current<TT, TW><<<(unsigned)blocks, 256, 0, st>>>(S, W);
+  return cudaGetLastError();
+}
+
+template <class TT, class TW>
+cudaError_t vgl_proposals(const SysParams& S, const WalkParams& W, int e0, int e1,
+                          const void* prop, void* out, cudaStream_t st) {
+  constexpr int V = TabVec<TT>::V;
+  const int ns = e0 < S.n_up ? S.n_up : S.n_dn;
+  const long long chunks = (ns + 32 * V - 1) / (32 * V);
+  const long long warps = (long long)W.n_w * (e1 - e0) * chunks;
+  const long long blocks = (warps * 32 + 255) / 256;
+  k_vgl_proposals<TT, TW><<<(unsigned)blocks, 256, 0, st>>>(
+      S, W, e0, e1, static_cast<const Prop*>(prop), static_cast<TW*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+const TtLaunch& tt_launch_f64() {
+  static const TtLaunch L{TabVec<double>::V, vgl_current<double, double>,
+                          vgl_proposals<double, double>};
+  return L;
+}
+const TtLaunch& tt_launch_f32() {
+  static const TtLaunch L{TabVec<float>::V, vgl_current<float, float>, vgl_proposals<float, float>};
+  return L;
+}
+const TtLaunch& tt_launch_bf16() {
+  static const TtLaunch L{TabVec<__nv_bfloat16>::V, vgl_current<__nv_bfloat16, float>,
+                          vgl_proposals<__nv_bfloat16, float>};
+  return L;
+}
+
+}  // namespace qmcgb

@@ -1,0 +1,69 @@
+// Instantiations of the kernels that depend on the working precision.
+#include "qmc_kernels.cuh"
+#include "qmc_launch.h"
+
+namespace qmcgb {
+namespace {
+
+template <class TW>
+cudaError_t reinvert(const SysParams& S, const WalkParams& W, cudaStream_t st) {
+  k_reinvert<TW><<<2 * W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W);
+  return cudaGetLastError();
+}
+
+template <class TW>
+size_t sweep_smem(int n_e, int ld_v, int k) {
+  return sweep_smem_bytes<TW>(n_e, ld_v, k, kThreads / 32);
+}
+
+template <class TW>
+cudaError_t sweep(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1, int k,
+                  const void* P, const void* prop, int reinv_period, int reinv_on_acc,
+                  bool fixed_node, cudaStream_t st) {
+  const size_t smem = sweep_smem<TW>(S.n_e, W.ld_v, k);
+  auto kern = fixed_node ? k_sweep<TW, true> : k_sweep<TW, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<W.n_w, kThreads, smem, st>>>(S, W, t, e0, e1, k, static_cast<const TW*>(P),
+                                      static_cast<const Prop*>(prop), reinv_period,
+                                      reinv_on_acc);
+  return cudaGetLastError();
+}
+
+template <class TW>
+cudaError_t local_energy(const SysParams& S, const WalkParams& W, cudaStream_t st) {
+  const size_t smem = energy_smem_bytes(S.n_e, sizeof(TW));
+  cudaError_t e = cudaFuncSetAttribute(k_local_energy<TW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_local_energy<TW><<<W.n_w, kThreads, smem, st>>>(S, W);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+const TwLaunch& tw_launch_f64() {
+  static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
+                          sweep_smem<double>};
+  return L;
+}
+const TwLaunch& tw_launch_f32() {
+  static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
+                          sweep_smem<float>};
+  return L;
+}
+
+cudaError_t launch_proposals(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1,
+                             void* prop, cudaStream_t st) {
+  const long long n = (long long)W.n_w * (e1 - e0);
+  const int blocks = (int)((n + 255) / 256);
+  k_proposals<<<blocks, 256, 0, st>>>(S, W, t, e0, e1, static_cast<Prop*>(prop));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const WalkParams& W, double* out, long long* nacc, cudaStream_t st) {
+  k_accumulate<<<1, 256, 0, st>>>(W, out, nacc);
+  return cudaGetLastError();
+}
+
+}  // namespace qmcgb

@@ -1,0 +1,38 @@
+// Launchers of the kernels, one set per working precision (TW) and table type (TT).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "qmc_internal.h"
+
+namespace qmcgb {
+
+// Kernels that depend on the working precision only (TW = double or float).
+struct TwLaunch {
+  size_t tw_size;
+  cudaError_t (*reinvert)(const SysParams&, const WalkParams&, cudaStream_t);
+  cudaError_t (*sweep)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1, int k,
+                       const void* P, const void* prop, int reinv_period, int reinv_on_acc,
+                       bool fixed_node, cudaStream_t);
+  cudaError_t (*local_energy)(const SysParams&, const WalkParams&, cudaStream_t);
+  size_t (*sweep_smem)(int n_e, int ld_v, int k);
+};
+const TwLaunch& tw_launch_f64();
+const TwLaunch& tw_launch_f32();
+
+// Kernels that depend on the coefficient-table type.
+struct TtLaunch {
+  int vec;   // orbitals per 16-byte load
+  cudaError_t (*vgl_current)(const SysParams&, const WalkParams&, cudaStream_t);
+  cudaError_t (*vgl_proposals)(const SysParams&, const WalkParams&, int e0, int e1,
+                               const void* prop, void* out, cudaStream_t);
+};
+const TtLaunch& tt_launch_f64();
+const TtLaunch& tt_launch_f32();
+const TtLaunch& tt_launch_bf16();
+
+// Precision-independent kernels.
+cudaError_t launch_proposals(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
+                             void* prop, cudaStream_t);
+cudaError_t launch_accumulate(const WalkParams&, double* out, long long* nacc, cudaStream_t);
+
+}  // namespace qmcgb

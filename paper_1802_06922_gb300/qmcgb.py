@@ -1,0 +1,249 @@
+"""ctypes binding of libqmcgb (include/qmcgb.h): argument marshalling only.
+
+Every step of the particle-by-particle path runs in the library's CUDA kernels. Loading
+fails loudly (``RuntimeError``) when the library is missing or cannot be loaded; there is
+no CPU fallback. Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); they are passed to the library as plain pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqmcgb.so")
+
+QMC_OK, QMC_EINVAL, QMC_ENOMEM, QMC_ECUDA, QMC_ESINGULAR, QMC_ETIMEOUT, QMC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA",
+                -4: "QMC_ESINGULAR", -5: "QMC_ETIMEOUT", -6: "QMC_ESTATE"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+MOVES = {"metropolis": 0, "drift": 1}
+
+# Exported symbols and their ctypes signatures (argtypes, restype), as declared in
+# include/qmcgb.h.
+class SystemDesc(C.Structure):
+    _fields_ = [("n_up", C.c_int), ("n_dn", C.c_int), ("L", C.c_double), ("n_ion", C.c_int),
+                ("ion_pos", C.POINTER(C.c_double)), ("ion_Z", C.c_double),
+                ("kappa", C.c_double), ("with_potential", C.c_int), ("prec", C.c_int),
+                ("move", C.c_int), ("step", C.c_double), ("delay_k", C.c_int),
+                ("reinv_period", C.c_int), ("reinv_on_accepted", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+_vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+SIGNATURES = {
+    "qmc_system_create": ([C.POINTER(SystemDesc), C.POINTER(_vp)], _i),
+    "qmc_system_set_spline": ([_vp, _i, _i, _i, _i, _vp], _i),
+    "qmc_system_set_jastrow": ([_vp, _i, _i, _d, _vp, _i, _d], _i),
+    "qmc_walkers_create": ([_vp, _i, _vp, C.POINTER(_vp)], _i),
+    "qmc_sweep": ([_vp, _i, _vp], _i),
+    "qmc_measure": ([_vp, _vp, _vp, _vp], _i),
+    "qmc_accumulate_energy": ([_vp, _vp, _vp], _i),
+    "qmc_trace_enable": ([_vp, _vp, _sz], _i),
+    "qmc_replay_decisions": ([_vp, _vp, _i], _i),
+    "qmc_get_positions": ([_vp, _vp, _vp], _i),
+    "qmc_get_state": ([_vp, _vp, C.POINTER(_sz)], _i),
+    "qmc_set_state": ([_vp, _vp, _sz], _i),
+    "qmc_check_errors": ([_vp, _vp], _i),
+    "qmc_launch_count": ([_vp], C.c_int64),
+    "qmc_walkers_destroy": ([_vp], None),
+    "qmc_system_destroy": ([_vp], None),
+    "qmc_last_error": ([], C.c_char_p),
+}
+
+_lib: Optional[C.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libqmcgb (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    if not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqmcgb not found at {path}; run paper_1802_06922_gb300.build")
+    lib = C.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+class QMCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int):
+    if status != QMC_OK:
+        raise QMCError(status, load().qmc_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    assert a.is_contiguous(), "tensors must be contiguous"
+    return a.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class System:
+    """One system: cell, ions, orbital table, Jastrow functors, move parameters."""
+
+    def __init__(self, n_up, n_dn, L, ions, precision="fp64", move="metropolis", step=0.3,
+                 delay_k=1, reinv_period=0, reinv_on_accepted=False, seed=0, ion_Z=4.0,
+                 kappa=1.0, with_potential=True):
+        lib = load()
+        ions = np.ascontiguousarray(np.asarray(ions, dtype=np.float64).reshape(-1, 3))
+        self._ions = ions
+        d = SystemDesc(int(n_up), int(n_dn), float(L), int(ions.shape[0]),
+                       ions.ctypes.data_as(C.POINTER(C.c_double)), float(ion_Z), float(kappa),
+                       int(bool(with_potential)), PRECISIONS[precision], MOVES[move],
+                       float(step), int(delay_k), int(reinv_period), int(bool(reinv_on_accepted)),
+                       int(seed) & 0xFFFFFFFFFFFFFFFF)
+        h = C.c_void_p()
+        _check(lib.qmc_system_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.n_up, self.n_dn, self.L, self.precision = int(n_up), int(n_dn), float(L), precision
+
+    def set_spline(self, coef: np.ndarray):
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        nx, ny, nz, n_orb = coef.shape
+        _check(load().qmc_system_set_spline(self.h, nx, ny, nz, n_orb, coef.ctypes.data))
+
+    def set_jastrow(self, which: int, p, rcut: float, cusp: Optional[float] = None):
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        _check(load().qmc_system_set_jastrow(self.h, int(which), p.shape[0] - 1, float(rcut),
+                                             p.ctypes.data, int(cusp is not None),
+                                             float(cusp or 0.0)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qmc_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Walkers:
+    """A set of walkers of one system, resident on the GPU."""
+
+    def __init__(self, system: System, positions):
+        lib = load()
+        self.system = system
+        pos = positions
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float64)
+        self.n_w = int(pos.shape[0])
+        self.n_e = system.n_up + system.n_dn
+        h = C.c_void_p()
+        _check(lib.qmc_walkers_create(system.h, self.n_w, _ptr(pos), C.byref(h)))
+        self.h = h
+
+    def sweep(self, n: int = 1, stream=None):
+        _check(load().qmc_sweep(self.h, int(n), _stream_ptr(stream)))
+
+    def measure(self, e_local=None, log_psi=None, stream=None):
+        """Fill e_local / log_psi (numpy or torch, [n_w] float64); returns numpy copies
+        when both are None."""
+        if e_local is None and log_psi is None:
+            e = np.zeros(self.n_w)
+            l = np.zeros(self.n_w)
+            _check(load().qmc_measure(self.h, e.ctypes.data, l.ctypes.data, _stream_ptr(stream)))
+            return e, l
+        _check(load().qmc_measure(self.h, _ptr(e_local), _ptr(log_psi), _stream_ptr(stream)))
+        return e_local, log_psi
+
+    def accumulate(self, out=None, stream=None):
+        o = np.zeros(4) if out is None else out
+        _check(load().qmc_accumulate_energy(self.h, _ptr(o), _stream_ptr(stream)))
+        return o
+
+    def trace_enable(self, buf, nbytes: Optional[int] = None):
+        if buf is None:
+            _check(load().qmc_trace_enable(self.h, None, 0))
+            return
+        nb = buf.numel() * buf.element_size() if nbytes is None else nbytes
+        _check(load().qmc_trace_enable(self.h, _ptr(buf), nb))
+
+    def replay(self, bits, n_sweeps: int):
+        if bits is None:
+            _check(load().qmc_replay_decisions(self.h, None, 0))
+            return
+        if isinstance(bits, np.ndarray):
+            bits = np.ascontiguousarray(bits, dtype=np.uint8)
+        _check(load().qmc_replay_decisions(self.h, _ptr(bits), int(n_sweeps)))
+
+    def positions(self, out=None, stream=None):
+        o = np.zeros((self.n_w, self.n_e, 3)) if out is None else out
+        _check(load().qmc_get_positions(self.h, _ptr(o), _stream_ptr(stream)))
+        return o
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(load().qmc_get_state(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().qmc_get_state(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, state: bytes):
+        buf = C.create_string_buffer(state, len(state))
+        _check(load().qmc_set_state(self.h, buf, len(state)))
+
+    def check(self, stream=None):
+        _check(load().qmc_check_errors(self.h, _stream_ptr(stream)))
+
+    def launch_count(self) -> int:
+        return int(load().qmc_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qmc_walkers_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0,
+                       reinv_on_accepted=False, step=None, move=None) -> System:
+    """System (with spline table and Jastrow functors) from a ``synthetic.build_inputs``
+    dictionary, or any dictionary with the same keys."""
+    spec = inputs["spec"]
+    s = System(spec.n_up, spec.n_dn, spec.L, inputs["ions"], precision=precision,
+               move=move or spec.move, step=spec.step if step is None else step,
+               delay_k=delay_k, reinv_period=reinv_period,
+               reinv_on_accepted=reinv_on_accepted, seed=inputs["seed"], ion_Z=spec.ion_Z,
+               kappa=spec.kappa, with_potential=spec.with_potential)
+    s.set_spline(inputs["coef"])
+    j = inputs["jastrow"]
+    for which, key in enumerate(("eI", "same", "opp")):
+        p = j.get(key, np.zeros(0))
+        if p.size:
+            s.set_jastrow(which, p, inputs["rcut"])
+    return s

@@ -1,0 +1,115 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical
+seeded inputs, move by move."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from synthetic import build_inputs, small_spec, spec_for
+
+from parity_util import assert_trace_close, bf16_round, oracle_vmc, rel_err
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1802_06922_gb300 as q   # noqa: E402
+
+
+def _gpu_run(inputs, walker_ids, n_sweeps, precision="fp64", delay_k=1, reinv_period=0,
+             reinv_on_accepted=False, forced=None, coef=None):
+    d = dict(inputs)
+    if coef is not None:
+        d["coef"] = coef
+    s = q.system_from_inputs(d, precision=precision, delay_k=delay_k,
+                             reinv_period=reinv_period, reinv_on_accepted=reinv_on_accepted)
+    w = q.Walkers(s, np.ascontiguousarray(inputs["pos"][walker_ids]))
+    ne = s.n_up + s.n_dn
+    buf = torch.zeros((n_sweeps, len(walker_ids), ne, 8), dtype=torch.float64, device="cuda")
+    w.trace_enable(buf)
+    if forced is not None:
+        bits = np.ascontiguousarray(
+            forced.reshape(len(walker_ids), n_sweeps, ne).transpose(1, 0, 2).astype(np.uint8))
+        w.replay(bits, n_sweeps)
+    energies = []
+    for _ in range(n_sweeps):
+        w.sweep(1)
+        energies.append(w.measure())
+    tr = buf.cpu().numpy().transpose(1, 0, 2, 3).reshape(len(walker_ids), n_sweeps * ne, 8)
+    en = np.array(energies)          # [sweeps][2][n_w]
+    pos = w.positions()
+    w.close()
+    s.close()
+    return tr, en, pos
+
+
+def test_plane_wave_fp64_parity_and_zero_variance():
+    inputs = build_inputs(spec_for("pw14"), n_walkers=4)
+    ids = np.arange(4)
+    tr, en, pos = _gpu_run(inputs, ids, 3)
+    walkers, ref, ref_en = oracle_vmc(inputs, ids, 3)
+    assert_trace_close(tr, ref, 1e-10)
+    e_gpu = en[:, 0, :].T           # [n_w][sweeps]
+    assert np.all(rel_err(e_gpu, ref_en[..., 0], 1.0) < 1e-10)
+    assert np.all(rel_err(en[:, 1, :].T, ref_en[..., 2], 1.0) < 1e-10)
+    assert np.allclose(pos, np.array([w.R for w in walkers]), rtol=0, atol=1e-12)
+    # spline orbitals reproduce the zero-variance kinetic energy up to the spline error
+    e_ref = 2 * 6 * (2 * np.pi / 10) ** 2 / 2
+    assert np.all(np.abs(e_gpu - e_ref) / e_ref < ((2 * np.pi / 10) * (10 / 32)) ** 2)
+
+
+@pytest.mark.parametrize("delay_k", [1, 3])
+def test_slater_jastrow_fp64_parity_ragged(delay_k):
+    # 70 up / 66 down electrons: two 64-orbital chunks per FP64 warp with a ragged tail,
+    # a delay window that does not divide the block
+    inputs = build_inputs(small_spec(70, 66, grid=12, n_orb=72), n_walkers=2)
+    ids = np.arange(2)
+    tr, en, _ = _gpu_run(inputs, ids, 1, delay_k=delay_k)
+    _, ref, ref_en = oracle_vmc(inputs, ids, 1)
+    assert_trace_close(tr, ref, 1e-10)
+    assert np.all(rel_err(en[:, 0, :].T, ref_en[..., 0], 1.0) < 1e-10)
+    assert np.all(rel_err(en[:, 1, :].T, ref_en[..., 2], 1.0) < 1e-10)
+
+
+@pytest.mark.parametrize("precision,delay_k", [("fp32", 1), ("fp32", 4), ("bf16", 4)])
+def test_mixed_precision_lockstep(precision, delay_k):
+    inputs = build_inputs(small_spec(40, 40, grid=16), n_walkers=3)
+    ids = np.arange(3)
+    coef = bf16_round(inputs["coef"]) if precision == "bf16" else None
+    _, ref, ref_en = oracle_vmc(inputs, ids, 2, coef=coef)
+    forced = ref[..., 7]
+    tr, en, _ = _gpu_run(inputs, ids, 2, precision=precision, delay_k=delay_k,
+                         reinv_period=16, reinv_on_accepted=True, forced=forced, coef=coef)
+    # ratio gate: 1e-4 relative (floor 1e-3) at the 99.9th percentile
+    r = rel_err(tr[..., 0], ref[..., 0], 1e-3)
+    assert np.quantile(r, 0.999) < 1e-4, (r.max(), np.quantile(r, 0.999))
+    # a GPU decision that would differ from the oracle's must sit at u ~ A
+    own = tr[..., 5] < tr[..., 6]
+    flips = own != (ref[..., 7] == 1)
+    if flips.any():
+        assert np.all(np.abs(tr[..., 5] - ref[..., 6])[flips] <= 1e-4 * ref[..., 6][flips] + 1e-12)
+    # local energy gate: 1e-5 Ha per electron
+    ne = inputs["spec"].n_elec
+    assert np.max(np.abs(en[:, 0, :].T - ref_en[..., 0])) / ne < 1e-5
+
+
+def test_walker_state_round_trip_and_errors():
+    inputs = build_inputs(small_spec(5, 4, grid=8), n_walkers=3)
+    s = q.system_from_inputs(inputs)
+    w = q.Walkers(s, inputs["pos"])
+    w.sweep(2)
+    st = w.get_state()
+    e1, l1 = w.measure()
+    w.sweep(1)
+    e2, _ = w.measure()
+    w.set_state(st)
+    e1b, l1b = w.measure()
+    assert np.allclose(e1b, e1, rtol=1e-12) and np.allclose(l1b, l1, rtol=1e-12)
+    w.sweep(1)
+    assert np.allclose(w.measure()[0], e2, rtol=1e-12)
+    with pytest.raises(q.QMCError):
+        w.set_state(st[:-8])
+    w.close()
+    s.close()
