@@ -157,6 +157,16 @@ qmc_status qmc_get_positions(qmc_walkers_t w, double* pos, void* stream);
 qmc_status qmc_get_state(qmc_walkers_t w, void* buf, size_t* len);
 qmc_status qmc_set_state(qmc_walkers_t w, const void* buf, size_t len);
 
+/* Inspection of one walker's state (synchronous; host or device output):
+ *   qmc_get_inverse:  Binv[e][j] = (A^-1)[j][e] of spin block `spin` (0 up, 1 down) as
+ *                     doubles [N_s][N_s] (row e is the column of A^-1 that a move of the
+ *                     block's e-th electron dots with phi(r'));
+ *   qmc_get_orbitals: value, gradient x, y, z and Laplacian of orbitals 0..N_s-1 at every
+ *                     electron's current position, doubles [n_e][5][max(n_up, n_dn)].
+ * QMC_EINVAL for a walker index outside [0, n_walkers) or spin outside {0, 1}. */
+qmc_status qmc_get_inverse(qmc_walkers_t w, int walker, int spin, double* out);
+qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out);
+
 /* Waits for the walkers' queued work on `stream` and reports deferred device errors. */
 qmc_status qmc_check_errors(qmc_walkers_t w, void* stream);
 

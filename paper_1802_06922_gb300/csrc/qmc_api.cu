@@ -338,7 +338,7 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
       {(void**)&W.log_psi, nw * sizeof(double)},
       {(void**)&W.n_acc, nw * sizeof(long long)},
       {(void**)&W.acc_since, nw * 2 * sizeof(int)},
-      {(void**)&W.scratch64, nw * (size_t)W.ld_v * W.ld_v * sizeof(double)},
+      {(void**)&W.scratch64, 2 * nw * (size_t)W.ld_v * W.ld_v * sizeof(double)},
       {(void**)&W.err, sizeof(int)},
       {(void**)&w->d_P, nw * (size_t)w->chunk * 5 * W.ld_v * tw},
       {(void**)&w->d_prop, nw * (size_t)w->chunk * sizeof(Prop)},
@@ -554,6 +554,57 @@ extern "C" qmc_status qmc_set_state(qmc_walkers_t w, const void* buf, size_t len
   QMC_CUDA(cudaMemcpy(w->W.weight, p, nw * sizeof(double), cudaMemcpyHostToDevice));
   w->sweep = h.sweep;
   return setup_state(w, 0);
+}
+
+namespace {
+// Copies n elements of working precision at dev to host doubles.
+qmc_status fetch_tw(const qmc_walkers_s* w, const void* dev, size_t n, std::vector<double>& out) {
+  out.resize(n);
+  if (w->sys->tw->tw_size == sizeof(double)) {
+    QMC_CUDA(cudaMemcpy(out.data(), dev, n * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> f(n);
+    QMC_CUDA(cudaMemcpy(f.data(), dev, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) out[i] = f[i];
+  }
+  return QMC_OK;
+}
+}  // namespace
+
+extern "C" qmc_status qmc_get_inverse(qmc_walkers_t w, int walker, int spin, double* out) {
+  if (!w || !out) return fail(QMC_EINVAL, "qmc_get_inverse: NULL argument");
+  const SysParams& P = w->sys->P;
+  if (walker < 0 || walker >= w->W.n_w || spin < 0 || spin > 1)
+    return fail(QMC_EINVAL, "qmc_get_inverse: walker or spin out of range");
+  qmc_status r = check_err(w, 0);
+  if (r != QMC_OK) return r;
+  const size_t ns = spin ? P.n_dn : P.n_up;
+  const size_t off = (size_t)walker * ((size_t)P.n_up * P.n_up + (size_t)P.n_dn * P.n_dn) +
+                     (spin ? (size_t)P.n_up * P.n_up : 0);
+  std::vector<double> h;
+  r = fetch_tw(w, static_cast<const char*>(w->W.binv) + off * w->sys->tw->tw_size, ns * ns, h);
+  if (r != QMC_OK) return r;
+  QMC_CUDA(cudaMemcpy(out, h.data(), h.size() * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out) {
+  if (!w || !out) return fail(QMC_EINVAL, "qmc_get_orbitals: NULL argument");
+  const SysParams& P = w->sys->P;
+  if (walker < 0 || walker >= w->W.n_w) return fail(QMC_EINVAL, "qmc_get_orbitals: walker out of range");
+  qmc_status r = check_err(w, 0);
+  if (r != QMC_OK) return r;
+  const int ld = w->W.ld_v, nsm = std::max(P.n_up, P.n_dn);
+  std::vector<double> h;
+  r = fetch_tw(w, static_cast<const char*>(w->W.vgl) + (size_t)walker * P.n_e * 5 * ld * w->sys->tw->tw_size,
+               (size_t)P.n_e * 5 * ld, h);
+  if (r != QMC_OK) return r;
+  std::vector<double> o((size_t)P.n_e * 5 * nsm, 0.0);
+  for (int e = 0; e < P.n_e; ++e)
+    for (int c = 0; c < 5; ++c)
+      for (int j = 0; j < nsm; ++j) o[((size_t)e * 5 + c) * nsm + j] = h[((size_t)e * 5 + c) * ld + j];
+  QMC_CUDA(cudaMemcpy(out, o.data(), o.size() * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
 }
 
 extern "C" qmc_status qmc_check_errors(qmc_walkers_t w, void* stream) {

@@ -60,7 +60,7 @@ struct WalkParams {
   int* acc_since;      // [W][2] accepted (or proposed) moves since the last re-inversion
   double* trace;       // optional [W][n_e][8] for the current sweep
   const uint8_t* forced;  // optional [W][n_e] decisions
-  double* scratch64;   // [W][max N_s]^2 FP64 work matrices for re-inversion
+  double* scratch64;   // [W][2][ld_v][ld_v] FP64 work matrices for re-inversion
   int* err;            // device error flags
 };
 

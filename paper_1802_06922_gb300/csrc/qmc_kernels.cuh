@@ -252,7 +252,7 @@ __device__ void reinvert_block(const SysParams& S, const WalkParams& Wk, int w, 
   if (ns == 0) return;
   const int first = spin ? S.n_up : 0;
   const size_t msz = (size_t)Wk.ld_v * Wk.ld_v;
-  double* M = Wk.scratch64 + (size_t)w * msz;
+  double* M = Wk.scratch64 + (size_t)(2 * w + spin) * msz;   // one work matrix per (walker, spin)
   const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * S.n_e * 5 * Wk.ld_v;
   for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) {
     const int j = i / ns, e = i % ns;

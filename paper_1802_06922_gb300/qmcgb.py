@@ -48,6 +48,8 @@ SIGNATURES = {
     "qmc_get_positions": ([_vp, _vp, _vp], _i),
     "qmc_get_state": ([_vp, _vp, C.POINTER(_sz)], _i),
     "qmc_set_state": ([_vp, _vp, _sz], _i),
+    "qmc_get_inverse": ([_vp, _i, _i, _vp], _i),
+    "qmc_get_orbitals": ([_vp, _i, _vp], _i),
     "qmc_check_errors": ([_vp, _vp], _i),
     "qmc_launch_count": ([_vp], C.c_int64),
     "qmc_walkers_destroy": ([_vp], None),
@@ -211,6 +213,17 @@ class Walkers:
     def set_state(self, state: bytes):
         buf = C.create_string_buffer(state, len(state))
         _check(load().qmc_set_state(self.h, buf, len(state)))
+
+    def inverse(self, walker: int, spin: int) -> np.ndarray:
+        ns = self.system.n_dn if spin else self.system.n_up
+        o = np.zeros((ns, ns))
+        _check(load().qmc_get_inverse(self.h, int(walker), int(spin), o.ctypes.data))
+        return o
+
+    def orbitals(self, walker: int) -> np.ndarray:
+        o = np.zeros((self.n_e, 5, max(self.system.n_up, self.system.n_dn)))
+        _check(load().qmc_get_orbitals(self.h, int(walker), o.ctypes.data))
+        return o
 
     def check(self, stream=None):
         _check(load().qmc_check_errors(self.h, _stream_ptr(stream)))

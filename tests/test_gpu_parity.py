@@ -113,3 +113,39 @@ def test_walker_state_round_trip_and_errors():
         w.set_state(st[:-8])
     w.close()
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_orbitals_and_inverse_at_setup(precision):
+    """Stage check: orbital VGL at the initial positions against the oracle's tricubic
+    evaluation, and the FP64 re-inversion against numpy's LU inverse."""
+    from oracle.orbitals import SplineOrbitals
+    inputs = build_inputs(small_spec(70, 66, grid=12, n_orb=72), n_walkers=2)
+    s = q.system_from_inputs(inputs, precision=precision)
+    w = q.Walkers(s, inputs["pos"])
+    orb = SplineOrbitals(inputs["coef"], inputs["spec"].L)
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    for wk in range(2):
+        got = w.orbitals(wk)
+        R = inputs["pos"][wk]
+        for e in range(0, 136, 5):
+            ns = 70 if e < 70 else 66
+            v, g, lap = orb.vgl(R[e])
+            ref = np.vstack([v[None, :ns], g[:, :ns], lap[None, :ns]])
+            scale = np.abs(ref).max()
+            assert np.abs(got[e, :, :ns] - ref).max() <= tol * scale, (e, np.abs(got[e, :, :ns] - ref).max())
+        for spin, (first, ns) in enumerate(((0, 70), (70, 66))):
+            A = np.array([orb.values(R[first + i])[:ns] for i in range(ns)])
+            Binv = w.inverse(wk, spin)
+            ref = np.linalg.inv(A).T
+            err = np.abs(Binv - ref).max() / np.abs(ref).max()
+            # FP32 form: the matrix entries themselves are single precision, so the
+            # inverse can differ from the FP64 one by about cond(A) * 2^-24
+            eps = 1e-14 if precision == "fp64" else 2.0 ** -24
+            assert err < 10 * np.linalg.cond(A) * eps, (err, np.linalg.cond(A))
+            # the re-inversion is exact for its own input: A_gpu Binv^T = I
+            A_gpu = w.orbitals(wk)[first:first + ns, 0, :ns]
+            res = np.abs(A_gpu @ Binv.T - np.eye(ns)).max()
+            assert res < (1e-11 if precision == "fp64" else 2e-5), res
+    w.close()
+    s.close()
