@@ -1,0 +1,344 @@
+#!/usr/bin/env python
+"""Electron moves per second of the particle-by-particle VMC sweep on GB300.
+
+One step = one sweep of every walker: a Metropolis move proposed for each electron in
+turn (tricubic B-spline orbitals, determinant ratio with delayed rank-k inverse update,
+one- and two-body B-spline Jastrow, FP64 re-inversion at the configured cadence), then
+the local energy of every walker. The default workload is the 512-electron synthetic
+Slater-Jastrow system (256 up + 256 down, 256 orbitals on a 64^3 FP32 table of 268 MB,
+128 ions, 256 walkers).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): every rank runs an independent replica with its own walkers and
+Philox stream (weak scaling, no collective on the data path); the timed region is
+bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "electron moves/sec at N=512; mixed-vs-FP64 speedup at matched E_L error"
+UNIT = "electron moves/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--preset", default="sj512")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    p.add_argument("--delay-k", type=int, default=16)
+    p.add_argument("--reinv-period", type=int, default=128)
+    p.add_argument("--fp64-steps", type=int, default=4)
+    p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--cpu-cores", type=int, default=0)
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ workload description
+def workload(spec, precision, delay_k, reinv_period):
+    tab = {"fp32": "FP32", "bf16": "BF16", "fp64": "FP64"}[precision]
+    upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
+    re = f"FP64 re-inversion every {reinv_period} moves" if reinv_period else "no re-inversion"
+    return (f"{spec.name}: {spec.n_elec} electrons ({spec.n_up} up/{spec.n_dn} down), "
+            f"{spec.n_orb} orbitals on a {spec.grid}^3 {tab} tricubic B-spline table, "
+            f"{spec.n_ion} ions, J1/J2 B-spline M={spec.jastrow_M}, {spec.n_walkers} walkers, "
+            f"Metropolis sigma={spec.step}, {upd}, {re}")
+
+
+def table_bytes(spec, precision):
+    ld = (spec.n_orb + 7) // 8 * 8
+    b = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
+    return spec.grid ** 3 * ld * b
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 9]
+        self.f.close()
+        os.unlink(self.f.name)
+        return rows
+
+    @staticmethod
+    def summarise(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(pool, spec, cores, n_walkers, n_moves, sweep=0):
+    moves, wall = pool.run(list(range(n_walkers)), 0, n_moves, sweep)
+    return {"value": moves / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_moves} consecutive electron moves (sweep {sweep}) of each of "
+                      f"{n_walkers} walkers of {spec.name}: {moves} moves in {wall:.1f} s, "
+                      f"one single-threaded process per core"}
+
+
+def run_reference(args, spec, rank, world):
+    from oracle.timing import OraclePool
+    if rank != 0:
+        return
+    cores = args.cpu_cores or os.cpu_count()
+    pool = OraclePool(args.preset, cores)
+    per_step = max(1, 64 // max(1, spec.n_elec // 64))          # ~1 s of moves per core
+    for s in range(args.warmup):
+        pool.run(list(range(cores)), (s * per_step) % spec.n_elec, per_step)
+    tot, wall = 0, 0.0
+    for s in range(args.steps):
+        m, t = pool.run(list(range(cores)), ((args.warmup + s) * per_step) % spec.n_elec, per_step)
+        tot += m
+        wall += t
+    pool.close()
+    value = tot / wall
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload(spec, "fp64", 1, 0) + " (FP64 oracle: LU per move)",
+                       "walkers": spec.n_walkers, "electrons": spec.n_elec},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {per_step} consecutive moves of each of "
+                                       f"{cores} walkers, one process per core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def roofline(prof_ms, prof_n, spec, precision, moves_per_step, steps, peaks, delay_k, reinv_period):
+    """Roofline of the kernel class with the largest device time in the timed region."""
+    import paper_1802_06922_gb300.qmcgb as qb
+    names = qb.KERNEL_CLASSES
+    k = max(range(len(names)), key=lambda i: prof_ms[i])
+    name = names[k]
+    sec = prof_ms[k] / 1e3 / max(prof_n[k], 1)          # average launch duration
+    launches_per_step = prof_n[k] / steps
+    moves_per_launch = moves_per_step / max(launches_per_step, 1e-9)
+    bc = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if name == "vgl":
+        per_move = 64 * spec.n_orb * bc
+        achieved = per_move * moves_per_launch / sec / 1e9
+        out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+               "frac": achieved / hbm, "traffic": None, "kernel": "k_vgl_proposals",
+               "per_unit": f"64*N_orb*{bc} = {per_move} B per move"}
+    elif name == "sweep" and reinv_period:
+        # FP64 Gauss-Jordan: N_s^3 FMA (2 N_s^3 flop) per re-inversion
+        ns = spec.n_up
+        reinv_per_launch = moves_per_launch / reinv_period
+        flops = reinv_per_launch * 2.0 * ns ** 3
+        achieved = flops / sec / 1e12
+        peak = peaks.get("fp64_tflops", 1.26)
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak, "traffic": None, "kernel": "k_sweep",
+               "per_unit": f"2*N_s^3 = {2 * ns ** 3} FP64 flop per re-inversion, one per "
+                           f"{reinv_period} moves"}
+    else:
+        ns = spec.n_up
+        per_move = 2 * ns * ns * (4 if precision != "fp64" else 8) / max(delay_k, 1) * 1.5
+        achieved = per_move * moves_per_launch / sec / 1e9
+        out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+               "frac": achieved / hbm, "traffic": None, "kernel": f"k_{name}",
+               "per_unit": "inverse read+write per window flush"}
+    out["avg_launch_ms"] = sec * 1e3
+    out["share"] = prof_ms[k] / max(sum(prof_ms), 1e-12)
+    return out
+
+
+def run_ours(args, spec, rank, world, local_rank):
+    import numpy as np
+    pool = None
+    cores = args.cpu_cores or os.cpu_count()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle.timing import OraclePool
+        pool = OraclePool(args.preset, cores)           # spawned before the first GPU call
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import paper_1802_06922_gb300 as q
+    from synthetic import build_inputs
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    inputs = build_inputs(spec, seed=0)
+    inputs["seed"] = rank                                   # Philox stream of this replica
+    rng = np.random.default_rng(1000 + rank)
+    pos = rng.uniform(0, spec.L, size=(spec.n_walkers, spec.n_elec, 3))
+    stream = torch.cuda.current_stream()
+    moves_per_step = spec.n_walkers * spec.n_elec
+
+    def timed(system, n_steps, n_warm, profile=False):
+        w = q.Walkers(system, pos)
+        for _ in range(n_warm):
+            w.sweep(1, stream)
+        barrier()
+        l0 = w.launch_count()
+        if profile:
+            w.profile(True)
+        sampler = ClockSampler(local_rank) if profile else None
+        time.sleep(0.3 if profile else 0.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps):
+            w.sweep(1, stream)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clocks = ClockSampler.summarise(sampler.stop()) if sampler else None
+        prof = w.profile_read() if profile else None
+        launches = w.launch_count() - l0
+        w.check(stream)
+        e_loc, _ = w.measure()
+        w.close()
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, launches, clocks, e_loc
+
+    sysm = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+                                reinv_period=args.reinv_period, reinv_on_accepted=False)
+    ms, prof, launches, clocks, e_loc = timed(sysm, args.steps, args.warmup, profile=True)
+    value = world * moves_per_step * args.steps / (ms / 1e3)
+
+    # end to end through the public API with pinned host buffers: walker creation from
+    # host positions, every sweep followed by a device->host read of E_L and ln|Psi|,
+    # final positions read back
+    e2e_steps = args.e2e_steps or args.steps
+    pos_h = torch.from_numpy(pos).pin_memory()
+    e_h = torch.empty(spec.n_walkers, dtype=torch.float64).pin_memory()
+    l_h = torch.empty(spec.n_walkers, dtype=torch.float64).pin_memory()
+    pos_out = torch.empty_like(pos_h).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    w = q.Walkers(sysm, pos_h)
+    for _ in range(e2e_steps):
+        w.sweep(1, stream)
+        w.measure(e_h, l_h, stream)
+    w.positions(pos_out, stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    w.close()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * moves_per_step * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": pos.nbytes / e2e_steps,
+           "d2h_bytes_per_step": 2 * 8 * spec.n_walkers + pos.nbytes / e2e_steps,
+           "steps": e2e_steps,
+           "includes": "walker creation from pinned host positions (orbitals + FP64 inversion "
+                       "of every Slater matrix), per-sweep E_L and ln|Psi| read-back, final "
+                       "positions read-back"}
+    sysm.close()
+
+    fp64 = None
+    if not args.no_fp64:
+        s64 = q.system_from_inputs(inputs, precision="fp64", delay_k=1, reinv_period=0)
+        ms64, _, _, _, e64 = timed(s64, args.fp64_steps, 1)
+        s64.close()
+        v64 = world * moves_per_step * args.fp64_steps / (ms64 / 1e3)
+        fp64 = {"value": v64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                "dtype": "f64", "update": "Sherman-Morrison rank-1, no re-inversion"}
+
+    if rank != 0:
+        return
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    prof_ms, prof_n = prof
+    roof = roofline(prof_ms, prof_n, spec, args.precision, moves_per_step, args.steps, peaks,
+                    args.delay_k, args.reinv_period)
+    import paper_1802_06922_gb300.qmcgb as qb
+    kernels = {n: {"ms": float(prof_ms[i]), "launches": int(prof_n[i])}
+               for i, n in enumerate(qb.KERNEL_CLASSES) if prof_n[i]}
+    cpu = None
+    if pool is not None:
+        nw = min(spec.n_walkers, 2 * cores)
+        cpu = cpu_baseline(pool, spec, cores, nw, max(4, 32768 // spec.n_elec))
+        pool.close()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": workload(spec, args.precision, args.delay_k, args.reinv_period),
+                       "walkers_per_gpu": spec.n_walkers, "electrons": spec.n_elec,
+                       "moves_per_step": moves_per_step * world,
+                       "l2": f"inputs larger than L2: {table_bytes(spec, args.precision) / 1e6:.0f} MB "
+                             f"coefficient table gathered at random",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "gpu_launches": launches, "kernels": kernels, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64,
+            "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "e_local_mean": float(np.mean(e_loc))}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    from synthetic import spec_for
+    spec = spec_for(args.preset)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, spec, rank, world)
+    else:
+        run_ours(args, spec, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -170,6 +170,25 @@ qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out);
 /* Waits for the walkers' queued work on `stream` and reports deferred device errors. */
 qmc_status qmc_check_errors(qmc_walkers_t w, void* stream);
 
+/* Kernel classes reported by qmc_profile_read. */
+typedef enum {
+  QMC_K_PROPOSE = 0,      /* Metropolis proposals (Philox + Box-Muller) */
+  QMC_K_VGL = 1,          /* tricubic B-spline value/gradient/Laplacian at the proposals */
+  QMC_K_SWEEP = 2,        /* sequential ratio / accept / inverse-update sweep */
+  QMC_K_ENERGY = 3,       /* local energy and ln|Psi| */
+  QMC_K_REINVERT = 4,     /* standalone FP64 re-inversion */
+  QMC_K_VGL_CURRENT = 5,  /* orbitals at the current positions (set-up) */
+  QMC_K_ACCUMULATE = 6,   /* FP64 reductions over walkers */
+  QMC_NKERNELS = 8
+} qmc_kernel;
+
+/* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA
+ * events on its stream. qmc_profile_read synchronises, stores the summed device time (ms)
+ * and the launch count of each qmc_kernel class (arrays of QMC_NKERNELS, either may be
+ * NULL) and resets the sums. */
+qmc_status qmc_profile_enable(qmc_walkers_t w, int enable);
+qmc_status qmc_profile_read(qmc_walkers_t w, double* ms, int64_t* launches);
+
 /* Number of kernel launches the library enqueued since the walker set was created. */
 int64_t qmc_launch_count(qmc_walkers_t w);
 

@@ -96,7 +96,47 @@ struct qmc_walkers_s {
   int forced_sweeps = 0;
   int64_t launches = 0;
   bool energy_valid = false;
+  bool profiling = false;
+  struct Ev { int kind; cudaEvent_t a, b; };
+  std::vector<Ev> events;
+  double prof_ms[QMC_NKERNELS] = {0};
+  int64_t prof_n[QMC_NKERNELS] = {0};
 };
+
+namespace {
+// Launch bracket: counts one launch and, when profiling is on, records events around it.
+struct Bracket {
+  qmc_walkers_s* w;
+  cudaStream_t st;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Bracket(qmc_walkers_s* w_, cudaStream_t st_, int kind_) : w(w_), st(st_), kind(kind_) {
+    w->launches += 1;
+    if (!w->profiling) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  ~Bracket() {
+    if (!a) return;
+    cudaEventRecord(b, st);
+    w->events.push_back({kind, a, b});
+  }
+};
+
+void drain_events(qmc_walkers_s* w) {
+  for (auto& e : w->events) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      w->prof_ms[e.kind] += ms;
+      w->prof_n[e.kind] += 1;
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  w->events.clear();
+}
+}  // namespace
 
 // ------------------------------------------------------------------------ errors
 extern "C" const char* qmc_last_error(void) { return g_err.c_str(); }
@@ -268,10 +308,9 @@ qmc_status check_err(qmc_walkers_s* w, cudaStream_t st) {
 
 qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   qmc_system_s* s = w->sys;
-  QMC_CUDA(s->tt->vgl_current(s->P, w->W, st));
-  QMC_CUDA(s->tw->reinvert(s->P, w->W, st));
-  QMC_CUDA(s->tw->local_energy(s->P, w->W, st));
-  w->launches += 3;
+  { Bracket b(w, st, QMC_K_VGL_CURRENT); QMC_CUDA(s->tt->vgl_current(s->P, w->W, st)); }
+  { Bracket b(w, st, QMC_K_REINVERT); QMC_CUDA(s->tw->reinvert(s->P, w->W, st)); }
+  { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, w->W, st)); }
   QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
   w->energy_valid = true;
   return check_err(w, st);
@@ -396,15 +435,16 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
       const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
       for (int e0 = b0; e0 < b1; e0 += w->chunk) {
         const int e1 = std::min(b1, e0 + w->chunk);
-        QMC_CUDA(launch_proposals(P, W, w->sweep, e0, e1, w->d_prop, st));
-        QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, w->d_prop, w->d_P, st));
-        QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, s->d.delay_k, w->d_P, w->d_prop,
-                              s->d.reinv_period, s->d.reinv_on_accepted, false, st));
-        w->launches += 3;
+        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, w->sweep, e0, e1, w->d_prop, st)); }
+        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, w->d_prop, w->d_P, st)); }
+        {
+          Bracket b(w, st, QMC_K_SWEEP);
+          QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, s->d.delay_k, w->d_P, w->d_prop,
+                                s->d.reinv_period, s->d.reinv_on_accepted, false, st));
+        }
       }
     }
-    QMC_CUDA(s->tw->local_energy(P, W, st));
-    w->launches += 1;
+    { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(P, W, st)); }
     if (W.trace) ++w->traced;
     ++w->sweep;
     w->proposed += (long long)W.n_w * P.n_e;
@@ -423,8 +463,7 @@ extern "C" qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_
   if (!w) return fail(QMC_EINVAL, "qmc_measure: NULL walkers");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!w->energy_valid) {
-    QMC_CUDA(w->sys->tw->local_energy(w->sys->P, w->W, st));
-    w->launches += 1;
+    { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(w->sys->tw->local_energy(w->sys->P, w->W, st)); }
     w->energy_valid = true;
   }
   const size_t b = sizeof(double) * w->W.n_w;
@@ -438,8 +477,7 @@ extern "C" qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_
 extern "C" qmc_status qmc_accumulate_energy(qmc_walkers_t w, double* out, void* stream) {
   if (!w || !out) return fail(QMC_EINVAL, "qmc_accumulate_energy: NULL argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  QMC_CUDA(launch_accumulate(w->W, w->d_out, w->d_nacc, st));
-  w->launches += 1;
+  { Bracket b(w, st, QMC_K_ACCUMULATE); QMC_CUDA(launch_accumulate(w->W, w->d_out, w->d_nacc, st)); }
   double h[4];
   long long nacc = 0;
   QMC_CUDA(cudaMemcpyAsync(h, w->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -614,9 +652,28 @@ extern "C" qmc_status qmc_check_errors(qmc_walkers_t w, void* stream) {
 
 extern "C" int64_t qmc_launch_count(qmc_walkers_t w) { return w ? w->launches : 0; }
 
+extern "C" qmc_status qmc_profile_enable(qmc_walkers_t w, int enable) {
+  if (!w) return fail(QMC_EINVAL, "qmc_profile_enable: NULL walkers");
+  w->profiling = enable != 0;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_profile_read(qmc_walkers_t w, double* ms, int64_t* launches) {
+  if (!w) return fail(QMC_EINVAL, "qmc_profile_read: NULL walkers");
+  drain_events(w);
+  for (int k = 0; k < QMC_NKERNELS; ++k) {
+    if (ms) ms[k] = w->prof_ms[k];
+    if (launches) launches[k] = w->prof_n[k];
+    w->prof_ms[k] = 0.0;
+    w->prof_n[k] = 0;
+  }
+  return QMC_OK;
+}
+
 extern "C" void qmc_walkers_destroy(qmc_walkers_t w) {
   if (!w) return;
   cudaDeviceSynchronize();
+  drain_events(w);
   free_walkers(w);
   delete w;
 }

@@ -21,6 +21,8 @@ QMC_OK, QMC_EINVAL, QMC_ENOMEM, QMC_ECUDA, QMC_ESINGULAR, QMC_ETIMEOUT, QMC_ESTA
 STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA",
                 -4: "QMC_ESINGULAR", -5: "QMC_ETIMEOUT", -6: "QMC_ESTATE"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
+KERNEL_CLASSES = ("propose", "vgl", "sweep", "energy", "reinvert", "vgl_current",
+                  "accumulate", "other")
 MOVES = {"metropolis": 0, "drift": 1}
 
 # Exported symbols and their ctypes signatures (argtypes, restype), as declared in
@@ -52,6 +54,8 @@ SIGNATURES = {
     "qmc_get_orbitals": ([_vp, _i, _vp], _i),
     "qmc_check_errors": ([_vp, _vp], _i),
     "qmc_launch_count": ([_vp], C.c_int64),
+    "qmc_profile_enable": ([_vp, _i], _i),
+    "qmc_profile_read": ([_vp, _vp, _vp], _i),
     "qmc_walkers_destroy": ([_vp], None),
     "qmc_system_destroy": ([_vp], None),
     "qmc_last_error": ([], C.c_char_p),
@@ -227,6 +231,16 @@ class Walkers:
 
     def check(self, stream=None):
         _check(load().qmc_check_errors(self.h, _stream_ptr(stream)))
+
+    def profile(self, enable: bool = True):
+        _check(load().qmc_profile_enable(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """(ms, launches) per kernel class since the last read; indices as KERNEL_CLASSES."""
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+        _check(load().qmc_profile_read(self.h, ms.ctypes.data, n.ctypes.data))
+        return ms, n
 
     def launch_count(self) -> int:
         return int(load().qmc_launch_count(self.h))
