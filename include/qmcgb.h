@@ -170,6 +170,21 @@ qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out);
 /* Waits for the walkers' queued work on `stream` and reports deferred device errors. */
 qmc_status qmc_check_errors(qmc_walkers_t w, void* stream);
 
+/* Standalone FP64 re-inversion of a batch of Slater matrices (the periodic re-inversion
+ * of the sweep, exposed on its own; the determinant-ratio convention of Sec.
+ * "Multi-Determinant Slater-Jastrow Form").
+ *   prec   QMC_FP64: A and Binv are doubles; QMC_FP32 or QMC_FP32_BF16TAB: floats.
+ *   A      device [batch][n][n], A[b][e][j] = phi_j(r_e) (row e = orbitals of electron e).
+ *   Binv   device [batch][n][n], Binv[b][e][j] = (A^-1)[j][e].
+ *   logdet, sign  device [batch] doubles or NULL: ln|det A| and its sign; an exactly
+ *          singular matrix gets -inf, sign 0 and Binv = 0.
+ * Gauss-Jordan elimination with partial pivoting in FP64 on a work copy; the FP64 work
+ * matrices (batch * n * n doubles) are allocated on `stream` (stream-ordered) and released
+ * after the kernel. Asynchronous. QMC_EINVAL for n outside [1, 1024], batch outside
+ * [1, 2^20] or a host pointer; QMC_ENOMEM if the work area cannot be allocated. */
+qmc_status qmc_slater_invert(qmc_precision prec, const void* A, void* Binv, double* logdet,
+                             double* sign, int n, int batch, void* stream);
+
 /* Kernel classes reported by qmc_profile_read. */
 typedef enum {
   QMC_K_PROPOSE = 0,      /* Metropolis proposals (Philox + Box-Muller) */

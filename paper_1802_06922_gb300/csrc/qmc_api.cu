@@ -677,3 +677,25 @@ extern "C" void qmc_walkers_destroy(qmc_walkers_t w) {
   free_walkers(w);
   delete w;
 }
+
+// ------------------------------------------------------------------------ standalone S8
+extern "C" qmc_status qmc_slater_invert(qmc_precision prec, const void* A, void* Binv,
+                                        double* logdet, double* sign, int n, int batch,
+                                        void* stream) {
+  if (!A || !Binv) return fail(QMC_EINVAL, "qmc_slater_invert: NULL matrix pointer");
+  if (prec < QMC_FP64 || prec > QMC_FP32_BF16TAB) return fail(QMC_EINVAL, "qmc_slater_invert: unknown precision");
+  if (n < 1 || n > 1024) return fail(QMC_EINVAL, "qmc_slater_invert: n must be in [1, 1024]");
+  if (batch < 1 || batch > (1 << 20)) return fail(QMC_EINVAL, "qmc_slater_invert: batch must be in [1, 2^20]");
+  if (!is_device_ptr(A) || !is_device_ptr(Binv) || (logdet && !is_device_ptr(logdet)) ||
+      (sign && !is_device_ptr(sign)))
+    return fail(QMC_EINVAL, "qmc_slater_invert: every array must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const TwLaunch& tw = prec == QMC_FP64 ? tw_launch_f64() : tw_launch_f32();
+  double* work = nullptr;
+  QMC_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&work), (size_t)batch * n * n * sizeof(double), st));
+  const cudaError_t e = tw.invert_batch(A, Binv, logdet, sign, n, batch, work, st);
+  const cudaError_t f = cudaFreeAsync(work, st);
+  QMC_CUDA(e);
+  QMC_CUDA(f);
+  return QMC_OK;
+}

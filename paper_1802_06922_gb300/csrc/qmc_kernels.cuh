@@ -291,6 +291,43 @@ __global__ void __launch_bounds__(256) k_reinvert(SysParams S, WalkParams Wk) {
   reinvert_block<TW>(S, Wk, w, spin, colk, perm, redv, redi);
 }
 
+// Batched FP64 re-inversion of caller-supplied Slater matrices (one block per matrix):
+// A[b][e][j] = phi_j(r_e) in T, Binv[b][e][j] = (A^-1)[j][e] in T, ln|det A| and sign in
+// double (-inf and 0 for an exactly singular matrix). `work` holds one FP64 n x n matrix
+// per block.
+template <class T>
+__global__ void __launch_bounds__(256) k_invert_batch(const T* __restrict__ A, T* __restrict__ Binv,
+                                                     double* __restrict__ logdet,
+                                                     double* __restrict__ sign, int n,
+                                                     double* __restrict__ work) {
+  extern __shared__ __align__(16) char smem_i[];
+  double* colk = reinterpret_cast<double*>(smem_i);
+  double* redv = colk + n;
+  int* perm = reinterpret_cast<int*>(redv + 32);
+  int* redi = perm + n;
+  const size_t nn = (size_t)n * n;
+  const int b = blockIdx.x;
+  double* M = work + (size_t)b * nn;
+  const T* Ab = A + (size_t)b * nn;
+  for (size_t i = threadIdx.x; i < nn; i += blockDim.x) {
+    const size_t j = i / n, e = i % n;
+    M[i] = (double)Ab[e * n + j];
+  }
+  __syncthreads();
+  double ld, sg;
+  const bool ok = gj_invert_fp64(M, n, colk, perm, redv, redi, ld, sg);
+  T* Bb = Binv + (size_t)b * nn;
+  for (size_t i = threadIdx.x; i < nn; i += blockDim.x) Bb[i] = ok ? (T)M[i] : T(0);
+  if (threadIdx.x == 0) {
+    if (logdet) logdet[b] = ok ? ld : -INFINITY;
+    if (sign) sign[b] = ok ? sg : 0.0;
+  }
+}
+
+__host__ __device__ inline size_t invert_batch_smem_bytes(int n) {
+  return sizeof(double) * (n + 32) + sizeof(int) * (n + 32);
+}
+
 // =============================================================================
 // The sequential sweep of electrons [e0, e1) (one spin block) of every walker: one
 // thread block per walker. Per move (Sec. "Trial Moves", Eq. accept_reject):

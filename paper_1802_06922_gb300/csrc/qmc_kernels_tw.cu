@@ -40,16 +40,24 @@ cudaError_t local_energy(const SysParams& S, const WalkParams& W, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <class TW>
+cudaError_t invert_batch(const void* A, void* Binv, double* logdet, double* sign, int n,
+                         int batch, double* work, cudaStream_t st) {
+  k_invert_batch<TW><<<batch, kThreads, invert_batch_smem_bytes(n), st>>>(
+      static_cast<const TW*>(A), static_cast<TW*>(Binv), logdet, sign, n, work);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const TwLaunch& tw_launch_f64() {
   static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
-                          sweep_smem<double>};
+                          sweep_smem<double>, invert_batch<double>};
   return L;
 }
 const TwLaunch& tw_launch_f32() {
   static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
-                          sweep_smem<float>};
+                          sweep_smem<float>, invert_batch<float>};
   return L;
 }
 

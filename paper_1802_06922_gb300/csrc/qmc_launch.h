@@ -15,6 +15,8 @@ struct TwLaunch {
                        bool fixed_node, cudaStream_t);
   cudaError_t (*local_energy)(const SysParams&, const WalkParams&, cudaStream_t);
   size_t (*sweep_smem)(int n_e, int ld_v, int k);
+  cudaError_t (*invert_batch)(const void* A, void* Binv, double* logdet, double* sign, int n,
+                              int batch, double* work, cudaStream_t);
 };
 const TwLaunch& tw_launch_f64();
 const TwLaunch& tw_launch_f32();

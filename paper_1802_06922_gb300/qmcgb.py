@@ -59,6 +59,7 @@ SIGNATURES = {
     "qmc_walkers_destroy": ([_vp], None),
     "qmc_system_destroy": ([_vp], None),
     "qmc_last_error": ([], C.c_char_p),
+    "qmc_slater_invert": ([_i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
 }
 
 _lib: Optional[C.CDLL] = None
@@ -255,6 +256,15 @@ class Walkers:
             self.close()
         except Exception:
             pass
+
+
+def slater_invert(A, Binv, logdet=None, sign=None, stream=None):
+    """FP64 re-inversion of a batch of Slater matrices: A and Binv are CUDA tensors
+    [batch][n][n] (float64 or float32), logdet/sign CUDA float64 [batch] or None."""
+    prec = PRECISIONS["fp64"] if A.element_size() == 8 else PRECISIONS["fp32"]
+    batch, n, _ = A.shape
+    _check(load().qmc_slater_invert(prec, _ptr(A), _ptr(Binv), _ptr(logdet), _ptr(sign), n,
+                                    batch, _stream_ptr(stream)))
 
 
 def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0,
