@@ -185,6 +185,28 @@ qmc_status qmc_check_errors(qmc_walkers_t w, void* stream);
 qmc_status qmc_slater_invert(qmc_precision prec, const void* A, void* Binv, double* logdet,
                              double* sign, int n, int batch, void* stream);
 
+/* The same computation as qmc_slater_invert, for callers that must not allocate device
+ * memory: applications whose device memory is owned by their own pool allocator (a
+ * cudaMalloc from inside this library could fail, or fragment a pool that has reserved
+ * nearly all of HBM), and latency-sensitive loops that cannot accept the device-wide
+ * synchronisation and unpredictable latency an allocation or free may bring. The paper
+ * has no counterpart; this is a property of the library, not of the method.
+ *   Arguments, layouts and results are exactly those of qmc_slater_invert.
+ *   Work area: a fixed FP64 array compiled into libqmcgb, 2^21 doubles (16 MiB); every GPU
+ *   on which the library is used holds it until the process exits. batch * n * n must not
+ *   exceed 2^21 (for example 32 matrices of 256 x 256, or 8 of 512 x 512); a larger request
+ *   fails with QMC_EINVAL before anything is enqueued. No cudaMalloc, cudaFree or other
+ *   allocating routine is called.
+ *   The first call on each device looks up the work area's device address with that device
+ *   current; make that first call before any stream capture.
+ *   Every call uses the same work area, which keeps the last call's contents. A call
+ *   overwrites each work element before reading it, so nothing needs clearing, but calls
+ *   whose kernels overlap on the GPU (different streams or host threads) race on the work
+ *   area and corrupt each other's results: serialise them. Asynchronous on `stream`. */
+qmc_status qmc_slater_invert_noalloc(qmc_precision prec, const void* A, void* Binv,
+                                     double* logdet, double* sign, int n, int batch,
+                                     void* stream);
+
 /* Kernel classes reported by qmc_profile_read. */
 typedef enum {
   QMC_K_PROPOSE = 0,      /* Metropolis proposals (Philox + Box-Muller) */

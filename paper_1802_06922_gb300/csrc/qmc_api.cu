@@ -141,6 +141,11 @@ void drain_events(qmc_walkers_s* w) {
 // ------------------------------------------------------------------------ errors
 extern "C" const char* qmc_last_error(void) { return g_err.c_str(); }
 
+int qmcgb::set_last_error(int s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+
 // ------------------------------------------------------------------------ system
 extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out) {
   if (!desc || !out) return fail(QMC_EINVAL, "qmc_system_create: NULL argument");

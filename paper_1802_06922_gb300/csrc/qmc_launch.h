@@ -37,4 +37,7 @@ cudaError_t launch_proposals(const SysParams&, const WalkParams&, uint32_t t, in
                              void* prop, cudaStream_t);
 cudaError_t launch_accumulate(const WalkParams&, double* out, long long* nacc, cudaStream_t);
 
+// Records the message returned by qmc_last_error on this thread; returns s.
+int set_last_error(int s, const char* msg);
+
 }  // namespace qmcgb

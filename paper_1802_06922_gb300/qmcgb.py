@@ -60,6 +60,7 @@ SIGNATURES = {
     "qmc_system_destroy": ([_vp], None),
     "qmc_last_error": ([], C.c_char_p),
     "qmc_slater_invert": ([_i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
+    "qmc_slater_invert_noalloc": ([_i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
 }
 
 _lib: Optional[C.CDLL] = None
@@ -265,6 +266,15 @@ def slater_invert(A, Binv, logdet=None, sign=None, stream=None):
     batch, n, _ = A.shape
     _check(load().qmc_slater_invert(prec, _ptr(A), _ptr(Binv), _ptr(logdet), _ptr(sign), n,
                                     batch, _stream_ptr(stream)))
+
+
+def slater_invert_noalloc(A, Binv, logdet=None, sign=None, stream=None):
+    """As slater_invert, for callers that cannot allocate device memory: uses the
+    library's fixed 16 MiB work area (batch * n * n <= 2**21); concurrent calls race."""
+    prec = PRECISIONS["fp64"] if A.element_size() == 8 else PRECISIONS["fp32"]
+    batch, n, _ = A.shape
+    _check(load().qmc_slater_invert_noalloc(prec, _ptr(A), _ptr(Binv), _ptr(logdet), _ptr(sign),
+                                            n, batch, _stream_ptr(stream)))
 
 
 def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0,
