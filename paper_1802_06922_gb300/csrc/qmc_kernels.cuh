@@ -329,6 +329,144 @@ __host__ __device__ inline size_t invert_batch_smem_bytes(int n) {
 }
 
 // =============================================================================
+// Re-inversion of the single-precision forms by one Newton step with an accurate residual.
+// GB300 runs FP64 at 1/71 of the FP32 rate, so an O(N^3) FP64 inversion per period would
+// dominate the sweep. Instead, with X = A^-1 the current (drifted) inverse:
+//   R = I - A X   summed with the error-free transformations of Dot2 (Ogita, Rump and
+//                 Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005)):
+//                 TwoProduct by FMA and TwoSum, as accurate as a double-length product of
+//                 the single-precision A and X, on the FP32 pipe;
+//   X <- X + X R  in single precision (R is small, so this product needs no extra care).
+// One step takes an inverse that has drifted by |R| to one limited by the FP32 storage of
+// X (error ~ |R|^2 + 2^-24). Binv = X^T, so the update reads Binv[e] += sum_f R[f][e] Binv[f].
+// A residual above kRefineMax (or not finite) means the inverse is too far off for one
+// step; the caller then falls back to the FP64 Gauss-Jordan re-inversion.
+// =============================================================================
+constexpr float kRefineMax = 1e-2f;
+constexpr int kTileElems = 2 * 32 * 64;      // two 32 x 64 single-precision tiles
+
+__device__ __forceinline__ void dot2_step(float a, float b, float& P, float& E) {
+  const float h = __fmul_rn(a, b);
+  const float r = __fmaf_rn(a, b, -h);         // a*b = h + r exactly
+  const float x = __fadd_rn(P, h);             // TwoSum(P, h) = x + q exactly
+  const float z = __fsub_rn(x, P);
+  const float q = __fadd_rn(__fsub_rn(P, __fsub_rn(x, z)), __fsub_rn(h, z));
+  P = x;
+  E = __fadd_rn(E, __fadd_rn(q, r));
+}
+
+// Returns max |R| over the matrix (identical in every thread).
+static __device__ float refine_inverse(const SysParams& S, const WalkParams& Wk, int w, int spin,
+                                float* tile, float* redf) {
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int first = spin ? S.n_up : 0;
+  const int ld5 = 5 * Wk.ld_v;
+  const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
+  float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+             (spin ? S.n_up * S.n_up : 0);
+  float* Rg = reinterpret_cast<float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
+  float* Bn = Rg + (size_t)ns * ns;
+  float* As = tile;
+  float* Bs = tile + 32 * 64;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float rmax = 0.f;
+  // R = I - A Binv^T, 64 x 64 output tiles, 4 x 4 outputs per thread
+  for (int te = 0; te < ns; te += 64)
+    for (int tf = 0; tf < ns; tf += 64) {
+      float P[4][4], E[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[i][j] = E[i][j] = 0.f;
+      for (int k0 = 0; k0 < ns; k0 += 32) {
+        __syncthreads();
+        for (int i = tid; i < 64 * 32; i += blockDim.x) {
+          const int r = i & 63, kk = i >> 6, j = k0 + kk;
+          const int e = te + r, f = tf + r;
+          As[kk * 64 + r] = (e < ns && j < ns) ? VG[(size_t)e * ld5 + j] : 0.f;
+          Bs[kk * 64 + r] = (f < ns && j < ns) ? B[(size_t)f * ns + j] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 32; ++kk) {
+          float a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            a[i] = As[kk * 64 + ty + 16 * i];
+            b[i] = Bs[kk * 64 + tx + 16 * i];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dot2_step(a[i], b[j], P[i][j], E[i][j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = te + ty + 16 * i, f = tf + tx + 16 * j;
+          if (e < ns && f < ns) {
+            const float r = __fsub_rn(__fsub_rn(e == f ? 1.f : 0.f, P[i][j]), E[i][j]);
+            Rg[(size_t)e * ns + f] = r;
+            rmax = fmaxf(rmax, isfinite(r) ? fabsf(r) : INFINITY);
+          }
+        }
+    }
+  // max |R| over the block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  __syncthreads();
+  if ((tid & 31) == 0) redf[tid >> 5] = rmax;
+  __syncthreads();
+  rmax = 0.f;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) rmax = fmaxf(rmax, redf[q]);
+  if (!(rmax <= kRefineMax)) return rmax;
+  // Bn[e][j] = Binv[e][j] + sum_f R[f][e] Binv[f][j]
+  for (int te = 0; te < ns; te += 64)
+    for (int tj = 0; tj < ns; tj += 64) {
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      for (int f0 = 0; f0 < ns; f0 += 32) {
+        __syncthreads();
+        for (int i = tid; i < 64 * 32; i += blockDim.x) {
+          const int c = i & 63, kk = i >> 6, f = f0 + kk;
+          As[kk * 64 + c] = (f < ns && te + c < ns) ? Rg[(size_t)f * ns + te + c] : 0.f;
+          Bs[kk * 64 + c] = (f < ns && tj + c < ns) ? B[(size_t)f * ns + tj + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 32; ++kk) {
+          float a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            a[i] = As[kk * 64 + ty + 16 * i];
+            b[i] = Bs[kk * 64 + tx + 16 * i];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = te + ty + 16 * i, c = tj + tx + 16 * j;
+          if (e < ns && c < ns) Bn[(size_t)e * ns + c] = B[(size_t)e * ns + c] + acc[i][j];
+        }
+    }
+  __syncthreads();
+  for (int i = tid; i < ns * ns; i += blockDim.x) B[i] = Bn[i];
+  __syncthreads();
+  return rmax;
+}
+
+// =============================================================================
 // The sequential sweep of electrons [e0, e1) (one spin block) of every walker: one
 // thread block per walker. Per move (Sec. "Trial Moves", Eq. accept_reject):
 //   x  = column e of the current inverse = Binv0[e] - sum_l z_l U_l   (delayed window)
@@ -366,6 +504,7 @@ struct SweepSmem {
   int* perm;     // [ld_v]
   int* redi;     // [32]
   int* flag;     // [4]
+  float* tile;   // [kTileElems] refinement tiles (single-precision forms only)
 };
 
 template <class TW>
@@ -374,7 +513,9 @@ __host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int
   b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (5 + 2 * k + nwarps) + (size_t)k * k +
                      4 * k + 2 * k * nwarps + 32 * 12 + 4);
   b += sizeof(int) * (k + ld_v + 32 + 4);
-  return (b + 15) & ~size_t(15);
+  b = (b + 15) & ~size_t(15);
+  if (sizeof(TW) == 4) b += sizeof(float) * kTileElems;
+  return b;
 }
 
 template <class TW>
@@ -404,7 +545,9 @@ __device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, in
   s.wrow = ip; ip += k;
   s.perm = ip; ip += ld_v;
   s.redi = ip; ip += 32;
-  s.flag = ip;
+  s.flag = ip; ip += 4;
+  const size_t off = (reinterpret_cast<char*>(ip) - base + 15) & ~size_t(15);
+  s.tile = reinterpret_cast<float*>(base + off);
   return s;
 }
 
@@ -651,10 +794,17 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
           m = 0;
         }
         __syncthreads();
-        reinvert_block<TW>(S, Wk, w, spin, sm.colk, sm.perm, sm.redv, sm.redi);
-        if (tid == 0) {
-          logdet = Wk.logdet[2 * w + spin];
-          sgn = Wk.sgn[2 * w + spin];
+        bool full = true;
+        if constexpr (sizeof(TW) == 4) {
+          // FP64-accurate refinement; ln|det| keeps its FP64 accumulation of the ratios
+          full = !(refine_inverse(S, Wk, w, spin, sm.tile, reinterpret_cast<float*>(sm.red)) <= kRefineMax);
+        }
+        if (full) {
+          reinvert_block<TW>(S, Wk, w, spin, sm.colk, sm.perm, sm.redv, sm.redi);
+          if (tid == 0) {
+            logdet = Wk.logdet[2 * w + spin];
+            sgn = Wk.sgn[2 * w + spin];
+          }
         }
         since = 0;
       }

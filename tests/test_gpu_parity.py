@@ -149,3 +149,27 @@ def test_orbitals_and_inverse_at_setup(precision):
             assert res < (1e-11 if precision == "fp64" else 2e-5), res
     w.close()
     s.close()
+
+
+def test_fp32_refinement_reaches_storage_accuracy():
+    """The single-precision re-inversion (one Newton step with a Dot2 residual) leaves an
+    inverse whose error is set by FP32 storage, not by the condition number or the number
+    of rank-k updates since the last re-inversion."""
+    inputs = build_inputs(small_spec(64, 64, grid=12, n_orb=72), n_walkers=2)
+    errs = {}
+    for period in (0, 16):
+        s = q.system_from_inputs(inputs, precision="fp32", delay_k=4, reinv_period=period)
+        w = q.Walkers(s, inputs["pos"])
+        w.sweep(3)
+        worst = 0.0
+        for wk in range(2):
+            orb = w.orbitals(wk)
+            for spin in range(2):
+                A = orb[64 * spin:64 * (spin + 1), 0, :64]
+                ref = np.linalg.inv(A).T
+                worst = max(worst, np.abs(w.inverse(wk, spin) - ref).max() / np.abs(ref).max())
+        errs[period] = worst
+        w.close()
+        s.close()
+    assert errs[16] < 64 * 2.0 ** -24, errs
+    assert errs[16] <= errs[0], errs
