@@ -216,7 +216,9 @@ typedef enum {
   QMC_K_REINVERT = 4,     /* standalone FP64 re-inversion */
   QMC_K_VGL_CURRENT = 5,  /* orbitals at the current positions (set-up) */
   QMC_K_ACCUMULATE = 6,   /* FP64 reductions over walkers */
-  QMC_NKERNELS = 8
+  QMC_K_FLUSH = 7,        /* batched application of the delayed-update windows */
+  QMC_K_REFINE = 8,       /* batched single-precision re-inversion (Newton step) */
+  QMC_NKERNELS = 10
 } qmc_kernel;
 
 /* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA

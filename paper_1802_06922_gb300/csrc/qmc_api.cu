@@ -96,6 +96,7 @@ struct qmc_walkers_s {
   int forced_sweeps = 0;
   int64_t launches = 0;
   bool energy_valid = false;
+  int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
   bool profiling = false;
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> events;
@@ -317,6 +318,7 @@ qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   { Bracket b(w, st, QMC_K_REINVERT); QMC_CUDA(s->tw->reinvert(s->P, w->W, st)); }
   { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, w->W, st)); }
   QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
+  w->since_moves[0] = w->since_moves[1] = 0;
   w->energy_valid = true;
   return check_err(w, st);
 }
@@ -325,7 +327,8 @@ void free_walkers(qmc_walkers_s* w) {
   WalkParams& W = w->W;
   void* ptrs[] = {W.pos, W.binv, W.vgl, W.logdet, W.sgn, W.wid, W.weight, W.e_loc, W.log_psi,
                   W.n_acc, W.acc_since, W.scratch64, W.err, w->d_P, w->d_prop, w->d_out,
-                  w->d_nacc, w->d_forced};
+                  w->d_nacc, w->d_forced, W.win_phi, W.win_u, W.win_cinv, W.win_row, W.win_m,
+                  W.refine_max};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -388,6 +391,12 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
       {(void**)&w->d_prop, nw * (size_t)w->chunk * sizeof(Prop)},
       {(void**)&w->d_out, 8 * sizeof(double)},
       {(void**)&w->d_nacc, sizeof(long long)},
+      {(void**)&W.win_phi, nw * (size_t)s->d.delay_k * W.ld_v * tw},
+      {(void**)&W.win_u, nw * (size_t)s->d.delay_k * W.ld_v * tw},
+      {(void**)&W.win_cinv, nw * (size_t)s->d.delay_k * s->d.delay_k * tw},
+      {(void**)&W.win_row, nw * (size_t)s->d.delay_k * sizeof(int)},
+      {(void**)&W.win_m, nw * sizeof(int)},
+      {(void**)&W.refine_max, nw * sizeof(float)},
   };
   for (auto& a : allocs) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -402,6 +411,9 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
   cudaMemset(W.vgl, 0, nw * ne * 5 * W.ld_v * tw);
   cudaMemset(W.err, 0, sizeof(int));
   cudaMemset(W.n_acc, 0, nw * sizeof(long long));
+  cudaMemset(W.win_m, 0, nw * sizeof(int));
+  cudaMemset(W.refine_max, 0, nw * sizeof(float));
+  W.kc = s->d.delay_k;
   std::vector<uint32_t> ids(nw);
   std::vector<double> ones(nw, 1.0);
   for (size_t i = 0; i < nw; ++i) ids[i] = (uint32_t)i;
@@ -436,16 +448,43 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
       W.trace = w->trace + w->traced * (size_t)W.n_w * P.n_e * 8;
     if (w->d_forced && sw < w->forced_sweeps)
       W.forced = w->d_forced + (size_t)sw * W.n_w * P.n_e;
+    const int kc = s->d.delay_k, period = s->d.reinv_period;
+    // windows are flushed by a batched kernel every kc moves unless the re-inversion
+    // cadence counts accepted moves (then everything stays inside the sweep kernel)
+    const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
+                     !(period > 0 && s->d.prec == QMC_FP64);
     for (int spin = 0; spin < 2; ++spin) {
       const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
-      for (int e0 = b0; e0 < b1; e0 += w->chunk) {
-        const int e1 = std::min(b1, e0 + w->chunk);
-        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, w->sweep, e0, e1, w->d_prop, st)); }
-        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, w->d_prop, w->d_P, st)); }
-        {
+      for (int pc0 = b0; pc0 < b1; pc0 += w->chunk) {
+        const int pc1 = std::min(b1, pc0 + w->chunk);
+        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, w->sweep, pc0, pc1, w->d_prop, st)); }
+        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, pc0, pc1, w->d_prop, w->d_P, st)); }
+        if (!ext) {
           Bracket b(w, st, QMC_K_SWEEP);
-          QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, s->d.delay_k, w->d_P, w->d_prop,
-                                s->d.reinv_period, s->d.reinv_on_accepted, false, st));
+          QMC_CUDA(s->tw->sweep(P, W, w->sweep, pc0, pc1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
+                                period, s->d.reinv_on_accepted, 0, false, st));
+          continue;
+        }
+        for (int e0 = pc0; e0 < pc1;) {
+          int e1 = std::min(pc1, e0 + kc);
+          if (period > 0) e1 = std::min(e1, e0 + (period - w->since_moves[spin]));
+          {
+            Bracket b(w, st, QMC_K_SWEEP);
+            QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
+                                  0, 0, 1, false, st));
+          }
+          { Bracket b(w, st, QMC_K_FLUSH); QMC_CUDA(s->tw->flush(P, W, spin, st)); }
+          w->launches += 1;   // the window reset that follows each flush
+          if (period > 0) {
+            w->since_moves[spin] += e1 - e0;
+            if (w->since_moves[spin] >= period) {
+              Bracket b(w, st, QMC_K_REFINE);
+              QMC_CUDA(s->tw->refine(P, W, spin, st));
+              w->launches += 2;   // residual, update and commit kernels
+              w->since_moves[spin] = 0;
+            }
+          }
+          e0 = e1;
         }
       }
     }

@@ -132,6 +132,53 @@ __device__ __forceinline__ void jastrow_u(const SysParams& S, int f, T r, T& u, 
   d2u *= scale * scale;
 }
 
+// The three radial functors staged in shared memory: reading knots through a per-thread
+// index from kernel parameters would serialise the constant-bank accesses of a warp.
+// p is zero-padded beyond M so the four-point stencil needs no bounds test.
+template <class T>
+struct JastrowTab {
+  int M[3];
+  T rc[3], scale[3];
+  T p[3][kMaxKnots + 4];
+};
+
+template <class T>
+__device__ __forceinline__ void jastrow_tab_fill(const SysParams& S, JastrowTab<T>& J) {
+  for (int i = threadIdx.x; i < 3 * (kMaxKnots + 4); i += blockDim.x) {
+    const int f = i / (kMaxKnots + 4), m = i % (kMaxKnots + 4);
+    J.p[f][m] = (m <= S.jM[f]) ? Cst<T>::knot(S, f, m) : T(0);
+  }
+  if (threadIdx.x < 3) {
+    const int f = threadIdx.x;
+    J.M[f] = S.jM[f];
+    J.rc[f] = Cst<T>::rc(S, f);
+    J.scale[f] = S.jM[f] ? T(S.jM[f]) / Cst<T>::rc(S, f) : T(0);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void jastrow_eval(const JastrowTab<T>& J, int f, T r, T& u, T& du,
+                                             T& d2u) {
+  u = du = d2u = T(0);
+  if (!(r < J.rc[f])) return;
+  const T scale = J.scale[f];
+  const T s = r * scale;
+  int i = (int)tfloor(s);
+  if (i < 0) i = 0;
+  const T t = s - T(i);
+  T b[4], db[4], d2b[4];
+  bspline_w<T>(t, b, db, d2b);
+  const T* p = J.p[f] + i;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    u += p[q] * b[q];
+    du += p[q] * db[q];
+    d2u += p[q] * d2b[q];
+  }
+  du *= scale;
+  d2u *= scale * scale;
+}
+
 // Yukawa pair potential exp(-kappa r)/r for r < L/2 (stand-in for v_ee, v_eI).
 template <class T>
 __device__ __forceinline__ T yukawa(T r, T kappa, T L) {

@@ -62,6 +62,14 @@ struct WalkParams {
   const uint8_t* forced;  // optional [W][n_e] decisions
   double* scratch64;   // [W][2][ld_v][ld_v] FP64 work matrices for re-inversion
   int* err;            // device error flags
+  // delayed-update window handed from the sweep kernel to the batched flush kernel
+  int kc;              // window capacity (delay rank k)
+  void* win_phi;       // [W][kc][ld_v] new orbital rows of the accepted moves
+  void* win_u;         // [W][kc][ld_v] Binv0 rows of the moved electrons
+  void* win_cinv;      // [W][kc][kc]   C^-1
+  int* win_row;        // [W][kc]       row (electron index within the spin block)
+  int* win_m;          // [W]           fill
+  float* refine_max;   // [W]           max |I - A X| of the last refinement
 };
 
 }  // namespace qmcgb

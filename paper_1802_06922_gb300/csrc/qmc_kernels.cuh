@@ -483,15 +483,16 @@ static __device__ float refine_inverse(const SysParams& S, const WalkParams& Wk,
 template <class TW>
 struct SweepSmem {
   double* posd;  // [3][n_e] exact positions
-  double* outd;  // [16] block sums and per-move scalars
+  double* outd;  // [16] block sums
   double* colk;  // [ld_v]  re-inversion
   double* redv;  // [32]
+  double* propb; // [2][4] double-buffered proposal (x, y, z, u)
   TW* posw;      // [3][n_e] positions in working precision
-  TW* phi;       // [4][ld_v]   proposal value and gradient
-  TW* row0;      // [ld_v]      Binv0[e]
+  TW* phib;      // [2][5 * ld_v] double-buffered proposal orbitals (value, grad, lap)
+  TW* rowb;      // [2][ld_v]     double-buffered Binv0[e]
   TW* wphi;      // [k][ld_v]   window: new orbital rows
   TW* wu;        // [k][ld_v]   window: Binv0 rows of the moved electrons
-  TW* rowbuf;    // [nwarps][ld_v]
+  TW* rowbuf;    // [nwarps][2][ld_v]  flush: double-buffered rows
   TW* cinv;      // [k][k]
   TW* dvec;      // [k]
   TW* zvec;      // [k]
@@ -499,7 +500,7 @@ struct SweepSmem {
   TW* yvec;      // [k]
   TW* dz;        // [nwarps][2k]  flush: per-warp d and z
   TW* red;       // [32][12]
-  TW* rnew;      // [4]
+  TW* sc;        // [8] per-move scalars: r' (3), R
   int* wrow;     // [k]
   int* perm;     // [ld_v]
   int* redi;     // [32]
@@ -509,30 +510,34 @@ struct SweepSmem {
 
 template <class TW>
 __host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int nwarps) {
-  size_t b = sizeof(double) * (3 * (size_t)n_e + 16 + ld_v + 32);
-  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (5 + 2 * k + nwarps) + (size_t)k * k +
-                     4 * k + 2 * k * nwarps + 32 * 12 + 4);
+  size_t b = sizeof(double) * (3 * (size_t)n_e + 16 + ld_v + 32 + 8);
+  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 2 + 2 * k + 2 * nwarps) + (size_t)k * k +
+                     4 * k + 2 * k * nwarps + 32 * 12 + 8);
   b += sizeof(int) * (k + ld_v + 32 + 4);
   b = (b + 15) & ~size_t(15);
   if (sizeof(TW) == 4) b += sizeof(float) * kTileElems;
-  return b;
+  return b + 16;
 }
 
 template <class TW>
 __device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, int k, int nwarps) {
   SweepSmem<TW> s;
   double* d = reinterpret_cast<double*>(base);
+  s.propb = d; d += 8;                 // first: 16-byte aligned for cp.async
   s.posd = d; d += 3 * n_e;
   s.outd = d; d += 16;
   s.colk = d; d += ld_v;
   s.redv = d; d += 32;
-  TW* t = reinterpret_cast<TW*>(d);
+  // working-precision arrays start 16-byte aligned (cp.async targets)
+  char* c = reinterpret_cast<char*>(d);
+  c = base + ((c - base + 15) & ~size_t(15));
+  TW* t = reinterpret_cast<TW*>(c);
+  s.phib = t; t += 10 * ld_v;
+  s.rowb = t; t += 2 * ld_v;
   s.posw = t; t += 3 * n_e;
-  s.phi = t; t += 4 * ld_v;
-  s.row0 = t; t += ld_v;
   s.wphi = t; t += (size_t)k * ld_v;
   s.wu = t; t += (size_t)k * ld_v;
-  s.rowbuf = t; t += (size_t)nwarps * ld_v;
+  s.rowbuf = t; t += (size_t)nwarps * 2 * ld_v;
   s.cinv = t; t += k * k;
   s.dvec = t; t += k;
   s.zvec = t; t += k;
@@ -540,7 +545,7 @@ __device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, in
   s.yvec = t; t += k;
   s.dz = t; t += 2 * k * nwarps;
   s.red = t; t += 32 * 12;
-  s.rnew = t; t += 4;
+  s.sc = t; t += 8;
   int* ip = reinterpret_cast<int*>(t);
   s.wrow = ip; ip += k;
   s.perm = ip; ip += ld_v;
@@ -551,17 +556,49 @@ __device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, in
   return s;
 }
 
+// ---------------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Apply the window (m rows) to every row of Binv0 (B, ns x ns) and empty it:
 // Binv0[n] -= sum_l z_l U_l with z = C^-1 d_n, d_n[l] = Phi_l . Binv0[n] - delta(n, e_l).
 template <class TW>
 __device__ void flush_window(TW* __restrict__ B, int ns, int m, int kc,
                              const SweepSmem<TW>& sm, int ld_v) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  TW* rb = sm.rowbuf + (size_t)warp * ld_v;
+  TW* rbuf = sm.rowbuf + (size_t)warp * 2 * ld_v;     // two row buffers per warp
   TW* dw = sm.dz + (size_t)warp * 2 * kc;
   TW* zw = dw + kc;
-  for (int n = warp; n < ns; n += nw) {
-    for (int j = lane; j < ns; j += 32) rb[j] = B[(size_t)n * ns + j];
+  if (warp < ns) {
+    for (int j = lane; j < ns; j += 32) cp_async_elem(rbuf + j, B + (size_t)warp * ns + j);
+    cp_async_commit();
+  }
+  int it = 0;
+  for (int n = warp; n < ns; n += nw, ++it) {
+    TW* rb = rbuf + (size_t)(it & 1) * ld_v;
+    const int nn = n + nw;
+    if (nn < ns) {          // the next row of this warp is fetched while this one is used
+      TW* nb = rbuf + (size_t)((it + 1) & 1) * ld_v;
+      for (int j = lane; j < ns; j += 32) cp_async_elem(nb + j, B + (size_t)nn * ns + j);
+      cp_async_commit();
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      cp_async_wait_all();
+    }
     __syncwarp();
     for (int l = 0; l < m; ++l) {
       TW s = TW(0);
@@ -587,34 +624,54 @@ __device__ void flush_window(TW* __restrict__ B, int ns, int m, int kc,
   }
 }
 
+template <class TW>
+__device__ __forceinline__ TW texp(TW x);
+template <> __device__ __forceinline__ double texp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float texp<float>(float x) { return expf(x); }
+
 template <class TW, bool kFixedNode>
 __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint32_t t, int e0,
                                               int e1, int kc, const TW* __restrict__ Pv,
-                                              const Prop* __restrict__ prop, int reinv_period,
-                                              int reinv_on_acc) {
+                                              const Prop* __restrict__ prop, int p_e0, int p_n,
+                                              int reinv_period, int reinv_on_acc, int ext_flush) {
   extern __shared__ __align__(16) char smem_s[];
+  __shared__ JastrowTab<TW> jt;
   const int w = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = nt >> 5;
   const int n_e = S.n_e, ld_v = Wk.ld_v;
   SweepSmem<TW> sm = carve<TW>(smem_s, n_e, ld_v, kc, nw);
+  jastrow_tab_fill<TW>(S, jt);
   const int spin = e0 >= S.n_up ? 1 : 0;
   const int first = spin ? S.n_up : 0;
   const int ns = spin ? S.n_dn : S.n_up;
-  const int nmov = e1 - e0;
   const TW Lw = Cst<TW>::L(S);
   const TW* ionw = Cst<TW>::ions(S);
   TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
           (spin ? S.n_up * S.n_up : 0);
   TW* VG = static_cast<TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
   double* gpos = Wk.pos + (size_t)w * 3 * n_e;
+  const int vec = 16 / (int)sizeof(TW);            // TW elements per 16-byte copy
+  // prefetch of move index e (orbital row, proposal, inverse row) into buffer b
+  auto prefetch = [&](int e, int b, bool with_row) {
+    const size_t mvi = (size_t)w * p_n + (e - p_e0);
+    const TW* src = Pv + mvi * 5 * ld_v;
+    TW* dst = sm.phib + (size_t)b * 5 * ld_v;
+    for (int i = tid * vec; i < 5 * ld_v; i += nt * vec) cp_async16(dst + i, src + i);
+    if (tid < 2) cp_async16(sm.propb + 4 * b + 2 * tid, reinterpret_cast<const double*>(prop + mvi) + 2 * tid);
+    if (with_row) {
+      const TW* rs = B + (size_t)(e - first) * ns;
+      TW* rd = sm.rowb + (size_t)b * ld_v;
+      for (int j = tid; j < ns; j += nt) cp_async_elem(rd + j, rs + j);
+    }
+    cp_async_commit();
+  };
   for (int i = tid; i < 3 * n_e; i += nt) {
     const double p = gpos[i];
     sm.posd[i] = p;
     sm.posw[i] = (TW)p;
   }
-  // per-walker scalars live in thread 0
-  double logdet = 0.0, sgn = 1.0;
+  double logdet = 0.0, sgn = 1.0;        // thread 0
   long long nacc = 0;
   if (tid == 0) {
     logdet = Wk.logdet[2 * w + spin];
@@ -622,26 +679,24 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
   }
   int since = Wk.acc_since[2 * w + spin];
   int m = 0;
-  __syncthreads();
+  prefetch(e0, 0, true);
   for (int e = e0; e < e1; ++e) {
     const int row = e - first;
-    const size_t mv = (size_t)w * nmov + (e - e0);
-    const TW* Pe = Pv + mv * 5 * ld_v;
-    if (tid == 0) {
-      const Prop pr = prop[mv];
-      sm.outd[10] = pr.x; sm.outd[11] = pr.y; sm.outd[12] = pr.z; sm.outd[13] = pr.u;
-      sm.rnew[0] = (TW)pr.x; sm.rnew[1] = (TW)pr.y; sm.rnew[2] = (TW)pr.z;
-    }
-    for (int j = tid; j < ns; j += nt) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) sm.phi[c * ld_v + j] = Pe[c * ld_v + j];
-      sm.row0[j] = B[(size_t)row * ns + j];
-    }
+    const int cur = (e - e0) & 1;
+    cp_async_wait_all();
     __syncthreads();
+    if (e + 1 < e1) prefetch(e + 1, cur ^ 1, true);
+    const TW* phi = sm.phib + (size_t)cur * 5 * ld_v;
+    const TW* row0 = sm.rowb + (size_t)cur * ld_v;
+    if (tid == 0) {
+      sm.sc[0] = (TW)sm.propb[4 * cur];
+      sm.sc[1] = (TW)sm.propb[4 * cur + 1];
+      sm.sc[2] = (TW)sm.propb[4 * cur + 2];
+    }
     // d_l = Phi_l . Binv0[e]
     for (int l = warp; l < m; l += nw) {
       TW s = TW(0);
-      for (int j = lane; j < ns; j += 32) s += sm.wphi[(size_t)l * ld_v + j] * sm.row0[j];
+      for (int j = lane; j < ns; j += 32) s += sm.wphi[(size_t)l * ld_v + j] * row0[j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) sm.dvec[l] = s;
@@ -658,20 +713,20 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
     {
       TW a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       for (int j = tid; j < ns; j += nt) {
-        const TW r0 = sm.row0[j];
+        const TW r0 = row0[j];
         TW xv = r0;
         for (int l = 0; l < m; ++l) xv -= sm.zvec[l] * sm.wu[(size_t)l * ld_v + j];
-        a0 += sm.phi[j] * xv;
-        a1 += sm.phi[ld_v + j] * xv;
-        a2 += sm.phi[2 * ld_v + j] * xv;
-        a3 += sm.phi[3 * ld_v + j] * xv;
-        a4 += sm.phi[j] * r0;
+        a0 += phi[j] * xv;
+        a1 += phi[ld_v + j] * xv;
+        a2 += phi[2 * ld_v + j] * xv;
+        a3 += phi[3 * ld_v + j] * xv;
+        a4 += phi[j] * r0;
       }
       acc[0] = a0; acc[1] = a1; acc[2] = a2; acc[3] = a3; acc[4] = a4;
     }
     // Jastrow difference and gradient at r'
     {
-      const TW rn[3] = {sm.rnew[0], sm.rnew[1], sm.rnew[2]};
+      const TW rn[3] = {sm.sc[0], sm.sc[1], sm.sc[2]};
       const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
       TW dj = 0, gx = 0, gy = 0, gz = 0;
       const int ntot = n_e + S.n_ion;
@@ -687,7 +742,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
           q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
           f = 0;
         }
-        if (S.jM[f] == 0) continue;
+        if (jt.M[f] == 0) continue;
         TW dn[3], dq[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -697,8 +752,8 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         const TW rnn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
         const TW roo = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
         TW un, dun, d2n, uo, duo, d2o;
-        jastrow_u<TW>(S, f, rnn, un, dun, d2n);
-        jastrow_u<TW>(S, f, roo, uo, duo, d2o);
+        jastrow_eval<TW>(jt, f, rnn, un, dun, d2n);
+        jastrow_eval<TW>(jt, f, roo, uo, duo, d2o);
         dj += un - uo;
         if (rnn > TW(0)) {
           const TW g = dun / rnn;
@@ -707,51 +762,65 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       }
       acc[5] = dj; acc[6] = gx; acc[7] = gy; acc[8] = gz;
     }
-    block_sum<9, TW>(acc, sm.red, sm.outd);
-    // decision by thread 0 (double), broadcast through shared memory
+    // block sums; warp partials added by thread 0 in working precision
+    warp_sum<9, TW>(acc);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) sm.red[warp * 9 + k] = acc[k];
+    __syncthreads();
     if (tid == 0) {
-      const double R = sm.outd[0], dJ = sm.outd[5], u = sm.outd[13];
-      const bool ok = (R != 0.0) && isfinite(R);
-      const double A = ok ? fmin(1.0, R * R * exp(2.0 * dJ)) : 0.0;
-      bool accept = u < A;
-      if (kFixedNode && R < 0.0) accept = false;
+      TW tot[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        TW v = TW(0);
+        for (int q = 0; q < nw; ++q) v += sm.red[q * 9 + k];
+        tot[k] = v;
+      }
+      const TW R = tot[0], dJ = tot[5];
+      const double u = sm.propb[4 * cur + 3];
+      const bool ok = (R != TW(0)) && isfinite(R);
+      const TW A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
+      bool accept = u < (double)A;
+      if (kFixedNode && R < TW(0)) accept = false;
       if (Wk.forced) accept = Wk.forced[(size_t)w * n_e + e] != 0;
       if (Wk.trace) {
         double* tr = Wk.trace + ((size_t)w * n_e + e) * 8;
-        tr[0] = R;
-        tr[1] = dJ;
-        tr[2] = (ok ? sm.outd[1] / R : 0.0) + sm.outd[6];
-        tr[3] = (ok ? sm.outd[2] / R : 0.0) + sm.outd[7];
-        tr[4] = (ok ? sm.outd[3] / R : 0.0) + sm.outd[8];
+        tr[0] = (double)R;
+        tr[1] = (double)dJ;
+        tr[2] = (ok ? (double)(tot[1] / R) : 0.0) + (double)tot[6];
+        tr[3] = (ok ? (double)(tot[2] / R) : 0.0) + (double)tot[7];
+        tr[4] = (ok ? (double)(tot[3] / R) : 0.0) + (double)tot[8];
         tr[5] = u;
-        tr[6] = A;
+        tr[6] = (double)A;
         tr[7] = accept ? 1.0 : 0.0;
       }
       sm.flag[0] = accept;
       if (accept) {
         ++nacc;
-        logdet += log(fabs(R));
-        if (R < 0) sgn = -sgn;
-        sm.posd[e] = sm.outd[10]; sm.posd[n_e + e] = sm.outd[11]; sm.posd[2 * n_e + e] = sm.outd[12];
-        sm.posw[e] = sm.rnew[0]; sm.posw[n_e + e] = sm.rnew[1]; sm.posw[2 * n_e + e] = sm.rnew[2];
+        logdet += (double)log(fabs(R));
+        if (R < TW(0)) sgn = -sgn;
+        sm.posd[e] = sm.propb[4 * cur];
+        sm.posd[n_e + e] = sm.propb[4 * cur + 1];
+        sm.posd[2 * n_e + e] = sm.propb[4 * cur + 2];
+        sm.posw[e] = sm.sc[0]; sm.posw[n_e + e] = sm.sc[1]; sm.posw[2 * n_e + e] = sm.sc[2];
         sm.wrow[m] = row;
-        sm.rnew[3] = (TW)R;
+        sm.sc[3] = R;
       }
     }
     __syncthreads();
     const bool accept = sm.flag[0] != 0;
+    bool changed = false;     // Binv0 rewritten during this move (prefetched row is stale)
     if (accept) {
       TW* dst = VG + (size_t)e * 5 * ld_v;
+      for (int i = tid; i < 5 * ld_v; i += nt) dst[i] = phi[i];
       for (int j = tid; j < ns; j += nt) {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) dst[c * ld_v + j] = Pe[c * ld_v + j];
-        sm.wphi[(size_t)m * ld_v + j] = sm.phi[j];
-        sm.wu[(size_t)m * ld_v + j] = sm.row0[j];
+        sm.wphi[(size_t)m * ld_v + j] = phi[j];
+        sm.wu[(size_t)m * ld_v + j] = row0[j];
       }
       // border of C: crow[l'] = phi' . U_l'
       for (int l = warp; l < m; l += nw) {
         TW s = TW(0);
-        for (int j = lane; j < ns; j += 32) s += sm.phi[j] * sm.wu[(size_t)l * ld_v + j];
+        for (int j = lane; j < ns; j += 32) s += phi[j] * sm.wu[(size_t)l * ld_v + j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) sm.crow[l] = s;
@@ -764,7 +833,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       }
       __syncthreads();
       // C^-1 of the bordered matrix (Schur complement s = R)
-      const TW sinv = TW(1) / sm.rnew[3];
+      const TW sinv = TW(1) / sm.sc[3];
       for (int i = tid; i < (m + 1) * (m + 1); i += nt) {
         const int a = i / (m + 1), b = i % (m + 1);
         TW v;
@@ -780,10 +849,10 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       }
       ++m;
       __syncthreads();
-      if (m == kc) {
+      if (m == kc && !ext_flush) {
         flush_window<TW>(B, ns, m, kc, sm, ld_v);
         m = 0;
-        __syncthreads();
+        changed = true;
       }
     }
     if (reinv_period > 0) {
@@ -793,6 +862,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
           flush_window<TW>(B, ns, m, kc, sm, ld_v);
           m = 0;
         }
+        cp_async_wait_all();   // the prefetch must land before the tiles reuse nothing it targets
         __syncthreads();
         bool full = true;
         if constexpr (sizeof(TW) == 4) {
@@ -807,11 +877,35 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
           }
         }
         since = 0;
+        changed = true;
       }
     }
-    __syncthreads();
+    if (changed && e + 1 < e1) {
+      // the inverse changed after the next row was prefetched: fetch it again
+      cp_async_wait_all();
+      __syncthreads();
+      const int nrow = e + 1 - first;
+      TW* rd = sm.rowb + (size_t)(cur ^ 1) * ld_v;
+      for (int j = tid; j < ns; j += nt) rd[j] = B[(size_t)nrow * ns + j];
+    }
   }
-  if (m > 0) flush_window<TW>(B, ns, m, kc, sm, ld_v);
+  cp_async_wait_all();
+  __syncthreads();
+  if (ext_flush) {
+    // hand the window to the batched flush kernel
+    TW* gphi = static_cast<TW*>(Wk.win_phi) + (size_t)w * kc * ld_v;
+    TW* gu = static_cast<TW*>(Wk.win_u) + (size_t)w * kc * ld_v;
+    TW* gc = static_cast<TW*>(Wk.win_cinv) + (size_t)w * kc * kc;
+    for (int i = tid; i < m * ld_v; i += nt) {
+      gphi[i] = sm.wphi[i];
+      gu[i] = sm.wu[i];
+    }
+    for (int i = tid; i < kc * kc; i += nt) gc[i] = sm.cinv[i];
+    for (int i = tid; i < m; i += nt) Wk.win_row[(size_t)w * kc + i] = sm.wrow[i];
+    if (tid == 0) Wk.win_m[w] = m;
+  } else if (m > 0) {
+    flush_window<TW>(B, ns, m, kc, sm, ld_v);
+  }
   __syncthreads();
   for (int i = tid; i < 3 * n_e; i += nt) gpos[i] = sm.posd[i];
   if (tid == 0) {
@@ -820,6 +914,245 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
     Wk.n_acc[w] += nacc;
     Wk.acc_since[2 * w + spin] = since;
   }
+}
+
+// =============================================================================
+// Batched flush of the delayed-update windows (Sec. "Multi-Determinant Slater-Jastrow
+// Form", delayed updates): for every walker, with the window's new orbital rows Phi_l,
+// the inverse rows U_l = Binv0[e_l] and C^-1,
+//   D[n][l] = Binv0[n] . Phi_l - delta(n, e_l),   Z[n] = C^-1 D[n],   Binv0[n] -= Z[n] U,
+// i.e. two N_s x N_s x m products. Block (w, tile) owns kFlushRows rows of walker w's
+// inverse. Register blocking: a thread owns one row of D (m outputs) in phase A and
+// 8 threads share one row of the update in phase C.
+// =============================================================================
+constexpr int kFlushRows = 32;
+
+template <class TW>
+__host__ __device__ inline size_t flush_smem_bytes(int ld_v, int kc) {
+  return sizeof(TW) * ((size_t)2 * kc * ld_v + (size_t)kFlushRows * (ld_v + 1) +
+                       (size_t)kc * kc + (size_t)kFlushRows * (2 * kc + 1)) + sizeof(int) * kc + 16;
+}
+
+template <class TW>
+__global__ void __launch_bounds__(256) k_flush(SysParams S, WalkParams Wk, int spin) {
+  extern __shared__ __align__(16) char smem_f[];
+  const int w = blockIdx.x;
+  const int m = Wk.win_m[w];
+  if (m == 0) return;
+  const int kc = Wk.kc, ld_v = Wk.ld_v, ldb = ld_v + 1;
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int r0 = blockIdx.y * kFlushRows;
+  if (r0 >= ns) return;
+  const int nr = min(kFlushRows, ns - r0);
+  TW* phi = reinterpret_cast<TW*>(smem_f);
+  TW* U = phi + (size_t)kc * ld_v;
+  TW* Bt = U + (size_t)kc * ld_v;
+  TW* ci = Bt + (size_t)kFlushRows * ldb;
+  TW* D = ci + kc * kc;
+  TW* Z = D + kFlushRows * kc;                 // row stride kc + 1 (bank spread)
+  int* wrow = reinterpret_cast<int*>(Z + kFlushRows * (kc + 1));
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const TW* gphi = static_cast<const TW*>(Wk.win_phi) + (size_t)w * kc * ld_v;
+  const TW* gu = static_cast<const TW*>(Wk.win_u) + (size_t)w * kc * ld_v;
+  const TW* gc = static_cast<const TW*>(Wk.win_cinv) + (size_t)w * kc * kc;
+  TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+          (spin ? S.n_up * S.n_up : 0);
+  for (int i = tid; i < m * ld_v; i += nt) { phi[i] = gphi[i]; U[i] = gu[i]; }
+  for (int i = tid; i < kc * kc; i += nt) ci[i] = gc[i];
+  for (int i = tid; i < m; i += nt) wrow[i] = Wk.win_row[(size_t)w * kc + i];
+  for (int i = tid; i < nr * ns; i += nt) {
+    const int r = i / ns, j = i % ns;
+    Bt[r * ldb + j] = B[(size_t)(r0 + r) * ns + j];
+  }
+  __syncthreads();
+  // phase A: D[r][l] = Bt[r] . Phi_l - delta
+  {
+    const int r = tid & 31, lg = tid >> 5, ng = nt >> 5;
+    if (r < nr) {
+      TW acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = TW(0);
+      const TW* br = Bt + r * ldb;
+      for (int j = 0; j < ns; ++j) {
+        const TW b = br[j];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int l = lg + q * ng;
+          if (l < m) acc[q] += b * phi[(size_t)l * ld_v + j];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int l = lg + q * ng;
+        if (l < m) D[r * kc + l] = acc[q] - (wrow[l] == r0 + r ? TW(1) : TW(0));
+      }
+    }
+  }
+  __syncthreads();
+  // phase B: Z[r] = C^-1 D[r]
+  for (int i = tid; i < nr * m; i += nt) {
+    const int r = i / m, l = i % m;
+    TW z = TW(0);
+    for (int lp = 0; lp < m; ++lp) z += ci[l * kc + lp] * D[r * kc + lp];
+    Z[r * (kc + 1) + l] = z;
+  }
+  __syncthreads();
+  // phase C: Binv0[r0 + r] -= Z[r] U
+  {
+    const int r = tid >> 3, c0 = tid & 7;
+    if (r < nr) {
+      const TW* zr = Z + r * (kc + 1);
+      for (int j = c0; j < ns; j += 8) {
+        TW v = Bt[r * ldb + j];
+        for (int l = 0; l < m; ++l) v -= zr[l] * U[(size_t)l * ld_v + j];
+        B[(size_t)(r0 + r) * ns + j] = v;
+      }
+    }
+  }
+}
+
+// Empty every window after a flush round.
+static __global__ void k_window_reset(WalkParams Wk) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < Wk.n_w) Wk.win_m[w] = 0;
+}
+
+// =============================================================================
+// Batched single-precision re-inversion (the refinement of refine_inverse as separate
+// kernels over all walkers): residual tiles with Dot2, then X <- X + X R.
+// =============================================================================
+template <class TW>
+__global__ void __launch_bounds__(256) k_refine_residual(SysParams S, WalkParams Wk, int spin) {
+  __shared__ float As[32 * 64], Bs[32 * 64];
+  const int w = blockIdx.x;
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int first = spin ? S.n_up : 0;
+  const int nt64 = (ns + 63) / 64;
+  const int te = (blockIdx.y / nt64) * 64, tf = (blockIdx.y % nt64) * 64;
+  const int ld5 = 5 * Wk.ld_v;
+  const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
+  const float* B = static_cast<const float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+                   (spin ? S.n_up * S.n_up : 0);
+  float* Rg = reinterpret_cast<float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float P[4][4], E[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) P[i][j] = E[i][j] = 0.f;
+  for (int k0 = 0; k0 < ns; k0 += 32) {
+    __syncthreads();
+    for (int i = tid; i < 64 * 32; i += blockDim.x) {
+      const int r = i & 63, kk = i >> 6, j = k0 + kk;
+      const int e = te + r, f = tf + r;
+      As[kk * 64 + r] = (e < ns && j < ns) ? VG[(size_t)e * ld5 + j] : 0.f;
+      Bs[kk * 64 + r] = (f < ns && j < ns) ? B[(size_t)f * ns + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[kk * 64 + ty + 16 * i];
+        b[i] = Bs[kk * 64 + tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dot2_step(a[i], b[j], P[i][j], E[i][j]);
+    }
+  }
+  float rmax = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = te + ty + 16 * i, f = tf + tx + 16 * j;
+      if (e < ns && f < ns) {
+        const float r = __fsub_rn(__fsub_rn(e == f ? 1.f : 0.f, P[i][j]), E[i][j]);
+        Rg[(size_t)e * ns + f] = r;
+        rmax = fmaxf(rmax, isfinite(r) ? fabsf(r) : INFINITY);
+      }
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(Wk.refine_max + w), __float_as_int(rmax));
+}
+
+// X <- X + X R: Bn[e][j] = Binv[e][j] + sum_f R[f][e] Binv[f][j] into the second half of
+// the walker's work area; walkers whose residual exceeded kRefineMax are skipped (they
+// take the FP64 re-inversion).
+template <class TW>
+__global__ void __launch_bounds__(256) k_refine_update(SysParams S, WalkParams Wk, int spin) {
+  __shared__ float As[32 * 64], Bs[32 * 64];
+  const int w = blockIdx.x;
+  if (!(Wk.refine_max[w] <= kRefineMax)) return;
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int nt64 = (ns + 63) / 64;
+  const int te = (blockIdx.y / nt64) * 64, tj = (blockIdx.y % nt64) * 64;
+  const float* B = static_cast<const float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+                   (spin ? S.n_up * S.n_up : 0);
+  const float* Rg = reinterpret_cast<const float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
+  float* Bn = const_cast<float*>(Rg) + (size_t)ns * ns;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int f0 = 0; f0 < ns; f0 += 32) {
+    __syncthreads();
+    for (int i = tid; i < 64 * 32; i += blockDim.x) {
+      const int c = i & 63, kk = i >> 6, f = f0 + kk;
+      As[kk * 64 + c] = (f < ns && te + c < ns) ? Rg[(size_t)f * ns + te + c] : 0.f;
+      Bs[kk * 64 + c] = (f < ns && tj + c < ns) ? B[(size_t)f * ns + tj + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[kk * 64 + ty + 16 * i];
+        b[i] = Bs[kk * 64 + tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = te + ty + 16 * i, c = tj + tx + 16 * j;
+      if (e < ns && c < ns) Bn[(size_t)e * ns + c] = B[(size_t)e * ns + c] + acc[i][j];
+    }
+}
+
+// Copies the refined inverse back (walkers that refined), and re-inverts in FP64 the
+// walkers whose residual was too large.
+template <class TW>
+__global__ void __launch_bounds__(256) k_refine_commit(SysParams S, WalkParams Wk, int spin) {
+  extern __shared__ __align__(16) char smem_c[];
+  const int w = blockIdx.x;
+  const int ns = spin ? S.n_dn : S.n_up;
+  float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
+             (spin ? S.n_up * S.n_up : 0);
+  if (Wk.refine_max[w] <= kRefineMax) {
+    const float* Bn = reinterpret_cast<const float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v) +
+                      (size_t)ns * ns;
+    for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) B[i] = Bn[i];
+  } else {
+    double* colk = reinterpret_cast<double*>(smem_c);
+    double* redv = colk + Wk.ld_v;
+    int* perm = reinterpret_cast<int*>(redv + 32);
+    int* redi = perm + Wk.ld_v;
+    reinvert_block<TW>(S, Wk, w, spin, colk, perm, redv, redi);
+  }
+  if (threadIdx.x == 0) Wk.refine_max[w] = 0.f;
 }
 
 // =============================================================================
@@ -832,6 +1165,8 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
 template <class TW>
 __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk) {
   extern __shared__ __align__(16) char smem_e[];
+  __shared__ JastrowTab<TW> jt;
+  jastrow_tab_fill<TW>(S, jt);
   TW* posw = reinterpret_cast<TW*>(smem_e);                  // [3][n_e]
   const int w = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -887,9 +1222,9 @@ __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk
           const TW y = yukawa<TW>(r, kap, Lw);
           pv += (j < n_e) ? y : -Zw * y;
         }
-        if (S.jM[f] == 0) continue;
+        if (jt.M[f] == 0) continue;
         TW u, du, d2u;
-        jastrow_u<TW>(S, f, r, u, du, d2u);
+        jastrow_eval<TW>(jt, f, r, u, du, d2u);
         if (once) jj += u;
         if (r > TW(0)) {
           const TW g = du / r;

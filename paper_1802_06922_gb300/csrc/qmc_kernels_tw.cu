@@ -18,16 +18,51 @@ size_t sweep_smem(int n_e, int ld_v, int k) {
 
 template <class TW>
 cudaError_t sweep(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1, int k,
-                  const void* P, const void* prop, int reinv_period, int reinv_on_acc,
-                  bool fixed_node, cudaStream_t st) {
+                  const void* P, const void* prop, int p_e0, int p_n, int reinv_period,
+                  int reinv_on_acc, int ext_flush, bool fixed_node, cudaStream_t st) {
   const size_t smem = sweep_smem<TW>(S.n_e, W.ld_v, k);
   auto kern = fixed_node ? k_sweep<TW, true> : k_sweep<TW, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<W.n_w, kThreads, smem, st>>>(S, W, t, e0, e1, k, static_cast<const TW*>(P),
-                                      static_cast<const Prop*>(prop), reinv_period,
-                                      reinv_on_acc);
+                                      static_cast<const Prop*>(prop), p_e0, p_n, reinv_period,
+                                      reinv_on_acc, ext_flush);
   return cudaGetLastError();
+}
+
+template <class TW>
+cudaError_t flush(const SysParams& S, const WalkParams& W, int spin, cudaStream_t st) {
+  const int ns = spin ? S.n_dn : S.n_up;
+  const size_t smem = flush_smem_bytes<TW>(W.ld_v, W.kc);
+  cudaError_t e = cudaFuncSetAttribute(k_flush<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(W.n_w, (ns + kFlushRows - 1) / kFlushRows);
+  k_flush<TW><<<grid, kThreads, smem, st>>>(S, W, spin);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_window_reset<<<(W.n_w + 255) / 256, 256, 0, st>>>(W);
+  return cudaGetLastError();
+}
+
+template <class TW>
+cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, cudaStream_t st) {
+  const int ns = spin ? S.n_dn : S.n_up;
+  if (ns == 0) return cudaSuccess;
+  if constexpr (sizeof(TW) == 4) {
+    const int nt64 = (ns + 63) / 64;
+    const dim3 grid(W.n_w, nt64 * nt64);
+    k_refine_residual<TW><<<grid, kThreads, 0, st>>>(S, W, spin);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_refine_update<TW><<<grid, kThreads, 0, st>>>(S, W, spin);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_refine_commit<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
+    return cudaGetLastError();
+  } else {
+    // double precision needs no refinement: FP64 Gauss-Jordan of that spin block
+    return cudaErrorNotSupported;
+  }
 }
 
 template <class TW>
@@ -52,12 +87,13 @@ cudaError_t invert_batch(const void* A, void* Binv, double* logdet, double* sign
 
 const TwLaunch& tw_launch_f64() {
   static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
-                          sweep_smem<double>, invert_batch<double>};
+                          sweep_smem<double>, invert_batch<double>, flush<double>,
+                          refine<double>};
   return L;
 }
 const TwLaunch& tw_launch_f32() {
   static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
-                          sweep_smem<float>, invert_batch<float>};
+                          sweep_smem<float>, invert_batch<float>, flush<float>, refine<float>};
   return L;
 }
 

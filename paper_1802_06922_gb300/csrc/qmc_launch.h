@@ -11,12 +11,14 @@ struct TwLaunch {
   size_t tw_size;
   cudaError_t (*reinvert)(const SysParams&, const WalkParams&, cudaStream_t);
   cudaError_t (*sweep)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1, int k,
-                       const void* P, const void* prop, int reinv_period, int reinv_on_acc,
-                       bool fixed_node, cudaStream_t);
+                       const void* P, const void* prop, int p_e0, int p_n, int reinv_period,
+                       int reinv_on_acc, int ext_flush, bool fixed_node, cudaStream_t);
   cudaError_t (*local_energy)(const SysParams&, const WalkParams&, cudaStream_t);
   size_t (*sweep_smem)(int n_e, int ld_v, int k);
   cudaError_t (*invert_batch)(const void* A, void* Binv, double* logdet, double* sign, int n,
                               int batch, double* work, cudaStream_t);
+  cudaError_t (*flush)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
+  cudaError_t (*refine)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
 };
 const TwLaunch& tw_launch_f64();
 const TwLaunch& tw_launch_f32();

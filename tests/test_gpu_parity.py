@@ -60,7 +60,7 @@ def test_plane_wave_fp64_parity_and_zero_variance():
     assert np.all(np.abs(e_gpu - e_ref) / e_ref < ((2 * np.pi / 10) * (10 / 32)) ** 2)
 
 
-@pytest.mark.parametrize("delay_k", [1, 3])
+@pytest.mark.parametrize("delay_k", [1, 3, 8])
 def test_slater_jastrow_fp64_parity_ragged(delay_k):
     # 70 up / 66 down electrons: two 64-orbital chunks per FP64 warp with a ragged tail,
     # a delay window that does not divide the block
@@ -73,15 +73,17 @@ def test_slater_jastrow_fp64_parity_ragged(delay_k):
     assert np.all(rel_err(en[:, 1, :].T, ref_en[..., 2], 1.0) < 1e-10)
 
 
-@pytest.mark.parametrize("precision,delay_k", [("fp32", 1), ("fp32", 4), ("bf16", 4)])
-def test_mixed_precision_lockstep(precision, delay_k):
+@pytest.mark.parametrize("precision,delay_k,on_acc", [("fp32", 1, True), ("fp32", 4, True),
+                                                     ("bf16", 4, True), ("fp32", 8, False),
+                                                     ("bf16", 16, False)])
+def test_mixed_precision_lockstep(precision, delay_k, on_acc):
     inputs = build_inputs(small_spec(40, 40, grid=16), n_walkers=3)
     ids = np.arange(3)
     coef = bf16_round(inputs["coef"]) if precision == "bf16" else None
     _, ref, ref_en = oracle_vmc(inputs, ids, 2, coef=coef)
     forced = ref[..., 7]
     tr, en, _ = _gpu_run(inputs, ids, 2, precision=precision, delay_k=delay_k,
-                         reinv_period=16, reinv_on_accepted=True, forced=forced, coef=coef)
+                         reinv_period=16, reinv_on_accepted=on_acc, forced=forced, coef=coef)
     # ratio gate: 1e-4 relative (floor 1e-3) at the 99.9th percentile
     r = rel_err(tr[..., 0], ref[..., 0], 1e-3)
     assert np.quantile(r, 0.999) < 1e-4, (r.max(), np.quantile(r, 0.999))
