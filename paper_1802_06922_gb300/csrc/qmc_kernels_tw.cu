@@ -1,6 +1,7 @@
 // Instantiations of the kernels that depend on the working precision.
 #include "qmc_kernels.cuh"
 #include "qmc_launch.h"
+#include "qmc_tc_kernels.cuh"
 
 namespace qmcgb {
 namespace {
@@ -33,6 +34,18 @@ cudaError_t sweep(const SysParams& S, const WalkParams& W, uint32_t t, int e0, i
 template <class TW>
 cudaError_t flush(const SysParams& S, const WalkParams& W, int spin, cudaStream_t st) {
   const int ns = spin ? S.n_dn : S.n_up;
+  if constexpr (sizeof(TW) == 4) {
+    // single precision: both products of the flush on the tensor cores (3xTF32)
+    const size_t smem = flush_tc_smem_bytes(W.kc);
+    cudaError_t e = cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(W.n_w, (ns + kTcRows - 1) / kTcRows);
+    k_flush_tc<<<grid, kThreads, smem, st>>>(S, W, spin);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_window_reset<<<(W.n_w + 255) / 256, 256, 0, st>>>(W);
+    return cudaGetLastError();
+  }
   const size_t smem = flush_smem_bytes<TW>(W.ld_v, W.kc);
   cudaError_t e = cudaFuncSetAttribute(k_flush<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
