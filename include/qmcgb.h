@@ -50,6 +50,7 @@ extern "C" {
 
 typedef struct qmc_system_s* qmc_system_t;
 typedef struct qmc_walkers_s* qmc_walkers_t;
+typedef struct qmc_dmc_s* qmc_dmc_t;
 
 typedef enum {
   QMC_OK = 0,
@@ -206,6 +207,36 @@ qmc_status qmc_slater_invert(qmc_precision prec, const void* A, void* Binv, doub
 qmc_status qmc_slater_invert_noalloc(qmc_precision prec, const void* A, void* Binv,
                                      double* logdet, double* sign, int n, int batch,
                                      void* stream);
+
+/* Branching DMC over one or more systems (Sec. "Diffusion Monte Carlo"), each advancing
+ * on its own stream so that systems of uneven size share the GPU. Every system must use
+ * QMC_MOVE_DRIFT (tau = step). One step of a system: a sweep of drift-diffusion moves with
+ * the fixed-node rule (a move that changes the sign of Psi is rejected), the local energy,
+ * the weights w = exp(-tau/2 (E_L(old) + E_L(new) - 2 E_T)) (Eq. pmc:g_growth and
+ * Eq. pmc:walker_weight), M = floor(w + xi) copies of each walker (xi from Philox block
+ * (step, 0xB, walker ID, 2)), children renormalised to weight 1 and appended in parent
+ * order (the first copy keeps the parent's ID, further copies take new consecutive IDs),
+ * the population capped at capacity_factor times the initial count, and the trial energy
+ * fed back as E_T <- E_w - ln(N / N_0) / (10 tau) with E_w the weighted mean E_L.
+ *   qmc_dmc_create: n_walkers[i] initial walkers of systems[i] at host positions[i]
+ *                   ([n][n_e][3]), initial trial energies e_trial[i]; walker IDs 0..n-1.
+ *                   The driver owns its walker storage; the systems must outlive it.
+ *   qmc_dmc_step:   n_steps steps of every system, ordered after prior work on `stream`
+ *                   and before later work on it. Asynchronous; populations stay on the GPU.
+ *   qmc_dmc_read:   out[8] = population, sum of weights, sum of weight * E_L, weighted mean
+ *                   E_L, E_T used, E_T for the next step, next free walker ID, population
+ *                   before the last branching (host or device). Synchronous.
+ *   qmc_dmc_walkers: positions [n][n_e][3], IDs [n] and E_L [n] of the current population
+ *                   (any may be NULL); *n_out = population; QMC_EINVAL if n > max_walkers. */
+qmc_status qmc_dmc_create(qmc_system_t const* systems, const int* n_walkers,
+                          const double* const* positions, const double* e_trial, int n_systems,
+                          int capacity_factor, qmc_dmc_t* out);
+qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream);
+qmc_status qmc_dmc_read(qmc_dmc_t d, int system, double* out);
+qmc_status qmc_dmc_walkers(qmc_dmc_t d, int system, int max_walkers, double* pos, uint32_t* ids,
+                           double* e_local, int* n_out);
+int64_t qmc_dmc_launch_count(qmc_dmc_t d);
+void qmc_dmc_destroy(qmc_dmc_t d);
 
 /* Kernel classes reported by qmc_profile_read. */
 typedef enum {

@@ -5,6 +5,8 @@ B-spline Jastrow factors) behind the C ABI of ``include/qmcgb.h``.
 The Python layer is a thin ctypes binding (``qmcgb``); the work runs in the CUDA
 kernels of ``libqmcgb.so`` built from ``csrc/`` for sm_103a.
 """
-from .qmcgb import (QMCError, System, Walkers, load, system_from_inputs)  # noqa: F401
+from .qmcgb import (DMC, QMCError, System, Walkers, load, slater_invert,  # noqa: F401
+                    slater_invert_noalloc, system_from_inputs)
 
-__all__ = ["QMCError", "System", "Walkers", "load", "system_from_inputs"]
+__all__ = ["DMC", "QMCError", "System", "Walkers", "load", "slater_invert",
+           "slater_invert_noalloc", "system_from_inputs"]

@@ -354,24 +354,23 @@ qmc_status upload_positions(qmc_walkers_s* w, const double* pos, bool pos_on_dev
 }
 }  // namespace
 
-extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const double* pos,
-                                         qmc_walkers_t* out) {
-  if (!s || !out || !pos) return fail(QMC_EINVAL, "qmc_walkers_create: NULL argument");
-  *out = nullptr;
-  if (!s->has_spline) return fail(QMC_EINVAL, "qmc_walkers_create: set the spline table first");
-  if (n_walkers < 1 || n_walkers > (1 << 20)) return fail(QMC_EINVAL, "n_walkers must be in [1, 2^20]");
+namespace {
+// Allocates the device arrays of a walker set with `cap` slots (all zeroed where it
+// matters); `proposals` adds the buffers of the batched Metropolis proposals.
+qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s** out) {
   const SysParams& P = s->P;
   qmc_walkers_s* w = new qmc_walkers_s;
   w->sys = s;
   WalkParams& W = w->W;
-  W.n_w = n_walkers;
+  W.n_w = cap;
   const int ns_max = std::max(P.n_up, P.n_dn);
   W.ld_v = round_up(std::max(ns_max, 1), 8);
   const size_t tw = s->tw->tw_size;
-  const size_t nw = n_walkers, ne = P.n_e;
+  const size_t nw = cap, ne = P.n_e;
   w->chunk = ns_max;
   // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
   while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
+  const size_t np = proposals ? nw * (size_t)w->chunk : 1;
   const size_t nbinv = (size_t)P.n_up * P.n_up + (size_t)P.n_dn * P.n_dn;
   struct A { void** p; size_t bytes; } allocs[] = {
       {(void**)&W.pos, nw * 3 * ne * sizeof(double)},
@@ -387,8 +386,8 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
       {(void**)&W.acc_since, nw * 2 * sizeof(int)},
       {(void**)&W.scratch64, 2 * nw * (size_t)W.ld_v * W.ld_v * sizeof(double)},
       {(void**)&W.err, sizeof(int)},
-      {(void**)&w->d_P, nw * (size_t)w->chunk * 5 * W.ld_v * tw},
-      {(void**)&w->d_prop, nw * (size_t)w->chunk * sizeof(Prop)},
+      {(void**)&w->d_P, np * 5 * W.ld_v * tw},
+      {(void**)&w->d_prop, np * sizeof(Prop)},
       {(void**)&w->d_out, 8 * sizeof(double)},
       {(void**)&w->d_nacc, sizeof(long long)},
       {(void**)&W.win_phi, nw * (size_t)s->d.delay_k * W.ld_v * tw},
@@ -403,7 +402,7 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
     if (e != cudaSuccess) {
       free_walkers(w);
       delete w;
-      return fail(QMC_ENOMEM, "qmc_walkers_create: cannot allocate %zu bytes: %s", a.bytes,
+      return fail(QMC_ENOMEM, "cannot allocate %zu bytes of walker state: %s", a.bytes,
                   cudaGetErrorString(e));
     }
   }
@@ -411,16 +410,40 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
   cudaMemset(W.vgl, 0, nw * ne * 5 * W.ld_v * tw);
   cudaMemset(W.err, 0, sizeof(int));
   cudaMemset(W.n_acc, 0, nw * sizeof(long long));
+  cudaMemset(W.acc_since, 0, nw * 2 * sizeof(int));
   cudaMemset(W.win_m, 0, nw * sizeof(int));
   cudaMemset(W.refine_max, 0, nw * sizeof(float));
   W.kc = s->d.delay_k;
-  std::vector<uint32_t> ids(nw);
-  std::vector<double> ones(nw, 1.0);
-  for (size_t i = 0; i < nw; ++i) ids[i] = (uint32_t)i;
-  cudaMemcpy(W.wid, ids.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice);
-  cudaMemcpy(W.weight, ones.data(), nw * sizeof(double), cudaMemcpyHostToDevice);
+  *out = w;
+  return QMC_OK;
+}
+
+// IDs 0..n-1, weights 1, positions from the caller, orbitals, FP64 inverses and E_L.
+qmc_status init_walkers(qmc_walkers_s* w, int n, const double* pos) {
+  const int saved = w->W.n_w;
+  w->W.n_w = n;
+  std::vector<uint32_t> ids(n);
+  std::vector<double> ones(n, 1.0);
+  for (int i = 0; i < n; ++i) ids[i] = (uint32_t)i;
+  QMC_CUDA(cudaMemcpy(w->W.wid, ids.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  QMC_CUDA(cudaMemcpy(w->W.weight, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice));
   qmc_status st = upload_positions(w, pos, is_device_ptr(pos));
   if (st == QMC_OK) st = setup_state(w, 0);
+  if (saved != n) w->W.n_w = saved;
+  return st;
+}
+}  // namespace
+
+extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const double* pos,
+                                         qmc_walkers_t* out) {
+  if (!s || !out || !pos) return fail(QMC_EINVAL, "qmc_walkers_create: NULL argument");
+  *out = nullptr;
+  if (!s->has_spline) return fail(QMC_EINVAL, "qmc_walkers_create: set the spline table first");
+  if (n_walkers < 1 || n_walkers > (1 << 20)) return fail(QMC_EINVAL, "n_walkers must be in [1, 2^20]");
+  qmc_walkers_s* w = nullptr;
+  qmc_status st = alloc_walkers(s, n_walkers, s->d.move == QMC_MOVE_METROPOLIS, &w);
+  if (st != QMC_OK) return st;
+  st = init_walkers(w, n_walkers, pos);
   if (st != QMC_OK) {
     const std::string msg = g_err;
     free_walkers(w);
@@ -432,12 +455,70 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
   return QMC_OK;
 }
 
+namespace {
+// The sweeps of one walker set: Metropolis moves from batched proposals, or drift moves
+// with in-kernel orbital evaluation; windows flushed in batches every k moves unless the
+// re-inversion cadence counts accepted moves.
+qmc_status sweep_once(qmc_walkers_s* w, const WalkParams& W, bool fixed_node, cudaStream_t st) {
+  qmc_system_s* s = w->sys;
+  const SysParams& P = s->P;
+  const int kc = s->d.delay_k, period = s->d.reinv_period;
+  const bool drift = s->d.move == QMC_MOVE_DRIFT;
+  const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
+                   !(period > 0 && s->d.prec == QMC_FP64);
+  for (int spin = 0; spin < 2; ++spin) {
+    const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
+    const int pchunk = drift ? std::max(b1 - b0, 1) : w->chunk;
+    for (int pc0 = b0; pc0 < b1; pc0 += pchunk) {
+      const int pc1 = std::min(b1, pc0 + pchunk);
+      if (!drift) {
+        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, w->sweep, pc0, pc1, w->d_prop, st)); }
+        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, pc0, pc1, w->d_prop, w->d_P, st)); }
+      }
+      if (!ext) {
+        Bracket b(w, st, QMC_K_SWEEP);
+        if (drift)
+          QMC_CUDA(s->tt->sweep_drift(P, W, w->sweep, pc0, pc1, kc, period, s->d.reinv_on_accepted,
+                                      0, fixed_node, st));
+        else
+          QMC_CUDA(s->tw->sweep(P, W, w->sweep, pc0, pc1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
+                                period, s->d.reinv_on_accepted, 0, fixed_node, st));
+        continue;
+      }
+      for (int e0 = pc0; e0 < pc1;) {
+        int e1 = std::min(pc1, e0 + kc);
+        if (period > 0) e1 = std::min(e1, e0 + (period - w->since_moves[spin]));
+        {
+          Bracket b(w, st, QMC_K_SWEEP);
+          if (drift)
+            QMC_CUDA(s->tt->sweep_drift(P, W, w->sweep, e0, e1, kc, 0, 0, 1, fixed_node, st));
+          else
+            QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
+                                  0, 0, 1, fixed_node, st));
+        }
+        { Bracket b(w, st, QMC_K_FLUSH); QMC_CUDA(s->tw->flush(P, W, spin, st)); }
+        w->launches += 1;   // the window reset that follows each flush
+        if (period > 0) {
+          w->since_moves[spin] += e1 - e0;
+          if (w->since_moves[spin] >= period) {
+            Bracket b(w, st, QMC_K_REFINE);
+            QMC_CUDA(s->tw->refine(P, W, spin, st));
+            w->launches += 2;   // residual, update and commit kernels
+            w->since_moves[spin] = 0;
+          }
+        }
+        e0 = e1;
+      }
+    }
+  }
+  return QMC_OK;
+}
+}  // namespace
+
 extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
   if (!w) return fail(QMC_EINVAL, "qmc_sweep: NULL walkers");
   if (n_sweeps < 0) return fail(QMC_EINVAL, "qmc_sweep: n_sweeps < 0");
   qmc_system_s* s = w->sys;
-  if (s->d.move != QMC_MOVE_METROPOLIS)
-    return fail(QMC_EINVAL, "qmc_sweep: drift moves are taken by the DMC step");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const SysParams& P = s->P;
   for (int sw = 0; sw < n_sweeps; ++sw) {
@@ -448,46 +529,8 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
       W.trace = w->trace + w->traced * (size_t)W.n_w * P.n_e * 8;
     if (w->d_forced && sw < w->forced_sweeps)
       W.forced = w->d_forced + (size_t)sw * W.n_w * P.n_e;
-    const int kc = s->d.delay_k, period = s->d.reinv_period;
-    // windows are flushed by a batched kernel every kc moves unless the re-inversion
-    // cadence counts accepted moves (then everything stays inside the sweep kernel)
-    const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
-                     !(period > 0 && s->d.prec == QMC_FP64);
-    for (int spin = 0; spin < 2; ++spin) {
-      const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
-      for (int pc0 = b0; pc0 < b1; pc0 += w->chunk) {
-        const int pc1 = std::min(b1, pc0 + w->chunk);
-        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, w->sweep, pc0, pc1, w->d_prop, st)); }
-        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, pc0, pc1, w->d_prop, w->d_P, st)); }
-        if (!ext) {
-          Bracket b(w, st, QMC_K_SWEEP);
-          QMC_CUDA(s->tw->sweep(P, W, w->sweep, pc0, pc1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
-                                period, s->d.reinv_on_accepted, 0, false, st));
-          continue;
-        }
-        for (int e0 = pc0; e0 < pc1;) {
-          int e1 = std::min(pc1, e0 + kc);
-          if (period > 0) e1 = std::min(e1, e0 + (period - w->since_moves[spin]));
-          {
-            Bracket b(w, st, QMC_K_SWEEP);
-            QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
-                                  0, 0, 1, false, st));
-          }
-          { Bracket b(w, st, QMC_K_FLUSH); QMC_CUDA(s->tw->flush(P, W, spin, st)); }
-          w->launches += 1;   // the window reset that follows each flush
-          if (period > 0) {
-            w->since_moves[spin] += e1 - e0;
-            if (w->since_moves[spin] >= period) {
-              Bracket b(w, st, QMC_K_REFINE);
-              QMC_CUDA(s->tw->refine(P, W, spin, st));
-              w->launches += 2;   // residual, update and commit kernels
-              w->since_moves[spin] = 0;
-            }
-          }
-          e0 = e1;
-        }
-      }
-    }
+    qmc_status r = sweep_once(w, W, false, st);
+    if (r != QMC_OK) return r;
     { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(P, W, st)); }
     if (W.trace) ++w->traced;
     ++w->sweep;
@@ -742,4 +785,196 @@ extern "C" qmc_status qmc_slater_invert(qmc_precision prec, const void* A, void*
   QMC_CUDA(e);
   QMC_CUDA(f);
   return QMC_OK;
+}
+
+// ------------------------------------------------------------------------ DMC
+struct qmc_dmc_s {
+  struct Sys {
+    qmc_system_s* sys = nullptr;
+    qmc_walkers_s* w[2] = {nullptr, nullptr};   // two slot buffers; walkers move on branching
+    DmcParams D{};
+    double* e_old[2] = {nullptr, nullptr};
+    int parity = 0;
+    cudaStream_t st = nullptr;
+  };
+  std::vector<Sys> sys;
+  uint32_t step = 0;
+  cudaEvent_t ev_in = nullptr;
+  std::vector<cudaEvent_t> ev_out;
+};
+
+namespace {
+void free_dmc(qmc_dmc_s* d) {
+  for (auto& y : d->sys) {
+    for (auto* w : y.w)
+      if (w) { free_walkers(w); delete w; }
+    cudaFree(y.e_old[0]);
+    cudaFree(y.e_old[1]);
+    cudaFree(y.D.src_of);
+    cudaFree(y.D.wid_next);
+    cudaFree(y.D.n_live);
+    cudaFree(y.D.next_id);
+    cudaFree(y.D.e_trial);
+    cudaFree(y.D.stats);
+    if (y.st) cudaStreamDestroy(y.st);
+  }
+  if (d->ev_in) cudaEventDestroy(d->ev_in);
+  for (auto e : d->ev_out) cudaEventDestroy(e);
+  delete d;
+}
+}  // namespace
+
+extern "C" qmc_status qmc_dmc_create(qmc_system_t const* systems, const int* n_walkers,
+                                     const double* const* positions, const double* e_trial,
+                                     int n_systems, int capacity_factor, qmc_dmc_t* out) {
+  if (!systems || !n_walkers || !positions || !e_trial || !out)
+    return fail(QMC_EINVAL, "qmc_dmc_create: NULL argument");
+  *out = nullptr;
+  if (n_systems < 1 || n_systems > 64) return fail(QMC_EINVAL, "qmc_dmc_create: n_systems must be in [1, 64]");
+  if (capacity_factor < 1 || capacity_factor > 8)
+    return fail(QMC_EINVAL, "qmc_dmc_create: capacity_factor must be in [1, 8]");
+  qmc_dmc_s* d = new qmc_dmc_s;
+  d->sys.resize(n_systems);
+  for (int i = 0; i < n_systems; ++i) {
+    qmc_system_s* s = systems[i];
+    auto& y = d->sys[i];
+    y.sys = s;
+    if (!s || !s->has_spline || !positions[i]) { free_dmc(d); return fail(QMC_EINVAL, "qmc_dmc_create: system %d incomplete", i); }
+    if (s->d.move != QMC_MOVE_DRIFT) { free_dmc(d); return fail(QMC_EINVAL, "qmc_dmc_create: system %d must use drift moves", i); }
+    const int n0 = n_walkers[i];
+    const int cap = n0 * capacity_factor;
+    if (n0 < 1 || cap > 1024 * 1024) { free_dmc(d); return fail(QMC_EINVAL, "qmc_dmc_create: bad walker count for system %d", i); }
+    qmc_status st = alloc_walkers(s, cap, false, &y.w[0]);
+    if (st == QMC_OK) st = alloc_walkers(s, cap, false, &y.w[1]);
+    if (st == QMC_OK) st = init_walkers(y.w[0], n0, positions[i]);
+    if (st != QMC_OK) { const std::string m = g_err; free_dmc(d); g_err = m; return st; }
+    DmcParams& D = y.D;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&y.e_old[0], cap * sizeof(double));
+    e = e ? e : cudaMalloc(&y.e_old[1], cap * sizeof(double));
+    e = e ? e : cudaMalloc(&D.src_of, cap * sizeof(int));
+    e = e ? e : cudaMalloc(&D.wid_next, cap * sizeof(uint32_t));
+    e = e ? e : cudaMalloc(&D.n_live, 2 * sizeof(int));
+    e = e ? e : cudaMalloc(&D.next_id, sizeof(uint32_t));
+    e = e ? e : cudaMalloc(&D.e_trial, sizeof(double));
+    e = e ? e : cudaMalloc(&D.stats, 8 * sizeof(double));
+    e = e ? e : cudaStreamCreateWithFlags(&y.st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { free_dmc(d); return fail(QMC_ENOMEM, "qmc_dmc_create: %s", cudaGetErrorString(e)); }
+    const int live[2] = {n0, 0};
+    const uint32_t nid = (uint32_t)n0;
+    cudaMemcpy(D.n_live, live, sizeof live, cudaMemcpyHostToDevice);
+    cudaMemcpy(D.next_id, &nid, sizeof nid, cudaMemcpyHostToDevice);
+    cudaMemcpy(D.e_trial, &e_trial[i], sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemset(D.stats, 0, 8 * sizeof(double));
+    cudaMemcpy(y.e_old[0], y.w[0]->W.e_loc, n0 * sizeof(double), cudaMemcpyDeviceToDevice);
+    D.n_target = n0;
+    D.cap = cap;
+    D.tau = s->d.step;
+    for (int b = 0; b < 2; ++b) {
+      y.w[b]->W.n_w = cap;
+      y.w[b]->W.n_live = D.n_live + b;
+    }
+  }
+  cudaEventCreateWithFlags(&d->ev_in, cudaEventDisableTiming);
+  d->ev_out.resize(n_systems);
+  for (auto& e : d->ev_out) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  *out = d;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
+  if (!d) return fail(QMC_EINVAL, "qmc_dmc_step: NULL driver");
+  if (n_steps < 0) return fail(QMC_EINVAL, "qmc_dmc_step: n_steps < 0");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  QMC_CUDA(cudaEventRecord(d->ev_in, cs));
+  for (auto& y : d->sys) QMC_CUDA(cudaStreamWaitEvent(y.st, d->ev_in, 0));
+  for (int k = 0; k < n_steps; ++k) {
+    // the systems advance concurrently, one stream each
+    for (auto& y : d->sys) {
+      qmc_walkers_s* w = y.w[y.parity];
+      qmc_walkers_s* w2 = y.w[y.parity ^ 1];
+      WalkParams W = w->W;
+      W.trace = nullptr;
+      W.forced = nullptr;
+      w->sweep = d->step;
+      qmc_status r = sweep_once(w, W, true, y.st);
+      if (r != QMC_OK) return r;
+      { Bracket b(w, y.st, QMC_K_ENERGY); QMC_CUDA(y.sys->tw->local_energy(y.sys->P, W, y.st)); }
+      DmcParams D = y.D;
+      D.e_old = y.e_old[y.parity];
+      D.e_old_next = y.e_old[y.parity ^ 1];
+      QMC_CUDA(y.sys->tw->dmc_branch(y.sys->P, W, D, y.parity, d->step, y.st));
+      QMC_CUDA(y.sys->tw->dmc_copy(y.sys->P, W, w2->W, D, y.parity, y.st));
+      w->launches += 2;
+      y.parity ^= 1;
+    }
+    ++d->step;
+  }
+  for (size_t i = 0; i < d->sys.size(); ++i) {
+    QMC_CUDA(cudaEventRecord(d->ev_out[i], d->sys[i].st));
+    QMC_CUDA(cudaStreamWaitEvent(cs, d->ev_out[i], 0));
+  }
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_read(qmc_dmc_t d, int system, double* out) {
+  if (!d || !out) return fail(QMC_EINVAL, "qmc_dmc_read: NULL argument");
+  if (system < 0 || system >= (int)d->sys.size()) return fail(QMC_EINVAL, "qmc_dmc_read: bad system");
+  auto& y = d->sys[system];
+  QMC_CUDA(cudaStreamSynchronize(y.st));
+  qmc_status r = check_err(y.w[0], y.st);
+  if (r == QMC_OK) r = check_err(y.w[1], y.st);
+  if (r != QMC_OK) return r;
+  double st[8];
+  int live[2];
+  uint32_t nid;
+  double et;
+  QMC_CUDA(cudaMemcpy(st, y.D.stats, sizeof st, cudaMemcpyDeviceToHost));
+  QMC_CUDA(cudaMemcpy(live, y.D.n_live, sizeof live, cudaMemcpyDeviceToHost));
+  QMC_CUDA(cudaMemcpy(&nid, y.D.next_id, sizeof nid, cudaMemcpyDeviceToHost));
+  QMC_CUDA(cudaMemcpy(&et, y.D.e_trial, sizeof et, cudaMemcpyDeviceToHost));
+  const double o[8] = {(double)live[y.parity], st[0], st[1], st[2], st[3], et, (double)nid, st[4]};
+  QMC_CUDA(cudaMemcpy(out, o, sizeof o, cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_walkers(qmc_dmc_t d, int system, int max_walkers, double* pos,
+                                      uint32_t* ids, double* e_local, int* n_out) {
+  if (!d || !n_out) return fail(QMC_EINVAL, "qmc_dmc_walkers: NULL argument");
+  if (system < 0 || system >= (int)d->sys.size()) return fail(QMC_EINVAL, "qmc_dmc_walkers: bad system");
+  auto& y = d->sys[system];
+  QMC_CUDA(cudaStreamSynchronize(y.st));
+  int live[2];
+  QMC_CUDA(cudaMemcpy(live, y.D.n_live, sizeof live, cudaMemcpyDeviceToHost));
+  const int n = live[y.parity];
+  *n_out = n;
+  if (n > max_walkers) return fail(QMC_EINVAL, "qmc_dmc_walkers: %d walkers do not fit in %d", n, max_walkers);
+  qmc_walkers_s* w = y.w[y.parity];
+  const int ne = y.sys->P.n_e;
+  if (pos) {
+    std::vector<double> h((size_t)n * ne * 3), o(h.size());
+    QMC_CUDA(cudaMemcpy(h.data(), w->W.pos, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < n; ++a)
+      for (int c = 0; c < 3; ++c)
+        for (int e = 0; e < ne; ++e) o[((size_t)a * ne + e) * 3 + c] = h[((size_t)a * 3 + c) * ne + e];
+    QMC_CUDA(cudaMemcpy(pos, o.data(), o.size() * sizeof(double), cudaMemcpyDefault));
+  }
+  if (ids) QMC_CUDA(cudaMemcpy(ids, w->W.wid, n * sizeof(uint32_t), cudaMemcpyDefault));
+  if (e_local) QMC_CUDA(cudaMemcpy(e_local, w->W.e_loc, n * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" int64_t qmc_dmc_launch_count(qmc_dmc_t d) {
+  if (!d) return 0;
+  int64_t n = 0;
+  for (auto& y : d->sys) n += y.w[0]->launches + y.w[1]->launches;
+  return n;
+}
+
+extern "C" void qmc_dmc_destroy(qmc_dmc_t d) {
+  if (!d) return;
+  cudaDeviceSynchronize();
+  for (auto& y : d->sys)
+    for (auto* w : y.w) drain_events(w);
+  free_dmc(d);
 }

@@ -70,6 +70,21 @@ struct WalkParams {
   int* win_row;        // [W][kc]       row (electron index within the spin block)
   int* win_m;          // [W]           fill
   float* refine_max;   // [W]           max |I - A X| of the last refinement
+  const int* n_live;   // optional device count: blocks of walkers >= *n_live return at once
+};
+
+// Device state of the branching DMC of one system.
+struct DmcParams {
+  double* e_old;        // [cap] E_L before this step's sweep (per slot of the current buffer)
+  double* e_old_next;   // [cap] the same for the other buffer
+  int* src_of;          // [cap] parent slot of each destination slot
+  uint32_t* wid_next;   // [cap] walker ID of each destination slot
+  int* n_live;          // [2] population of buffer 0 and 1
+  uint32_t* next_id;    // [1] next free walker ID
+  double* e_trial;      // [1] E_T
+  double* stats;        // [8] sum W, sum W E, weighted mean E, E_T used, population before, after
+  int n_target, cap;
+  double tau;
 };
 
 }  // namespace qmcgb

@@ -490,6 +490,7 @@ struct SweepSmem {
   TW* posw;      // [3][n_e] positions in working precision
   TW* phib;      // [2][5 * ld_v] double-buffered proposal orbitals (value, grad, lap)
   TW* rowb;      // [2][ld_v]     double-buffered Binv0[e]
+  TW* xs;        // [ld_v]        current column e of the inverse (window applied)
   TW* wphi;      // [k][ld_v]   window: new orbital rows
   TW* wu;        // [k][ld_v]   window: Binv0 rows of the moved electrons
   TW* rowbuf;    // [nwarps][2][ld_v]  flush: double-buffered rows
@@ -511,7 +512,7 @@ struct SweepSmem {
 template <class TW>
 __host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int nwarps) {
   size_t b = sizeof(double) * (3 * (size_t)n_e + 16 + ld_v + 32 + 8);
-  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 2 + 2 * k + 2 * nwarps) + (size_t)k * k +
+  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 3 + 2 * k + 2 * nwarps) + (size_t)k * k +
                      4 * k + 2 * k * nwarps + 32 * 12 + 8);
   b += sizeof(int) * (k + ld_v + 32 + 4);
   b = (b + 15) & ~size_t(15);
@@ -534,6 +535,7 @@ __device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, in
   TW* t = reinterpret_cast<TW*>(c);
   s.phib = t; t += 10 * ld_v;
   s.rowb = t; t += 2 * ld_v;
+  s.xs = t; t += ld_v;
   s.posw = t; t += 3 * n_e;
   s.wphi = t; t += (size_t)k * ld_v;
   s.wu = t; t += (size_t)k * ld_v;
@@ -629,7 +631,11 @@ __device__ __forceinline__ TW texp(TW x);
 template <> __device__ __forceinline__ double texp<double>(double x) { return exp(x); }
 template <> __device__ __forceinline__ float texp<float>(float x) { return expf(x); }
 
-template <class TW, bool kFixedNode>
+// kDrift: drift-diffusion proposals r' = r + tau grad ln|Psi| + sqrt(tau) xi (Eq.
+// pmc:driftdiffusion_step with the adopted lambda = 1/2), whose orbital values are gathered
+// in the kernel (table type TT) because the proposal depends on the current inverse; the
+// acceptance includes the Green's-function ratio of Eq. pmc:g_driftdiffusion.
+template <class TW, class TT, bool kFixedNode, bool kDrift>
 __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint32_t t, int e0,
                                               int e1, int kc, const TW* __restrict__ Pv,
                                               const Prop* __restrict__ prop, int p_e0, int p_n,
@@ -637,6 +643,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
   extern __shared__ __align__(16) char smem_s[];
   __shared__ JastrowTab<TW> jt;
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = nt >> 5;
   const int n_e = S.n_e, ld_v = Wk.ld_v;
@@ -655,10 +662,11 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
   // prefetch of move index e (orbital row, proposal, inverse row) into buffer b
   auto prefetch = [&](int e, int b, bool with_row) {
     const size_t mvi = (size_t)w * p_n + (e - p_e0);
-    const TW* src = Pv + mvi * 5 * ld_v;
+    const TW* src = kDrift ? VG + (size_t)e * 5 * ld_v : Pv + mvi * 5 * ld_v;
     TW* dst = sm.phib + (size_t)b * 5 * ld_v;
     for (int i = tid * vec; i < 5 * ld_v; i += nt * vec) cp_async16(dst + i, src + i);
-    if (tid < 2) cp_async16(sm.propb + 4 * b + 2 * tid, reinterpret_cast<const double*>(prop + mvi) + 2 * tid);
+    if (!kDrift && tid < 2)
+      cp_async16(sm.propb + 4 * b + 2 * tid, reinterpret_cast<const double*>(prop + mvi) + 2 * tid);
     if (with_row) {
       const TW* rs = B + (size_t)(e - first) * ns;
       TW* rd = sm.rowb + (size_t)b * ld_v;
@@ -686,9 +694,9 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
     cp_async_wait_all();
     __syncthreads();
     if (e + 1 < e1) prefetch(e + 1, cur ^ 1, true);
-    const TW* phi = sm.phib + (size_t)cur * 5 * ld_v;
+    TW* phi = sm.phib + (size_t)cur * 5 * ld_v;
     const TW* row0 = sm.rowb + (size_t)cur * ld_v;
-    if (tid == 0) {
+    if (!kDrift && tid == 0) {
       sm.sc[0] = (TW)sm.propb[4 * cur];
       sm.sc[1] = (TW)sm.propb[4 * cur + 1];
       sm.sc[2] = (TW)sm.propb[4 * cur + 2];
@@ -708,14 +716,88 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       sm.zvec[tid] = z;
     }
     __syncthreads();
-    // x = Binv0[e] - sum_l z_l U_l; ratio and gradient partial sums
+    // x = Binv0[e] - sum_l z_l U_l (column e of the current inverse)
+    for (int j = tid; j < ns; j += nt) {
+      TW xv = row0[j];
+      for (int l = 0; l < m; ++l) xv -= sm.zvec[l] * sm.wu[(size_t)l * ld_v + j];
+      sm.xs[j] = xv;
+    }
+    if constexpr (kDrift) {
+      // grad ln|Psi| at the current position: grad phi(r_e) . x + grad J(r_e)
+      __syncthreads();
+      TW g[6] = {0, 0, 0, 0, 0, 0};
+      for (int j = tid; j < ns; j += nt) {
+        const TW xv = sm.xs[j];
+        g[0] += phi[ld_v + j] * xv;
+        g[1] += phi[2 * ld_v + j] * xv;
+        g[2] += phi[3 * ld_v + j] * xv;
+      }
+      const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+      for (int j = tid; j < n_e + S.n_ion; j += nt) {
+        if (j == e) continue;
+        TW q[3];
+        int f;
+        if (j < n_e) {
+          q[0] = sm.posw[j]; q[1] = sm.posw[n_e + j]; q[2] = sm.posw[2 * n_e + j];
+          f = ((j >= S.n_up) == (e >= S.n_up)) ? 1 : 2;
+        } else {
+          const int I = j - n_e;
+          q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
+          f = 0;
+        }
+        if (jt.M[f] == 0) continue;
+        TW dq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dq[c] = min_image<TW>(ro[c] - q[c], Lw);
+        const TW r = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
+        TW u, du, d2u;
+        jastrow_eval<TW>(jt, f, r, u, du, d2u);
+        if (r > TW(0)) {
+          const TW gg = du / r;
+          g[3] += gg * dq[0]; g[4] += gg * dq[1]; g[5] += gg * dq[2];
+        }
+      }
+      warp_sum<6, TW>(g);
+      if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sm.red[warp * 6 + k] = g[k];
+      __syncthreads();
+      if (tid == 0) {
+        double go[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          TW v = TW(0);
+          for (int q = 0; q < nw; ++q) v += sm.red[q * 6 + c] + sm.red[q * 6 + 3 + c];
+          go[c] = (double)v;
+        }
+        double xi[3], u;
+        move_draws(S, t, (uint32_t)e, Wk.wid[w], xi, u);
+        const double tau = S.step, sq = sqrt(tau);
+        for (int c = 0; c < 3; ++c) {
+          const double rn = wrap_box(sm.posd[c * n_e + e] + tau * go[c] + sq * xi[c], S.L);
+          sm.propb[4 * cur + c] = rn;
+          sm.outd[10 + c] = go[c];
+          sm.sc[c] = (TW)rn;
+        }
+        sm.propb[4 * cur + 3] = u;
+      }
+      __syncthreads();
+      // orbital values, gradients and Laplacians at r' (one warp per 32V-orbital chunk)
+      {
+        constexpr int V = TabVec<TT>::V;
+        const double rr[3] = {sm.propb[4 * cur], sm.propb[4 * cur + 1], sm.propb[4 * cur + 2]};
+        const int chunks = (ns + 32 * V - 1) / (32 * V);
+        for (int ch = warp; ch < chunks; ch += nw) vgl_warp<TT, TW>(S, rr, ch * 32 * V, ns, phi, ld_v);
+      }
+      __syncthreads();
+    }
+    // ratio and gradient partial sums
     TW acc[9];
     {
       TW a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       for (int j = tid; j < ns; j += nt) {
         const TW r0 = row0[j];
-        TW xv = r0;
-        for (int l = 0; l < m; ++l) xv -= sm.zvec[l] * sm.wu[(size_t)l * ld_v + j];
+        const TW xv = sm.xs[j];
         a0 += phi[j] * xv;
         a1 += phi[ld_v + j] * xv;
         a2 += phi[2 * ld_v + j] * xv;
@@ -779,7 +861,24 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       const TW R = tot[0], dJ = tot[5];
       const double u = sm.propb[4 * cur + 3];
       const bool ok = (R != TW(0)) && isfinite(R);
-      const TW A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
+      TW A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
+      if constexpr (kDrift) {
+        if (ok) {
+          // T(R'->R) / T(R->R') with displacement d = r' - r (minimum image)
+          const double tau = S.step;
+          double f2 = 0.0, b2 = 0.0;
+          for (int c = 0; c < 3; ++c) {
+            const double d = min_image<double>(sm.propb[4 * cur + c] - sm.posd[c * n_e + e], S.L);
+            const double gn = (double)(tot[1 + c] / R) + (double)tot[6 + c];
+            const double fw = d - tau * sm.outd[10 + c];
+            const double bw = -d - tau * gn;
+            f2 += fw * fw;
+            b2 += bw * bw;
+          }
+          const double lr = 2.0 * log(fabs((double)R)) + 2.0 * (double)dJ + (f2 - b2) / (2.0 * tau);
+          A = (TW)fmin(1.0, exp(lr));
+        }
+      }
       bool accept = u < (double)A;
       if (kFixedNode && R < TW(0)) accept = false;
       if (Wk.forced) accept = Wk.forced[(size_t)w * n_e + e] != 0;
@@ -1169,6 +1268,7 @@ __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk
   jastrow_tab_fill<TW>(S, jt);
   TW* posw = reinterpret_cast<TW*>(smem_e);                  // [3][n_e]
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n_e = S.n_e, ld_v = Wk.ld_v;
   const double* P = Wk.pos + (size_t)w * 3 * n_e;

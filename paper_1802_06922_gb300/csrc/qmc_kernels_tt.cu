@@ -28,20 +28,34 @@ cudaError_t vgl_proposals(const SysParams& S, const WalkParams& W, int e0, int e
   return cudaGetLastError();
 }
 
+template <class TT, class TW>
+cudaError_t sweep_drift(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1,
+                        int k, int reinv_period, int reinv_on_acc, int ext_flush, bool fixed_node,
+                        cudaStream_t st) {
+  const size_t smem = sweep_smem_bytes<TW>(S.n_e, W.ld_v, k, kThreads / 32);
+  auto kern = fixed_node ? k_sweep<TW, TT, true, true> : k_sweep<TW, TT, false, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<W.n_w, kThreads, smem, st>>>(S, W, t, e0, e1, k, nullptr, nullptr, e0, e1 - e0,
+                                      reinv_period, reinv_on_acc, ext_flush);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const TtLaunch& tt_launch_f64() {
   static const TtLaunch L{TabVec<double>::V, vgl_current<double, double>,
-                          vgl_proposals<double, double>};
+                          vgl_proposals<double, double>, sweep_drift<double, double>};
   return L;
 }
 const TtLaunch& tt_launch_f32() {
-  static const TtLaunch L{TabVec<float>::V, vgl_current<float, float>, vgl_proposals<float, float>};
+  static const TtLaunch L{TabVec<float>::V, vgl_current<float, float>, vgl_proposals<float, float>,
+                          sweep_drift<float, float>};
   return L;
 }
 const TtLaunch& tt_launch_bf16() {
   static const TtLaunch L{TabVec<__nv_bfloat16>::V, vgl_current<__nv_bfloat16, float>,
-                          vgl_proposals<__nv_bfloat16, float>};
+                          vgl_proposals<__nv_bfloat16, float>, sweep_drift<__nv_bfloat16, float>};
   return L;
 }
 

@@ -2,6 +2,7 @@
 #include "qmc_kernels.cuh"
 #include "qmc_launch.h"
 #include "qmc_tc_kernels.cuh"
+#include "qmc_dmc.cuh"
 
 namespace qmcgb {
 namespace {
@@ -22,7 +23,7 @@ cudaError_t sweep(const SysParams& S, const WalkParams& W, uint32_t t, int e0, i
                   const void* P, const void* prop, int p_e0, int p_n, int reinv_period,
                   int reinv_on_acc, int ext_flush, bool fixed_node, cudaStream_t st) {
   const size_t smem = sweep_smem<TW>(S.n_e, W.ld_v, k);
-  auto kern = fixed_node ? k_sweep<TW, true> : k_sweep<TW, false>;
+  auto kern = fixed_node ? k_sweep<TW, TW, true, false> : k_sweep<TW, TW, false, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<W.n_w, kThreads, smem, st>>>(S, W, t, e0, e1, k, static_cast<const TW*>(P),
@@ -96,17 +97,31 @@ cudaError_t invert_batch(const void* A, void* Binv, double* logdet, double* sign
   return cudaGetLastError();
 }
 
+cudaError_t dmc_branch(const SysParams& S, const WalkParams& W, const DmcParams& D, int parity,
+                       uint32_t step, cudaStream_t st) {
+  k_dmc_branch<<<1, 1024, 0, st>>>(S, W, D, parity, step);
+  return cudaGetLastError();
+}
+
+template <class TW>
+cudaError_t dmc_copy(const SysParams& S, const WalkParams& src, const WalkParams& dst,
+                     const DmcParams& D, int parity, cudaStream_t st) {
+  k_dmc_copy<TW><<<D.cap, kThreads, 0, st>>>(S, src, dst, D, parity);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const TwLaunch& tw_launch_f64() {
   static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
                           sweep_smem<double>, invert_batch<double>, flush<double>,
-                          refine<double>};
+                          refine<double>, dmc_branch, dmc_copy<double>};
   return L;
 }
 const TwLaunch& tw_launch_f32() {
   static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
-                          sweep_smem<float>, invert_batch<float>, flush<float>, refine<float>};
+                          sweep_smem<float>, invert_batch<float>, flush<float>, refine<float>,
+                          dmc_branch, dmc_copy<float>};
   return L;
 }
 

@@ -19,6 +19,10 @@ struct TwLaunch {
                               int batch, double* work, cudaStream_t);
   cudaError_t (*flush)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
   cudaError_t (*refine)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
+  cudaError_t (*dmc_branch)(const SysParams&, const WalkParams&, const DmcParams&, int parity,
+                            uint32_t step, cudaStream_t);
+  cudaError_t (*dmc_copy)(const SysParams&, const WalkParams& src, const WalkParams& dst,
+                          const DmcParams&, int parity, cudaStream_t);
 };
 const TwLaunch& tw_launch_f64();
 const TwLaunch& tw_launch_f32();
@@ -29,6 +33,10 @@ struct TtLaunch {
   cudaError_t (*vgl_current)(const SysParams&, const WalkParams&, cudaStream_t);
   cudaError_t (*vgl_proposals)(const SysParams&, const WalkParams&, int e0, int e1,
                                const void* prop, void* out, cudaStream_t);
+  // drift-diffusion sweep of electrons [e0, e1) with in-kernel orbital evaluation
+  cudaError_t (*sweep_drift)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
+                             int k, int reinv_period, int reinv_on_acc, int ext_flush,
+                             bool fixed_node, cudaStream_t);
 };
 const TtLaunch& tt_launch_f64();
 const TtLaunch& tt_launch_f32();

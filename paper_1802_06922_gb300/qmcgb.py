@@ -61,6 +61,12 @@ SIGNATURES = {
     "qmc_last_error": ([], C.c_char_p),
     "qmc_slater_invert": ([_i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "qmc_slater_invert_noalloc": ([_i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
+    "qmc_dmc_create": ([_vp, _vp, _vp, _vp, _i, _i, C.POINTER(_vp)], _i),
+    "qmc_dmc_step": ([_vp, _i, _vp], _i),
+    "qmc_dmc_read": ([_vp, _i, _vp], _i),
+    "qmc_dmc_walkers": ([_vp, _i, _i, _vp, _vp, _vp, C.POINTER(_i)], _i),
+    "qmc_dmc_launch_count": ([_vp], C.c_int64),
+    "qmc_dmc_destroy": ([_vp], None),
 }
 
 _lib: Optional[C.CDLL] = None
@@ -250,6 +256,62 @@ class Walkers:
     def close(self):
         if getattr(self, "h", None):
             load().qmc_walkers_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DMC:
+    """Branching DMC over one or more systems (each a System with move="drift")."""
+
+    def __init__(self, systems, positions, e_trial, capacity_factor=2):
+        lib = load()
+        n = len(systems)
+        self.systems = list(systems)
+        self._pos = [np.ascontiguousarray(p, dtype=np.float64) for p in positions]
+        hs = (C.c_void_p * n)(*[s.h.value for s in systems])
+        nw = (C.c_int * n)(*[p.shape[0] for p in self._pos])
+        pp = (C.c_void_p * n)(*[p.ctypes.data for p in self._pos])
+        et = (C.c_double * n)(*[float(x) for x in e_trial])
+        h = C.c_void_p()
+        _check(lib.qmc_dmc_create(hs, nw, pp, et, n, int(capacity_factor), C.byref(h)))
+        self.h = h
+        self.cap = [int(p.shape[0]) * int(capacity_factor) for p in self._pos]
+
+    def step(self, n=1, stream=None):
+        _check(load().qmc_dmc_step(self.h, int(n), _stream_ptr(stream)))
+
+    def read(self, system):
+        """dict: population, sum_w, sum_we, e_mean, e_trial_used, e_trial_next, next_id,
+        population_before."""
+        o = np.zeros(8)
+        _check(load().qmc_dmc_read(self.h, int(system), o.ctypes.data))
+        keys = ("population", "sum_w", "sum_we", "e_mean", "e_trial_used", "e_trial_next",
+                "next_id", "population_before")
+        return dict(zip(keys, o))
+
+    def walkers(self, system):
+        cap = self.cap[system]
+        ne = self.systems[system].n_up + self.systems[system].n_dn
+        pos = np.zeros((cap, ne, 3))
+        ids = np.zeros(cap, dtype=np.uint32)
+        el = np.zeros(cap)
+        n = C.c_int(0)
+        _check(load().qmc_dmc_walkers(self.h, int(system), cap, pos.ctypes.data, ids.ctypes.data,
+                                      el.ctypes.data, C.byref(n)))
+        k = n.value
+        return pos[:k], ids[:k], el[:k]
+
+    def launch_count(self) -> int:
+        return int(load().qmc_dmc_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().qmc_dmc_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,100 @@
+"""GPU parity of drift-diffusion moves and branching DMC against the FP64 oracle."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from synthetic import build_inputs, small_spec, spec_for
+
+from parity_util import assert_trace_close, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1802_06922_gb300 as q   # noqa: E402
+from oracle.dmc import DMCPopulation   # noqa: E402
+from oracle.vmc import OracleSystem, run_vmc   # noqa: E402
+
+
+def _drift_inputs(n_up, n_dn, tau, n_walkers, grid=10):
+    spec = dataclasses.replace(small_spec(n_up, n_dn, grid=grid), move="drift", step=tau)
+    return build_inputs(spec, n_walkers=n_walkers)
+
+
+@pytest.mark.parametrize("delay_k", [1, 4])
+def test_drift_vmc_fp64_parity(delay_k):
+    inputs = _drift_inputs(9, 8, 0.05, 2)
+    ids = np.arange(2)
+    s = q.system_from_inputs(inputs, precision="fp64", delay_k=delay_k)
+    w = q.Walkers(s, inputs["pos"])
+    buf = torch.zeros((2, 2, 17, 8), dtype=torch.float64, device="cuda")
+    w.trace_enable(buf)
+    en = []
+    for _ in range(2):
+        w.sweep(1)
+        en.append(w.measure())
+    tr = buf.cpu().numpy().transpose(1, 0, 2, 3).reshape(2, 34, 8)
+    _, ref, ref_en = run_vmc(OracleSystem(inputs), inputs["pos"], ids, 2)
+    assert_trace_close(tr, ref, 1e-10)
+    assert np.all(rel_err(np.array(en)[:, 0, :].T, ref_en[..., 0], 1.0) < 1e-10)
+    w.close()
+    s.close()
+
+
+@pytest.mark.parametrize("delay_k", [1, 4])
+def test_branching_dmc_fp64_parity(delay_k):
+    tau, nw, steps = 0.02, 8, 3
+    inputs = _drift_inputs(6, 5, tau, nw)
+    osys = OracleSystem(inputs)
+    e0 = np.mean([osys.measure(osys.walker(R, i))[0] for i, R in enumerate(inputs["pos"])])
+    pop = DMCPopulation(osys, inputs["pos"], list(range(nw)), E_T=e0, capacity=2 * nw)
+    s = q.system_from_inputs(inputs, precision="fp64", delay_k=delay_k, move="drift", step=tau)
+    d = q.DMC([s], [inputs["pos"]], [e0], capacity_factor=2)
+    branched = False
+    for t in range(steps):
+        sum_w, e_mean, _ = pop.step(t)
+        d.step(1)
+        st = d.read(0)
+        pos, ids, el = d.walkers(0)
+        ref_ids = np.array([w.wid for w in pop.walkers])
+        assert st["population"] == len(pop.walkers) > 0
+        assert np.array_equal(ids, ref_ids), (ids, ref_ids)
+        assert np.allclose(pos, np.array([w.R for w in pop.walkers]), rtol=0, atol=1e-10)
+        assert np.allclose(el, pop.E_L, rtol=1e-10, atol=1e-10)
+        assert abs(st["sum_w"] - sum_w) < 1e-10 * sum_w
+        assert abs(st["e_mean"] - e_mean) < 1e-10 * max(1.0, abs(e_mean))
+        assert abs(st["e_trial_next"] - pop.E_T) < 1e-10 * max(1.0, abs(pop.E_T))
+        assert st["next_id"] == pop.next_id
+        branched |= st["population"] != st["population_before"] or len(set(ids)) != len(ids) or max(ids) >= nw
+    assert branched, "no branching event: the test does not exercise copies or deaths"
+    d.close()
+    s.close()
+
+
+def test_dmc_three_uneven_systems_run_together():
+    """The three systems of the batched DMC workload (64, 192, 384 electrons) at reduced
+    walker counts advance together; populations stay within capacity, energies finite."""
+    systems, pos, et = [], [], []
+    for name, nw in (("dmc64", 24), ("dmc192", 16), ("dmc384", 8)):
+        inputs = build_inputs(spec_for(name), n_walkers=nw)
+        s = q.system_from_inputs(inputs, precision="fp32", delay_k=16)
+        w = q.Walkers(s, inputs["pos"])
+        e, _ = w.measure()
+        w.close()
+        systems.append(s)
+        pos.append(inputs["pos"])
+        et.append(float(np.mean(e)))
+    d = q.DMC(systems, pos, et, capacity_factor=2)
+    d.step(3)
+    for i, nw in enumerate((24, 16, 8)):
+        st = d.read(i)
+        assert 0 < st["population"] <= 2 * nw
+        assert np.isfinite(st["e_mean"]) and np.isfinite(st["e_trial_next"])
+        _, ids, el = d.walkers(i)
+        assert len(set(ids.tolist())) == len(ids) and np.all(np.isfinite(el))
+    assert d.launch_count() > 0
+    d.close()
+    for s in systems:
+        s.close()
