@@ -216,6 +216,43 @@ __device__ __forceinline__ void block_sum(T (&v)[N], T* red, double* out) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------------ compensated sums
+// A pair (s, c) carries a sum whose value is s + c to about twice the working precision
+// (TwoProduct by FMA and TwoSum: the error-free transformations of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005). Used for the dot
+// products that decide a move, where cancellation can amplify single-precision rounding
+// by the ratio sum|phi_j x_j| / |R|. In double precision the pair degenerates to a sum.
+__device__ __forceinline__ void comp_fma(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(q, e));
+}
+__device__ __forceinline__ void comp_fma(double& s, double& c, double a, double b) { s += a * b; }
+__device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float z = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), q);
+}
+__device__ __forceinline__ void comp_merge(double& s, double& c, double s2, double c2) {
+  s += s2;
+  c += c2;
+}
+template <class T>
+__device__ __forceinline__ void warp_sum_comp(T& s, T& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const T c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    comp_merge(s, c, s2, c2);
+  }
+}
+
 // ------------------------------------------------------------------ table loads
 template <class TT> struct TabVec;
 template <> struct TabVec<double> {

@@ -509,19 +509,25 @@ struct SweepSmem {
   float* tile;   // [kTileElems] refinement tiles (single-precision forms only)
 };
 
+// `internal`: the kernel flushes windows and re-inverts itself (row buffers, flush
+// scratch and refinement tiles are needed); otherwise both happen in batched kernels.
 template <class TW>
-__host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int nwarps) {
+__host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int nwarps,
+                                                   bool internal = true) {
+  const int nrb = internal ? nwarps : 0;
   size_t b = sizeof(double) * (3 * (size_t)n_e + 16 + ld_v + 32 + 8);
-  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 3 + 2 * k + 2 * nwarps) + (size_t)k * k +
-                     4 * k + 2 * k * nwarps + 32 * 12 + 8);
+  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 3 + 2 * k + 2 * nrb) + (size_t)k * k +
+                     4 * k + 2 * k * nrb + 32 * 12 + 8);
   b += sizeof(int) * (k + ld_v + 32 + 4);
   b = (b + 15) & ~size_t(15);
-  if (sizeof(TW) == 4) b += sizeof(float) * kTileElems;
+  if (sizeof(TW) == 4 && internal) b += sizeof(float) * kTileElems;
   return b + 16;
 }
 
 template <class TW>
-__device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, int k, int nwarps) {
+__device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, int k, int nwarps,
+                                               bool internal) {
+  if (!internal) nwarps = 0;
   SweepSmem<TW> s;
   double* d = reinterpret_cast<double*>(base);
   s.propb = d; d += 8;                 // first: 16-byte aligned for cp.async
@@ -647,7 +653,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = nt >> 5;
   const int n_e = S.n_e, ld_v = Wk.ld_v;
-  SweepSmem<TW> sm = carve<TW>(smem_s, n_e, ld_v, kc, nw);
+  SweepSmem<TW> sm = carve<TW>(smem_s, n_e, ld_v, kc, nw, !ext_flush);
   jastrow_tab_fill<TW>(S, jt);
   const int spin = e0 >= S.n_up ? 1 : 0;
   const int first = spin ? S.n_up : 0;
@@ -701,26 +707,25 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       sm.sc[1] = (TW)sm.propb[4 * cur + 1];
       sm.sc[2] = (TW)sm.propb[4 * cur + 2];
     }
-    // d_l = Phi_l . Binv0[e]
+    // d_l = Phi_l . Binv0[e]  (compensated)
     for (int l = warp; l < m; l += nw) {
-      TW s = TW(0);
-      for (int j = lane; j < ns; j += 32) s += sm.wphi[(size_t)l * ld_v + j] * row0[j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) sm.dvec[l] = s;
+      TW s = TW(0), c = TW(0);
+      for (int j = lane; j < ns; j += 32) comp_fma(s, c, sm.wphi[(size_t)l * ld_v + j], row0[j]);
+      warp_sum_comp(s, c);
+      if (lane == 0) sm.dvec[l] = s + c;
     }
     __syncthreads();
     if (tid < m) {
-      TW z = TW(0);
-      for (int lp = 0; lp < m; ++lp) z += sm.cinv[tid * kc + lp] * sm.dvec[lp];
-      sm.zvec[tid] = z;
+      TW z = TW(0), zc = TW(0);
+      for (int lp = 0; lp < m; ++lp) comp_fma(z, zc, sm.cinv[tid * kc + lp], sm.dvec[lp]);
+      sm.zvec[tid] = z + zc;
     }
     __syncthreads();
-    // x = Binv0[e] - sum_l z_l U_l (column e of the current inverse)
+    // x = Binv0[e] - sum_l z_l U_l (column e of the current inverse), compensated
     for (int j = tid; j < ns; j += nt) {
-      TW xv = row0[j];
-      for (int l = 0; l < m; ++l) xv -= sm.zvec[l] * sm.wu[(size_t)l * ld_v + j];
-      sm.xs[j] = xv;
+      TW xv = row0[j], xc = TW(0);
+      for (int l = 0; l < m; ++l) comp_fma(xv, xc, -sm.zvec[l], sm.wu[(size_t)l * ld_v + j]);
+      sm.xs[j] = xv + xc;
     }
     if constexpr (kDrift) {
       // grad ln|Psi| at the current position: grad phi(r_e) . x + grad J(r_e)
@@ -791,18 +796,19 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       }
       __syncthreads();
     }
-    // ratio and gradient partial sums
+    // ratio (compensated), its companion phi'.Binv0[e] (compensated) and the gradient
     TW acc[9];
+    TW rc = TW(0), ac = TW(0);     // compensation parts of acc[0] and acc[4]
     {
       TW a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
       for (int j = tid; j < ns; j += nt) {
         const TW r0 = row0[j];
         const TW xv = sm.xs[j];
-        a0 += phi[j] * xv;
+        comp_fma(a0, rc, phi[j], xv);
         a1 += phi[ld_v + j] * xv;
         a2 += phi[2 * ld_v + j] * xv;
         a3 += phi[3 * ld_v + j] * xv;
-        a4 += phi[j] * r0;
+        comp_fma(a4, ac, phi[j], r0);
       }
       acc[0] = a0; acc[1] = a1; acc[2] = a2; acc[3] = a3; acc[4] = a4;
     }
@@ -844,19 +850,38 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       }
       acc[5] = dj; acc[6] = gx; acc[7] = gy; acc[8] = gz;
     }
-    // block sums; warp partials added by thread 0 in working precision
-    warp_sum<9, TW>(acc);
-    if (lane == 0)
+    // block sums; warp partials added by thread 0 in working precision, R and a compensated
+    warp_sum_comp(acc[0], rc);
+    warp_sum_comp(acc[4], ac);
+    {
+      TW rest[7] = {acc[1], acc[2], acc[3], acc[5], acc[6], acc[7], acc[8]};
+      warp_sum<7, TW>(rest);
+      acc[1] = rest[0]; acc[2] = rest[1]; acc[3] = rest[2];
+      acc[5] = rest[3]; acc[6] = rest[4]; acc[7] = rest[5]; acc[8] = rest[6];
+    }
+    if (lane == 0) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) sm.red[warp * 9 + k] = acc[k];
+      for (int k = 0; k < 9; ++k) sm.red[warp * 11 + k] = acc[k];
+      sm.red[warp * 11 + 9] = rc;
+      sm.red[warp * 11 + 10] = ac;
+    }
     __syncthreads();
     if (tid == 0) {
       TW tot[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         TW v = TW(0);
-        for (int q = 0; q < nw; ++q) v += sm.red[q * 9 + k];
+        for (int q = 0; q < nw; ++q) v += sm.red[q * 11 + k];
         tot[k] = v;
+      }
+      {
+        TW s0 = sm.red[0], c0 = sm.red[9], s4 = sm.red[4], c4 = sm.red[10];
+        for (int q = 1; q < nw; ++q) {
+          comp_merge(s0, c0, sm.red[q * 11], sm.red[q * 11 + 9]);
+          comp_merge(s4, c4, sm.red[q * 11 + 4], sm.red[q * 11 + 10]);
+        }
+        tot[0] = s0 + c0;
+        tot[4] = s4 + c4;
       }
       const TW R = tot[0], dJ = tot[5];
       const double u = sm.propb[4 * cur + 3];
@@ -904,6 +929,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         sm.posw[e] = sm.sc[0]; sm.posw[n_e + e] = sm.sc[1]; sm.posw[2 * n_e + e] = sm.sc[2];
         sm.wrow[m] = row;
         sm.sc[3] = R;
+        sm.sc[4] = tot[4];        // phi' . Binv0[e]: corner of the bordered C
       }
     }
     __syncthreads();
@@ -916,23 +942,28 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         sm.wphi[(size_t)m * ld_v + j] = phi[j];
         sm.wu[(size_t)m * ld_v + j] = row0[j];
       }
-      // border of C: crow[l'] = phi' . U_l'
+      // border of C: crow[l'] = phi' . U_l'  (compensated)
       for (int l = warp; l < m; l += nw) {
-        TW s = TW(0);
-        for (int j = lane; j < ns; j += 32) s += phi[j] * sm.wu[(size_t)l * ld_v + j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sm.crow[l] = s;
+        TW s = TW(0), c = TW(0);
+        for (int j = lane; j < ns; j += 32) comp_fma(s, c, phi[j], sm.wu[(size_t)l * ld_v + j]);
+        warp_sum_comp(s, c);
+        if (lane == 0) sm.crow[l] = s + c;
       }
       __syncthreads();
       if (tid < m) {
-        TW y = TW(0);
-        for (int l = 0; l < m; ++l) y += sm.crow[l] * sm.cinv[l * kc + tid];
-        sm.yvec[tid] = y;
+        TW y = TW(0), yc = TW(0);
+        for (int l = 0; l < m; ++l) comp_fma(y, yc, sm.crow[l], sm.cinv[l * kc + tid]);
+        sm.yvec[tid] = y + yc;
+      }
+      if (tid == 0) {
+        // Schur complement of the bordered C from its own entries: a - crow . C^-1 d
+        TW sv = sm.sc[4], sc2 = TW(0);
+        for (int l = 0; l < m; ++l) comp_fma(sv, sc2, -sm.crow[l], sm.zvec[l]);
+        sm.sc[5] = sv + sc2;
       }
       __syncthreads();
-      // C^-1 of the bordered matrix (Schur complement s = R)
-      const TW sinv = TW(1) / sm.sc[3];
+      // C^-1 of the bordered matrix
+      const TW sinv = TW(1) / sm.sc[5];
       for (int i = tid; i < (m + 1) * (m + 1); i += nt) {
         const int a = i / (m + 1), b = i % (m + 1);
         TW v;

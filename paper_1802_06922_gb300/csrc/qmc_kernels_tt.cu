@@ -32,7 +32,7 @@ template <class TT, class TW>
 cudaError_t sweep_drift(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1,
                         int k, int reinv_period, int reinv_on_acc, int ext_flush, bool fixed_node,
                         cudaStream_t st) {
-  const size_t smem = sweep_smem_bytes<TW>(S.n_e, W.ld_v, k, kThreads / 32);
+  const size_t smem = sweep_smem_bytes<TW>(S.n_e, W.ld_v, k, kThreads / 32, !ext_flush);
   auto kern = fixed_node ? k_sweep<TW, TT, true, true> : k_sweep<TW, TT, false, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -22,7 +22,7 @@ template <class TW>
 cudaError_t sweep(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1, int k,
                   const void* P, const void* prop, int p_e0, int p_n, int reinv_period,
                   int reinv_on_acc, int ext_flush, bool fixed_node, cudaStream_t st) {
-  const size_t smem = sweep_smem<TW>(S.n_e, W.ld_v, k);
+  const size_t smem = sweep_smem_bytes<TW>(S.n_e, W.ld_v, k, kThreads / 32, !ext_flush);
   auto kern = fixed_node ? k_sweep<TW, TW, true, false> : k_sweep<TW, TW, false, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

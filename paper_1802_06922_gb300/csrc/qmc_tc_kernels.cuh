@@ -5,11 +5,14 @@
 
 namespace qmcgb {
 
-// Split a float into a TF32 head (low 13 mantissa bits cleared) and the remainder, which
-// is exactly representable; the tensor core reads both as TF32. hi*hi + hi*lo + lo*hi
-// reproduces a single-precision product to about 2^-21 relative ("3xTF32").
+// Split a float into its nearest TF32 value and the remainder (|lo| <= 2^-12 |x|, exact in
+// FP32); the tensor core reads both as TF32, losing at most one bit of lo. The three
+// products hi*hi + hi*lo + lo*hi then reproduce a single-precision product to about
+// 2^-23 relative ("3xTF32").
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
   lo = x - hi;
 }
 
