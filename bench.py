@@ -149,44 +149,83 @@ def run_reference(args, spec, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
-def roofline(prof_ms, prof_n, spec, precision, moves_per_step, steps, peaks, delay_k, reinv_period):
-    """Roofline of the kernel class with the largest device time in the timed region."""
+N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
+
+
+def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, delay_k,
+                   reinv_period, sm_mhz):
+    """Roofline of one kernel class from its CUDA-event time inside the timed region.
+
+    achieved = algorithmic bytes (or operations) of one launch / the average launch time;
+    the per-unit figures are the ones stated in ``per_unit``."""
+    if not n:
+        return None
+    sec = ms / 1e3 / n                                   # average launch (bracket) time
+    per_step = n / steps
+    tw = 8 if precision == "fp64" else 4                 # inverse / orbital-row element
+    tab = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]   # spline-table element
+    ld = (spec.n_orb + 7) // 8 * 8
+    ns = spec.n_up
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    moves = moves_per_step / per_step                    # moves per launch
+    out = None
+    if name == "vgl":
+        per = 64 * ld * tab + 5 * ld * tw
+        out = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": per * moves / sec / 1e9,
+               "kernel": "k_vgl_proposals",
+               "per_unit": f"64*N_orb*{tab} B of coefficient rows read + 5*N_orb*{tw} B of "
+                           f"VGL written = {per} B per move"}
+    elif name == "sweep":
+        per = 5 * ld * tw + 3 * ns * tw
+        out = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": per * moves / sec / 1e9,
+               "kernel": "k_sweep",
+               "per_unit": f"proposal VGL row 5*N_orb*{tw} B + inverse row and the window rows "
+                           f"Phi, U 3*N_s*{tw} B = {per} B per move"}
+    elif name == "flush":
+        walkers = spec.n_walkers                         # one spin block of every walker
+        per = 2 * ns * ns * tw + 2 * delay_k * ns * tw
+        out = {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+               "achieved": per * walkers / sec / 1e9, "kernel": "k_flush_tc" if tw == 4 else "k_flush",
+               "per_unit": f"Binv0 read + write 2*N_s^2*{tw} B + window rows Phi, U "
+                           f"2*k*N_s*{tw} B = {per} B per walker and spin block"}
+    elif name == "refine":
+        # Dot2 residual: 10 FP32 instructions per product term (TwoProduct 2, TwoSum 6,
+        # error accumulation 2), then one FMA per term of X R: 11 N_s^3 lane operations
+        per = 11 * ns ** 3
+        peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
+        out = {"bound": "alu", "unit": "Tops/s (FP32 lane operations)", "peak": peak,
+               "achieved": per * spec.n_walkers / sec / 1e12,
+               "kernel": "k_refine_residual + k_refine_update + k_refine_commit",
+               "per_unit": f"11*N_s^3 = {per} FP32 lane operations per walker and spin block; "
+                           f"peak = {N_SM} SMs x {FP32_LANES} lanes x {sm_mhz:.0f} MHz median "
+                           f"sampled SM clock"}
+    elif name == "energy":
+        per = spec.n_elec * 5 * ld * tw + (spec.n_up ** 2 + spec.n_dn ** 2) * tw + 24 * spec.n_elec
+        out = {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+               "achieved": per * spec.n_walkers / sec / 1e9, "kernel": "k_local_energy",
+               "per_unit": f"VGL rows, inverse and positions = {per} B per walker"}
+    if out is not None:
+        out["frac"] = out["achieved"] / out["peak"]
+        out["traffic"] = None
+        out["avg_launch_ms"] = sec * 1e3
+    return out
+
+
+def roofline(prof_ms, prof_n, spec, precision, moves_per_step, steps, peaks, delay_k,
+             reinv_period, sm_mhz):
+    """Rooflines of every kernel class; the dominant class (largest device time) first."""
     import paper_1802_06922_gb300.qmcgb as qb
     names = qb.KERNEL_CLASSES
-    k = max(range(len(names)), key=lambda i: prof_ms[i])
-    name = names[k]
-    sec = prof_ms[k] / 1e3 / max(prof_n[k], 1)          # average launch duration
-    launches_per_step = prof_n[k] / steps
-    moves_per_launch = moves_per_step / max(launches_per_step, 1e-9)
-    bc = {"fp32": 4, "bf16": 2, "fp64": 8}[precision]
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    if name == "vgl":
-        per_move = 64 * spec.n_orb * bc
-        achieved = per_move * moves_per_launch / sec / 1e9
-        out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-               "frac": achieved / hbm, "traffic": None, "kernel": "k_vgl_proposals",
-               "per_unit": f"64*N_orb*{bc} = {per_move} B per move"}
-    elif name == "sweep" and reinv_period:
-        # FP64 Gauss-Jordan: N_s^3 FMA (2 N_s^3 flop) per re-inversion
-        ns = spec.n_up
-        reinv_per_launch = moves_per_launch / reinv_period
-        flops = reinv_per_launch * 2.0 * ns ** 3
-        achieved = flops / sec / 1e12
-        peak = peaks.get("fp64_tflops", 1.26)
-        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-               "frac": achieved / peak, "traffic": None, "kernel": "k_sweep",
-               "per_unit": f"2*N_s^3 = {2 * ns ** 3} FP64 flop per re-inversion, one per "
-                           f"{reinv_period} moves"}
-    else:
-        ns = spec.n_up
-        per_move = 2 * ns * ns * (4 if precision != "fp64" else 8) / max(delay_k, 1) * 1.5
-        achieved = per_move * moves_per_launch / sec / 1e9
-        out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-               "frac": achieved / hbm, "traffic": None, "kernel": f"k_{name}",
-               "per_unit": "inverse read+write per window flush"}
-    out["avg_launch_ms"] = sec * 1e3
-    out["share"] = prof_ms[k] / max(sum(prof_ms), 1e-12)
-    return out
+    total = max(float(sum(prof_ms)), 1e-12)
+    per_class = {}
+    for i, name in enumerate(names):
+        r = class_roofline(name, float(prof_ms[i]), int(prof_n[i]), spec, precision,
+                           moves_per_step, steps, peaks, delay_k, reinv_period, sm_mhz)
+        if r is not None:
+            r["share"] = float(prof_ms[i]) / total
+            per_class[name] = r
+    top = max(per_class, key=lambda k: per_class[k]["share"])
+    return dict(per_class[top], cls=top), per_class
 
 
 def run_ours(args, spec, rank, world, local_rank):
@@ -299,10 +338,12 @@ def run_ours(args, spec, rank, world, local_rank):
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     prof_ms, prof_n = prof
-    roof = roofline(prof_ms, prof_n, spec, args.precision, moves_per_step, args.steps, peaks,
-                    args.delay_k, args.reinv_period)
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    roof, per_class = roofline(prof_ms, prof_n, spec, args.precision, moves_per_step, args.steps,
+                               peaks, args.delay_k, args.reinv_period, sm_mhz)
     import paper_1802_06922_gb300.qmcgb as qb
-    kernels = {n: {"ms": float(prof_ms[i]), "launches": int(prof_n[i])}
+    kernels = {n: {"ms_per_step": float(prof_ms[i]) / args.steps, "launches": int(prof_n[i]),
+                   "roofline": per_class.get(n)}
                for i, n in enumerate(qb.KERNEL_CLASSES) if prof_n[i]}
     cpu = None
     if pool is not None:

@@ -38,10 +38,12 @@ cudaError_t flush(const SysParams& S, const WalkParams& W, int spin, cudaStream_
   if constexpr (sizeof(TW) == 4) {
     // single precision: both products of the flush on the tensor cores (3xTF32)
     const size_t smem = flush_tc_smem_bytes(W.kc);
-    cudaError_t e = cudaFuncSetAttribute(k_flush_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int mx = flush_tc_mpad(W.kc);
+    auto kern = mx <= 16 ? k_flush_tc<16> : mx <= 32 ? k_flush_tc<32> : k_flush_tc<64>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid(W.n_w, (ns + kTcRows - 1) / kTcRows);
-    k_flush_tc<<<grid, kThreads, smem, st>>>(S, W, spin);
+    kern<<<grid, kThreads, smem, st>>>(S, W, spin);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_window_reset<<<(W.n_w + 255) / 256, 256, 0, st>>>(W);

@@ -18,35 +18,58 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 
 constexpr long long kTcWaitPolls = 20000000;   // bounded mbarrier wait (polls)
 constexpr int kTcRows = 128;                    // M of every MMA: one TMEM lane per row
-constexpr int kTcKChunk = 32;                   // K elements staged per pass (tf32)
-constexpr int kTcNChunk = 128;                  // columns of the update per pass
+constexpr int kTcKChunk = 32;                   // K elements of Binv0 staged per pass (tf32)
+constexpr int kTcNChunk = 64;                   // columns of the update per accumulator
+constexpr int kTcCols = 128;                    // TMEM columns per block: two accumulators
 
 // Padded window width (a multiple of 16) for a window capacity kc.
 __host__ __device__ inline int flush_tc_mpad(int kc) { return (kc + 15) & ~15; }
 
-// Dynamic shared memory of k_flush_tc for a window capacity kc.
+// Dynamic shared memory of k_flush_tc for a window capacity kc. The first region holds
+// the Binv0 chunk during the first product and, once that is complete, the Z tile and the
+// two U^T buffers of the second.
 __host__ __device__ inline size_t flush_tc_smem_bytes(int kc) {
   const size_t mx = flush_tc_mpad(kc);
-  size_t b = 0;
-  b += 2 * (size_t)kTcRows * kTcKChunk * 4;     // Binv0 rows chunk, hi + lo
+  const size_t a1 = 2 * (size_t)kTcRows * kTcKChunk * 4;                       // hi + lo
+  const size_t zu = 2 * (size_t)kTcRows * mx * 4 + 2 * 2 * (size_t)kTcNChunk * mx * 4;
+  size_t b = a1 > zu ? a1 : zu;
   b += 2 * mx * kTcKChunk * 4;                  // Phi chunk, hi + lo
-  b += 2 * (size_t)kTcRows * mx * 4;            // Z, hi + lo
-  b += 2 * (size_t)kTcNChunk * mx * 4;          // U^T chunk, hi + lo
   b += (size_t)kc * kc * 4 + (size_t)kc * 4 + 64;
   return b;
+}
+
+// Stages one 16-float slice of a Binv0 row into the hi/lo TF32 tiles.
+__device__ __forceinline__ void stage_split16(const float (&x)[16], float* hi, float* lo, int r,
+                                              int k, int kcols) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    float4 h, l;
+    split_tf32(x[4 * t], h.x, l.x);
+    split_tf32(x[4 * t + 1], h.y, l.y);
+    split_tf32(x[4 * t + 2], h.z, l.z);
+    split_tf32(x[4 * t + 3], h.w, l.w);
+    const uint32_t off = tc::tile_offset(r, k + 4 * t, kcols, 4) >> 2;
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
+  }
 }
 
 // Flush of the delayed-update windows on the tensor cores (see k_flush for the
 // mathematics). Block (w, y) owns rows [128 y, 128 y + 128) of walker w's inverse:
 //   D  = Binv0[rows] Phi^T          (tcgen05 kind::tf32, 3 passes: 3xTF32), TMEM cols [0, mp)
 //   Z  = (D - delta) C^-T            (CUDA cores, one thread per row, from TMEM)
-//   P  = Z U                         (tcgen05, 3xTF32) in chunks of 128 columns, TMEM [128, 256)
+//   P  = Z U                         (tcgen05, 3xTF32) in chunks of 64 columns, alternating
+//                                    between TMEM cols [0, 64) and [64, 128)
 //   Binv0[rows] -= P                 (epilogue from TMEM)
-// Every MMA is issued by thread 0 and completes on an mbarrier that the block waits for
-// with a bounded poll; a timeout sets kErrTimeout and skips the rest of the block.
+// The loads of the next Binv0 chunk are in flight while the tensor core works on the
+// current one, and the epilogue's Binv0 values are loaded before its accumulator is ready,
+// so each pass costs about one memory latency. KP is the padded window capacity (16, 32
+// or 64). Every MMA is issued by thread 0 and completes on an mbarrier that the block
+// waits for with a bounded poll; a timeout sets kErrTimeout and skips the rest of the block.
+template <int KP>
 __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, int spin) {
   extern __shared__ __align__(1024) char smem_t[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[3];                    // first product; second product, 2 buffers
   __shared__ uint32_t tbase;
   const int w = blockIdx.x;
   const int m = Wk.win_m[w];
@@ -57,65 +80,95 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   const int nr = min(kTcRows, ns - r0);
   const int kc = Wk.kc, ld_v = Wk.ld_v;
   const int mp = (m + 15) & ~15;                // N of the first product, K of the second
-  const int mx = flush_tc_mpad(kc);             // staged width of the Z and U^T tiles
+  const int mx = flush_tc_mpad(kc);             // staged width of the Z and U^T tiles (<= KP)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // shared memory: region 1 (A1 during the first product; Z and U^T after it), Phi, C^-1
+  const size_t a1 = 2 * (size_t)kTcRows * kTcKChunk;
+  const size_t zu = 2 * (size_t)kTcRows * mx + 4 * (size_t)kTcNChunk * mx;
   float* A1h = reinterpret_cast<float*>(smem_t);
   float* A1l = A1h + kTcRows * kTcKChunk;
-  float* B1h = A1l + kTcRows * kTcKChunk;
-  float* B1l = B1h + mx * kTcKChunk;
-  float* Zh = B1l + mx * kTcKChunk;
+  float* Zh = A1h;
   float* Zl = Zh + kTcRows * mx;
-  float* Uh = Zl + kTcRows * mx;
-  float* Ul = Uh + kTcNChunk * mx;
-  float* ci = Ul + kTcNChunk * mx;
+  float* Ub = Zl + kTcRows * mx;                // [buffer][hi, lo][64 x mx]
+  float* B1h = A1h + (a1 > zu ? a1 : zu);
+  float* B1l = B1h + mx * kTcKChunk;
+  float* ci = B1l + mx * kTcKChunk;
   int* wrow = reinterpret_cast<int*>(ci + kc * kc);
   const float* gphi = static_cast<const float*>(Wk.win_phi) + (size_t)w * kc * ld_v;
   const float* gu = static_cast<const float*>(Wk.win_u) + (size_t)w * kc * ld_v;
   const float* gc = static_cast<const float*>(Wk.win_cinv) + (size_t)w * kc * kc;
   float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
              (spin ? S.n_up * S.n_up : 0);
+  const bool vec = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
   for (int i = tid; i < kc * kc; i += blockDim.x) ci[i] = gc[i];
   for (int i = tid; i < m; i += blockDim.x) wrow[i] = Wk.win_row[(size_t)w * kc + i];
   if (warp == 0) {
-    tc::tmem_alloc(&tbase, 256);
+    tc::tmem_alloc(&tbase, kTcCols);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&bar, 1);
+    for (int b = 0; b < 3; ++b) tc::mbar_init(&bar[b], 1);
     tc::fence_mbar_init();
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tbase;
-  uint32_t phase = 0;
   bool ok = true;
   // ---------------------------------------------------------------- D = Binv0 Phi^T
-  const int kc1 = kTcKChunk * 4 / 16;                      // 16-byte K columns per chunk
-  const uint32_t id1 = tc::instr_desc(tc::kFmtTF32, kTcRows, mp);
-  for (int k0 = 0; k0 < ns && ok; k0 += kTcKChunk) {
-    for (int i = tid; i < kTcRows * kTcKChunk; i += blockDim.x) {
-      const int r = i / kTcKChunk, k = i % kTcKChunk, j = k0 + k;
-      const float x = (r < nr && j < ns) ? B[(size_t)(r0 + r) * ns + j] : 0.f;
-      float hi, lo;
-      split_tf32(x, hi, lo);
-      const uint32_t off = tc::tile_offset(r, k, kc1, 4) >> 2;
-      A1h[off] = hi;
-      A1l[off] = lo;
+  // thread -> row lr of the tile, 16 consecutive columns lc.. of each 32-wide K chunk
+  const int lr = tid >> 1, lc = (tid & 1) * 16;
+  const int kc1 = kTcKChunk * 4 / 16;           // 16-byte K columns per chunk
+  const float* brow = B + (size_t)(r0 + lr) * ns;
+  float xa[16];
+  constexpr int kPhiPer = KP * kTcKChunk / 256;  // Phi elements per thread and chunk
+  float xp[kPhiPer];
+  auto load_chunk = [&](int k0) {
+    const int j = k0 + lc;
+    if (vec) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lr < nr && j + 4 * t < ns) v = *reinterpret_cast<const float4*>(brow + j + 4 * t);
+        xa[4 * t] = v.x; xa[4 * t + 1] = v.y; xa[4 * t + 2] = v.z; xa[4 * t + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) xa[t] = (lr < nr && j + t < ns) ? brow[j + t] : 0.f;
     }
-    for (int i = tid; i < mp * kTcKChunk; i += blockDim.x) {
-      const int l = i / kTcKChunk, k = i % kTcKChunk, j = k0 + k;
-      const float x = (l < m && j < ns) ? gphi[(size_t)l * ld_v + j] : 0.f;
-      float hi, lo;
-      split_tf32(x, hi, lo);
-      const uint32_t off = tc::tile_offset(l, k, kc1, 4) >> 2;
-      B1h[off] = hi;
-      B1l[off] = lo;
+#pragma unroll
+    for (int q = 0; q < kPhiPer; ++q) {
+      const int i = tid + 256 * q, l = i / kTcKChunk, jj = k0 + i % kTcKChunk;
+      xp[q] = (l < m && jj < ns) ? gphi[(size_t)l * ld_v + jj] : 0.f;
+    }
+  };
+  const uint32_t id1 = tc::instr_desc(tc::kFmtTF32, kTcRows, mp);
+  load_chunk(0);
+  uint32_t ph1 = 0;
+  for (int k0 = 0; k0 < ns; k0 += kTcKChunk) {
+    if (k0 > 0) {                               // the previous chunk's MMAs read A1 and B1
+      ok = tc::mbar_wait(&bar[0], ph1, kTcWaitPolls) && ok;
+      ph1 ^= 1u;
+    }
+    stage_split16(xa, A1h, A1l, lr, lc, kc1);
+#pragma unroll
+    for (int q = 0; q < kPhiPer; ++q) {
+      const int i = tid + 256 * q, l = i / kTcKChunk, k = i % kTcKChunk;
+      if (l < mx) {
+        float hi, lo;
+        split_tf32(xp[q], hi, lo);
+        const uint32_t off = tc::tile_offset(l, k, kc1, 4) >> 2;
+        B1h[off] = hi;
+        B1l[off] = lo;
+      }
     }
     tc::fence_async_smem();
-    __syncthreads();
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    if (k0 + kTcKChunk < ns) load_chunk(k0 + kTcKChunk);
     if (tid == 0) {
       tc::fence_after();
+#pragma unroll
       for (int s = 0; s < kTcKChunk / 8; ++s) {
         const uint64_t ah = tc::smem_desc(A1h + s * 64, 128, kc1 * 128);
         const uint64_t al = tc::smem_desc(A1l + s * 64, 128, kc1 * 128);
@@ -126,43 +179,65 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
         tc::mma_tf32(tmem, ah, bl, id1, 1u);
         tc::mma_tf32(tmem, al, bh, id1, 1u);
       }
-      tc::mma_commit(&bar);
+      tc::mma_commit(&bar[0]);
     }
-    ok = tc::mbar_wait(&bar, phase, kTcWaitPolls);
-    phase ^= 1u;
-    ok = __syncthreads_and(ok);
-    tc::fence_after();
   }
+  if (ok) ok = tc::mbar_wait(&bar[0], ph1, kTcWaitPolls);
+  ok = __syncthreads_and(ok);
+  tc::fence_after();
   // ---------------------------------------------------------------- Z = (D - delta) C^-T
-  if (ok && warp < 4) {
-    const int n = warp * 32 + lane;                         // TMEM lane = row in the tile
-    float d[64];
-#pragma unroll
-    for (int c = 0; c < 64; c += 16) {
-      if (c < mp) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) d[c + q] = v[q];
-      }
-    }
-#pragma unroll
-    for (int l = 0; l < 64; ++l)
-      if (l < m && wrow[l] == r0 + n) d[l] -= 1.f;
-    const int kz = mx * 4 / 16;                             // K columns of the Z tile
-    for (int l = 0; l < mp; ++l) {
-      float z = 0.f;
-      if (l < m) {
-#pragma unroll
-        for (int lp = 0; lp < 64; ++lp)
-          if (lp < m) z += ci[l * kc + lp] * d[lp];
-      }
-      if (n >= nr) z = 0.f;
+  const int kz = mx * 4 / 16;                   // 16-byte K columns of the Z and U^T tiles
+  const int n_chunks = (ns + kTcNChunk - 1) / kTcNChunk;
+  auto stage_u = [&](int c, int t0, int nt) {   // U^T chunk c into buffer c & 1
+    float* uh = Ub + (size_t)(c & 1) * 2 * kTcNChunk * mx;
+    float* ul = uh + kTcNChunk * mx;
+    const int j0 = c * kTcNChunk;
+    for (int i = t0; i < kTcNChunk * mx; i += nt) {
+      const int l = i / kTcNChunk, jj = i % kTcNChunk, j = j0 + jj;
+      const float x = (l < m && j < ns) ? gu[(size_t)l * ld_v + j] : 0.f;
       float hi, lo;
-      split_tf32(z, hi, lo);
-      const uint32_t off = tc::tile_offset(n, l, kz, 4) >> 2;
-      Zh[off] = hi;
-      Zl[off] = lo;
+      split_tf32(x, hi, lo);
+      const uint32_t off = tc::tile_offset(jj, l, kz, 4) >> 2;
+      uh[off] = hi;
+      ul[off] = lo;
+    }
+  };
+  if (ok) {
+    if (warp < 4) {
+      const int n = warp * 32 + lane;           // TMEM lane = row in the tile
+      float d[KP];
+#pragma unroll
+      for (int c = 0; c < KP; c += 16) {
+        if (c < mp) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) d[c + q] = v[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) d[c + q] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int l = 0; l < KP; ++l)
+        if (l < m && wrow[l] == r0 + n) d[l] -= 1.f;
+      for (int l = 0; l < mx; ++l) {
+        float z = 0.f;
+        if (l < m) {
+#pragma unroll
+          for (int lp = 0; lp < KP; ++lp)
+            if (lp < m) z = fmaf(ci[l * kc + lp], d[lp], z);
+        }
+        if (n >= nr) z = 0.f;
+        float hi, lo;
+        split_tf32(z, hi, lo);
+        const uint32_t off = tc::tile_offset(n, l, kz, 4) >> 2;
+        Zh[off] = hi;
+        Zl[off] = lo;
+      }
+    } else {
+      stage_u(0, tid - 128, 128);
+      if (n_chunks > 1) stage_u(1, tid - 128, 128);
     }
   }
   tc::fence_async_smem();
@@ -170,72 +245,83 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   ok = __syncthreads_and(ok);
   tc::fence_after();
   // ---------------------------------------------------------------- Binv0 -= Z U
-  const int kz = mx * 4 / 16;
   const uint32_t id2 = tc::instr_desc(tc::kFmtTF32, kTcRows, kTcNChunk);
-  for (int j0 = 0; j0 < ns && ok; j0 += kTcNChunk) {
-    for (int i = tid; i < kTcNChunk * mp; i += blockDim.x) {
-      const int jj = i / mp, l = i % mp, j = j0 + jj;
-      const float x = (l < m && j < ns) ? gu[(size_t)l * ld_v + j] : 0.f;
-      float hi, lo;
-      split_tf32(x, hi, lo);
-      const uint32_t off = tc::tile_offset(jj, l, kz, 4) >> 2;
-      Uh[off] = hi;
-      Ul[off] = lo;
+  auto issue2 = [&](int c) {                    // thread 0: P_c into TMEM cols (c & 1) * 64
+    const float* uh = Ub + (size_t)(c & 1) * 2 * kTcNChunk * mx;
+    const float* ul = uh + kTcNChunk * mx;
+    const uint32_t dst = tmem + (uint32_t)((c & 1) * kTcNChunk);
+    for (int s = 0; s < mp / 8; ++s) {
+      const uint64_t ah = tc::smem_desc(Zh + s * 64, 128, kz * 128);
+      const uint64_t al = tc::smem_desc(Zl + s * 64, 128, kz * 128);
+      const uint64_t bh = tc::smem_desc(uh + s * 64, 128, kz * 128);
+      const uint64_t bl = tc::smem_desc(ul + s * 64, 128, kz * 128);
+      const uint32_t first = (s == 0) ? 0u : 1u;
+      tc::mma_tf32(dst, ah, bh, id2, first);
+      tc::mma_tf32(dst, ah, bl, id2, 1u);
+      tc::mma_tf32(dst, al, bh, id2, 1u);
     }
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      for (int s = 0; s < mp / 8; ++s) {
-        const uint64_t ah = tc::smem_desc(Zh + s * 64, 128, kz * 128);
-        const uint64_t al = tc::smem_desc(Zl + s * 64, 128, kz * 128);
-        const uint64_t bh = tc::smem_desc(Uh + s * 64, 128, kz * 128);
-        const uint64_t bl = tc::smem_desc(Ul + s * 64, 128, kz * 128);
-        const uint32_t first = (s == 0) ? 0u : 1u;
-        tc::mma_tf32(tmem + 128, ah, bh, id2, first);
-        tc::mma_tf32(tmem + 128, ah, bl, id2, 1u);
-        tc::mma_tf32(tmem + 128, al, bh, id2, 1u);
-      }
-      tc::mma_commit(&bar);
-    }
-    ok = tc::mbar_wait(&bar, phase, kTcWaitPolls);
-    phase ^= 1u;
-    ok = __syncthreads_and(ok);
+    tc::mma_commit(&bar[1 + (c & 1)]);
+  };
+  if (ok && tid == 0) {
     tc::fence_after();
-    if (ok) {
-      const int q = warp & 3, h = warp >> 2;               // lane quarter, column half
-      const int n = q * 32 + lane;
+    issue2(0);
+  }
+  const int q4 = warp & 3, h2 = warp >> 2;      // lane quarter, column half of a chunk
+  const int n = q4 * 32 + lane;
+  float* erow = B + (size_t)(r0 + n) * ns;
+  for (int c = 0; c < n_chunks && ok; ++c) {
+    // the other accumulator and U^T buffer were released by the previous iteration
+    if (tid == 0 && c + 1 < n_chunks) {
+      tc::fence_after();
+      issue2(c + 1);
+    }
+    const int jb = c * kTcNChunk + h2 * 32;
+    float bv[32];
+    if (vec) {
 #pragma unroll
-      for (int c = 0; c < kTcNChunk / 2; c += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + 128 + h * (kTcNChunk / 2) + c, v);
-        if (n < nr) {
-          const int jb = j0 + h * (kTcNChunk / 2) + c;
-          float* row = B + (size_t)(r0 + n) * ns;
-          if ((ns & 3) == 0 && jb + 16 <= ns) {
-            float4* p4 = reinterpret_cast<float4*>(row + jb);
+      for (int t = 0; t < 8; ++t) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < nr && jb + 4 * t < ns) v = *reinterpret_cast<const float4*>(erow + jb + 4 * t);
+        bv[4 * t] = v.x; bv[4 * t + 1] = v.y; bv[4 * t + 2] = v.z; bv[4 * t + 3] = v.w;
+      }
+    } else {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              float4 b4 = p4[t];
-              b4.x -= v[4 * t]; b4.y -= v[4 * t + 1]; b4.z -= v[4 * t + 2]; b4.w -= v[4 * t + 3];
-              p4[t] = b4;
-            }
-          } else {
+      for (int t = 0; t < 32; ++t) bv[t] = (n < nr && jb + t < ns) ? erow[jb + t] : 0.f;
+    }
+    ok = tc::mbar_wait(&bar[1 + (c & 1)], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    tc::fence_after();
 #pragma unroll
-            for (int t = 0; t < 16; ++t)
-              if (jb + t < ns) row[jb + t] -= v[t];
-          }
-        }
+    for (int g = 0; g < 2; ++g) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (c & 1) * kTcNChunk + h2 * 32 + g * 16, v);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) bv[16 * g + t] -= v[t];
+    }
+    if (n < nr) {
+      if (vec) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (jb + 4 * t < ns)
+            *reinterpret_cast<float4*>(erow + jb + 4 * t) =
+                make_float4(bv[4 * t], bv[4 * t + 1], bv[4 * t + 2], bv[4 * t + 3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+          if (jb + t < ns) erow[jb + t] = bv[t];
       }
     }
+    // U^T buffer c & 1 is free (its MMAs completed): stage chunk c + 2 there
+    if (c + 2 < n_chunks) stage_u(c + 2, tid, blockDim.x);
+    tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
-    tc::fence_after();
   }
   if (!ok && tid == 0) atomicOr(Wk.err, kErrTimeout);
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, kTcCols);
 }
 
 }  // namespace qmcgb
