@@ -47,14 +47,23 @@ def parse_args():
     p.add_argument("--cpu-cores", type=int, default=0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--reinv-on-accepted", action="store_true",
+                   help="count the re-inversion period in accepted moves of each determinant")
+    p.add_argument("--workload", default="vmc", choices=["vmc", "dmc"],
+                   help="dmc: the batched uneven drift-diffusion/branching workload "
+                        "(64/192/384 electrons with 768/512/256 target walkers)")
+    p.add_argument("--dmc-vmc-sweeps", type=int, default=4,
+                   help="drift-diffusion VMC sweeps that equilibrate the walkers before DMC")
     return p.parse_args()
 
 
 # ------------------------------------------------------------------ workload description
-def workload(spec, precision, delay_k, reinv_period):
+def workload(spec, precision, delay_k, reinv_period, on_accepted=False):
     tab = {"fp32": "FP32", "bf16": "BF16", "fp64": "FP64"}[precision]
     upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
-    re = f"FP64 re-inversion every {reinv_period} moves" if reinv_period else "no re-inversion"
+    what = "accepted moves" if on_accepted else "moves"
+    re = (("FP64 re-inversion" if precision == "fp64" else "re-inversion (error-free Newton step)")
+          + f" every {reinv_period} {what}") if reinv_period else "no re-inversion"
     return (f"{spec.name}: {spec.n_elec} electrons ({spec.n_up} up/{spec.n_dn} down), "
             f"{spec.n_orb} orbitals on a {spec.grid}^3 {tab} tricubic B-spline table, "
             f"{spec.n_ion} ions, J1/J2 B-spline M={spec.jastrow_M}, {spec.n_walkers} walkers, "
@@ -287,7 +296,8 @@ def run_ours(args, spec, rank, world, local_rank):
         return ms, prof, launches, clocks, e_loc
 
     sysm = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                reinv_period=args.reinv_period, reinv_on_accepted=False)
+                                reinv_period=args.reinv_period,
+                                reinv_on_accepted=args.reinv_on_accepted)
     ms, prof, launches, clocks, e_loc = timed(sysm, args.steps, args.warmup, profile=True)
     value = world * moves_per_step * args.steps / (ms / 1e3)
 
@@ -355,7 +365,8 @@ def run_ours(args, spec, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": workload(spec, args.precision, args.delay_k, args.reinv_period),
+            "config": {"workload": workload(spec, args.precision, args.delay_k, args.reinv_period,
+                                            args.reinv_on_accepted),
                        "walkers_per_gpu": spec.n_walkers, "electrons": spec.n_elec,
                        "moves_per_step": moves_per_step * world,
                        "l2": f"inputs larger than L2: {table_bytes(spec, args.precision) / 1e6:.0f} MB "
@@ -368,6 +379,92 @@ def run_ours(args, spec, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+DMC_SYSTEMS = ("dmc64", "dmc192", "dmc384")
+
+
+def run_dmc(args, rank, world, local_rank):
+    """Batched uneven DMC: three systems advance together each step (drift-diffusion sweep,
+    local energy, branching and compaction; one stream per system). moves/s counts
+    sum_s N_e(s) * N_w(s, step) over the timed steps, each step bracketed by CUDA events on
+    the caller's stream (the systems' streams join it)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import paper_1802_06922_gb300 as q
+    from synthetic import build_inputs, spec_for
+    stream = torch.cuda.current_stream()
+    systems, pos, et, specs = [], [], [], []
+    for name in DMC_SYSTEMS:
+        spec = spec_for(name)
+        inputs = build_inputs(spec, seed=0)
+        inputs["seed"] = rank
+        s = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+                                 reinv_period=args.reinv_period, move="drift", step=spec.step)
+        # equilibrate with drift-diffusion VMC sweeps before branching starts (uniform
+        # random starting points put some walkers next to a node, where E_L is extreme)
+        w = q.Walkers(s, inputs["pos"])
+        w.sweep(args.dmc_vmc_sweeps, stream)
+        p_eq = w.positions()
+        e, _ = w.measure()
+        w.close()
+        systems.append(s)
+        pos.append(p_eq)
+        et.append(float(np.median(e)))
+        specs.append(spec)
+    d = q.DMC(systems, pos, et, capacity_factor=2)
+    d.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    l0 = d.launch_count()
+    total_ms, moves = 0.0, 0
+    pops = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        e0.record(stream)
+        d.step(1, stream)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        st = [d.read(i) for i in range(len(systems))]
+        pops.append([int(x["population_before"]) for x in st])
+        moves += sum(sp.n_elec * int(x["population_before"]) for sp, x in zip(specs, st))
+    launches = d.launch_count() - l0
+    final = [d.read(i) for i in range(len(systems))]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    d.close()
+    for s in systems:
+        s.close()
+    if rank != 0:
+        return
+    value = world * moves / (total_ms / 1e3)
+    line = {"metric": "electron moves/sec, batched uneven DMC (sum over systems of N_e x N_w per step)",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "; ".join(
+                           f"{sp.name}: {sp.n_elec} electrons, {sp.grid}^3 table, {sp.n_orb} "
+                           f"orbitals, {sp.n_walkers} target walkers" for sp in specs)
+                       + f"; drift-diffusion tau={specs[0].step}, branching, E_T feedback, "
+                         f"delayed rank-{args.delay_k}, re-inversion every {args.reinv_period} moves; "
+                         f"walkers equilibrated by {args.dmc_vmc_sweeps} VMC sweeps, E_T from "
+                         f"their median E_L",
+                       "parallelism": f"replicas x{world}; systems on concurrent streams"},
+            "populations_first_last": [pops[0], pops[-1]],
+            "e_mean_last": [float(x["e_mean"]) for x in final],
+            "e_trial_last": [float(x["e_trial_next"]) for x in final],
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     from synthetic import spec_for
@@ -377,6 +474,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, spec, rank, world)
+    elif args.workload == "dmc":
+        run_dmc(args, rank, world, local_rank)
     else:
         run_ours(args, spec, rank, world, local_rank)
 

@@ -7,7 +7,15 @@
 
 namespace qmcgb {
 
-
+// Copies M = floor(w + xi) of a walker, clamped to [0, cap] in double before the integer
+// conversion: a weight of 2^31 or more (a walker next to a node) or a non-finite one must
+// not overflow the prefix sums. Copies beyond the capacity are dropped in any case, so the
+// clamp leaves every kept slot unchanged.
+__device__ __forceinline__ int dmc_copies(double wgt, double xi, int cap) {
+  const double mf = floor(wgt + xi);
+  if (!(mf > 0.0)) return 0;
+  return mf >= (double)cap ? cap : (int)mf;
+}
 
 // One block: weights w = exp(-tau/2 (E_old + E_new - 2 E_T)) (Eq. pmc:g_growth, Eq.
 // pmc:walker_weight), copies M = floor(w + xi) with xi from Philox block (step, 0xB, ID, 2),
@@ -30,12 +38,12 @@ __global__ void __launch_bounds__(1024) k_dmc_branch(SysParams S, WalkParams Wk,
   for (int i = i0; i < i1; ++i) {
     const double wgt = exp(-0.5 * D.tau * (D.e_old[i] + Wk.e_loc[i] - 2.0 * et));
     const U32x4 r = philox4x32_10(step, 0xBu, Wk.wid[i], 2u, S.seed_lo, S.seed_hi);
-    const int M = (int)floor(wgt + unit_open(r.v[0]));
+    const int M = dmc_copies(wgt, unit_open(r.v[0]), D.cap);
     Wk.weight[i] = wgt;
     sw += wgt;
     swe += wgt * Wk.e_loc[i];
-    mloc += M;
-    xloc += M > 0 ? M - 1 : 0;
+    mloc = min(mloc + M, D.cap);                 // sums bounded by cap: no overflow
+    xloc = min(xloc + (M > 0 ? M - 1 : 0), D.cap);
   }
   // block sums of the weights
 #pragma unroll
@@ -62,16 +70,14 @@ __global__ void __launch_bounds__(1024) k_dmc_branch(SysParams S, WalkParams Wk,
   for (int i = i0; i < i1; ++i) {
     const double wgt = Wk.weight[i];
     const U32x4 r = philox4x32_10(step, 0xBu, Wk.wid[i], 2u, S.seed_lo, S.seed_hi);
-    const int M = (int)floor(wgt + unit_open(r.v[0]));
-    for (int c = 0; c < M; ++c) {
+    const int M = dmc_copies(wgt, unit_open(r.v[0]), D.cap);
+    for (int c = 0; c < M && dest + c < D.cap; ++c) {
       const int d = dest + c;
-      if (d < D.cap) {
-        D.src_of[d] = i;
-        D.wid_next[d] = c == 0 ? Wk.wid[i] : nid + (uint32_t)(xr + c - 1);
-      }
+      D.src_of[d] = i;
+      D.wid_next[d] = c == 0 ? Wk.wid[i] : nid + (uint32_t)(xr + c - 1);
     }
-    dest += M;
-    xr += M > 0 ? M - 1 : 0;
+    dest = min(dest + M, D.cap);
+    xr = min(xr + (M > 0 ? M - 1 : 0), D.cap);
   }
   __syncthreads();
   if (tid == 0) {

@@ -1067,6 +1067,7 @@ template <class TW>
 __global__ void __launch_bounds__(256) k_flush(SysParams S, WalkParams Wk, int spin) {
   extern __shared__ __align__(16) char smem_f[];
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;            // empty DMC slot
   const int m = Wk.win_m[w];
   if (m == 0) return;
   const int kc = Wk.kc, ld_v = Wk.ld_v, ldb = ld_v + 1;
@@ -1155,6 +1156,7 @@ template <class TW>
 __global__ void __launch_bounds__(256) k_refine_residual(SysParams S, WalkParams Wk, int spin) {
   __shared__ float As[32 * 64], Bs[32 * 64];
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
   const int ns = spin ? S.n_dn : S.n_up;
   const int first = spin ? S.n_up : 0;
   const int nt64 = (ns + 63) / 64;
@@ -1217,6 +1219,7 @@ template <class TW>
 __global__ void __launch_bounds__(256) k_refine_update(SysParams S, WalkParams Wk, int spin) {
   __shared__ float As[32 * 64], Bs[32 * 64];
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
   if (!(Wk.refine_max[w] <= kRefineMax)) return;
   const int ns = spin ? S.n_dn : S.n_up;
   const int nt64 = (ns + 63) / 64;
@@ -1268,6 +1271,7 @@ template <class TW>
 __global__ void __launch_bounds__(256) k_refine_commit(SysParams S, WalkParams Wk, int spin) {
   extern __shared__ __align__(16) char smem_c[];
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
   const int ns = spin ? S.n_dn : S.n_up;
   float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
              (spin ? S.n_up * S.n_up : 0);

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   __shared__ uint64_t bar[3];                    // first product; second product, 2 buffers
   __shared__ uint32_t tbase;
   const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;            // empty DMC slot
   const int m = Wk.win_m[w];
   if (m == 0) return;
   const int ns = spin ? S.n_dn : S.n_up;

@@ -98,3 +98,57 @@ def test_dmc_three_uneven_systems_run_together():
     d.close()
     for s in systems:
         s.close()
+
+
+def test_branching_saturates_at_capacity_with_huge_weights():
+    """A trial energy 2000 Ha above E_L gives weights near e^40 (beyond 2^31 copies): the
+    population fills the capacity with copies in parent order, exactly as the oracle drops
+    every copy beyond it, and the next step proceeds normally."""
+    tau, nw = 0.02, 8
+    inputs = _drift_inputs(6, 5, tau, nw)
+    osys = OracleSystem(inputs)
+    e0 = np.mean([osys.measure(osys.walker(R, i))[0] for i, R in enumerate(inputs["pos"])])
+    et = e0 + 2000.0
+    pop = DMCPopulation(osys, inputs["pos"], list(range(nw)), E_T=et, capacity=2 * nw)
+    s = q.system_from_inputs(inputs, precision="fp64", delay_k=1, move="drift", step=tau)
+    d = q.DMC([s], [inputs["pos"]], [et], capacity_factor=2)
+    for t in range(2):
+        sum_w, e_mean, _ = pop.step(t)
+        d.step(1)
+        st = d.read(0)
+        _, ids, el = d.walkers(0)
+        assert st["population"] == len(pop.walkers)
+        assert np.array_equal(ids, np.array([w.wid for w in pop.walkers]))
+        assert np.allclose(el, pop.E_L, rtol=1e-10, atol=1e-10)
+        assert abs(st["sum_w"] - sum_w) < 1e-10 * sum_w
+        assert st["next_id"] == pop.next_id
+    assert len(pop.walkers) > 0
+    d.close()
+    s.close()
+
+
+def test_dmc_uneven_systems_with_refinement():
+    """Batched DMC with the single-precision inverse refined every 32 moves: empty slots of
+    the capacity-padded buffers are skipped by every kernel (no error flag), populations stay
+    within capacity and energies finite over several steps."""
+    systems, pos, et, caps = [], [], [], []
+    for name, nw in (("dmc64", 48), ("dmc192", 24), ("dmc384", 12)):
+        inputs = build_inputs(spec_for(name), n_walkers=nw)
+        s = q.system_from_inputs(inputs, precision="fp32", delay_k=16, reinv_period=32)
+        w = q.Walkers(s, inputs["pos"])
+        e, _ = w.measure()
+        w.close()
+        systems.append(s)
+        pos.append(inputs["pos"])
+        et.append(float(np.mean(e)))
+        caps.append(2 * nw)
+    d = q.DMC(systems, pos, et, capacity_factor=2)
+    for _ in range(6):
+        d.step(1)
+        for i, cap in enumerate(caps):
+            st = d.read(i)                   # raises on any device error flag
+            assert 0 < st["population"] <= cap
+            assert np.isfinite(st["e_mean"])
+    d.close()
+    for s in systems:
+        s.close()
