@@ -198,16 +198,24 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
                "per_unit": f"Binv0 read + write 2*N_s^2*{tw} B + window rows Phi, U "
                            f"2*k*N_s*{tw} B = {per} B per walker and spin block"}
     elif name == "refine":
-        # Dot2 residual: 10 FP32 instructions per product term (TwoProduct 2, TwoSum 6,
-        # error accumulation 2), then one FMA per term of X R: 11 N_s^3 lane operations
-        per = 11 * ns ** 3
-        peak = N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
-        out = {"bound": "alu", "unit": "Tops/s (FP32 lane operations)", "peak": peak,
+        # error-free residual: 21 BF16 slice-pair products of N_s x N_s x N_s on tcgen05
+        pairs = sum(1 for i in range(1, 7) for j in range(1, 7) if i + j <= 7)
+        per = pairs * 2 * ns ** 3
+        peak = peaks.get("bf16_tflops", 1899.6)
+        out = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                "achieved": per * spec.n_walkers / sec / 1e12,
-               "kernel": "k_refine_residual + k_refine_update + k_refine_commit",
-               "per_unit": f"11*N_s^3 = {per} FP32 lane operations per walker and spin block; "
-                           f"peak = {N_SM} SMs x {FP32_LANES} lanes x {sm_mhz:.0f} MHz median "
-                           f"sampled SM clock"}
+               "kernel": "k_refine_scales + k_refine_residual_tc",
+               "per_unit": f"{pairs} slice pairs x 2*N_s^3 = {per} BF16 tensor flop per walker and "
+                           f"spin block (peak: measured cuBLAS BF16 burst)"}
+    elif name == "refine_update":
+        # X <- X + X R on the FP32 pipe: N_s^3 FMA = 2 N_s^3 flop
+        per = 2 * ns ** 3
+        peak = 2 * N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
+        out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+               "achieved": per * spec.n_walkers / sec / 1e12,
+               "kernel": "k_refine_update + k_refine_commit",
+               "per_unit": f"2*N_s^3 = {per} FP32 flop per walker and spin block; peak = 2 x "
+                           f"{N_SM} SMs x {FP32_LANES} lanes x {sm_mhz:.0f} MHz median sampled SM clock"}
     elif name == "energy":
         per = spec.n_elec * 5 * ld * tw + (spec.n_up ** 2 + spec.n_dn ** 2) * tw + 24 * spec.n_elec
         out = {"bound": "hbm", "unit": "GB/s", "peak": hbm,

@@ -248,7 +248,8 @@ typedef enum {
   QMC_K_VGL_CURRENT = 5,  /* orbitals at the current positions (set-up) */
   QMC_K_ACCUMULATE = 6,   /* FP64 reductions over walkers */
   QMC_K_FLUSH = 7,        /* batched application of the delayed-update windows */
-  QMC_K_REFINE = 8,       /* batched single-precision re-inversion (Newton step) */
+  QMC_K_REFINE = 8,       /* single-precision re-inversion: error-free residual R = I - A X */
+  QMC_K_REFINE_UPDATE = 9,/* single-precision re-inversion: X <- X + X R, commit or FP64 fallback */
   QMC_NKERNELS = 10
 } qmc_kernel;
 

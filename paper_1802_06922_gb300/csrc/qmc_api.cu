@@ -328,7 +328,7 @@ void free_walkers(qmc_walkers_s* w) {
   void* ptrs[] = {W.pos, W.binv, W.vgl, W.logdet, W.sgn, W.wid, W.weight, W.e_loc, W.log_psi,
                   W.n_acc, W.acc_since, W.scratch64, W.err, w->d_P, w->d_prop, w->d_out,
                   w->d_nacc, w->d_forced, W.win_phi, W.win_u, W.win_cinv, W.win_row, W.win_m,
-                  W.refine_max};
+                  W.refine_max, W.rscale};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -396,6 +396,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.win_row, nw * (size_t)s->d.delay_k * sizeof(int)},
       {(void**)&W.win_m, nw * sizeof(int)},
       {(void**)&W.refine_max, nw * sizeof(float)},
+      {(void**)&W.rscale, nw * 4 * (size_t)W.ld_v * sizeof(int)},
   };
   for (auto& a : allocs) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -501,9 +502,9 @@ qmc_status sweep_once(qmc_walkers_s* w, const WalkParams& W, bool fixed_node, cu
         if (period > 0) {
           w->since_moves[spin] += e1 - e0;
           if (w->since_moves[spin] >= period) {
-            Bracket b(w, st, QMC_K_REFINE);
-            QMC_CUDA(s->tw->refine(P, W, spin, st));
-            w->launches += 2;   // residual, update and commit kernels
+            { Bracket b(w, st, QMC_K_REFINE); QMC_CUDA(s->tw->refine(P, W, spin, 0, st)); }
+            { Bracket b(w, st, QMC_K_REFINE_UPDATE); QMC_CUDA(s->tw->refine(P, W, spin, 1, st)); }
+            w->launches += 2;   // row scales + residual, update + commit
             w->since_moves[spin] = 0;
           }
         }

@@ -70,6 +70,7 @@ struct WalkParams {
   int* win_row;        // [W][kc]       row (electron index within the spin block)
   int* win_m;          // [W]           fill
   float* refine_max;   // [W]           max |I - A X| of the last refinement
+  int* rscale;         // [W][2][2][ld_v] power-of-two exponents of the rows of A and X
   const int* n_live;   // optional device count: blocks of walkers >= *n_live return at once
 };
 

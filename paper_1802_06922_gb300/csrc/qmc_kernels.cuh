@@ -110,7 +110,7 @@ __device__ __forceinline__ void vgl_warp(const SysParams& S, const double r[3], 
 // VGL of every electron of every walker at its current position (walker set-up and
 // re-inversion): one warp per (walker, electron, 32V-orbital chunk).
 template <class TT, class TW>
-__global__ void __launch_bounds__(256) k_vgl_current(SysParams S, WalkParams Wk) {
+__global__ void __launch_bounds__(256, sizeof(TT) == 8 ? 1 : 2) k_vgl_current(SysParams S, WalkParams Wk) {
   constexpr int V = TabVec<TT>::V;
   const int chunks = (Wk.ld_v + 32 * V - 1) / (32 * V);
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -148,7 +148,7 @@ static __global__ void k_proposals(SysParams S, WalkParams Wk, uint32_t t, int e
 
 // VGL at every proposed position of a chunk: out[w][e-e0][5][ld_v].
 template <class TT, class TW>
-__global__ void __launch_bounds__(256) k_vgl_proposals(SysParams S, WalkParams Wk, int e0, int e1,
+__global__ void __launch_bounds__(256, sizeof(TT) == 8 ? 1 : 2) k_vgl_proposals(SysParams S, WalkParams Wk, int e0, int e1,
                                                       const Prop* __restrict__ prop,
                                                       TW* __restrict__ out) {
   constexpr int V = TabVec<TT>::V;

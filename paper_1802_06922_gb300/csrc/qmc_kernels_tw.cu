@@ -61,19 +61,27 @@ cudaError_t flush(const SysParams& S, const WalkParams& W, int spin, cudaStream_
 }
 
 template <class TW>
-cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, cudaStream_t st) {
+cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, cudaStream_t st) {
   const int ns = spin ? S.n_dn : S.n_up;
   if (ns == 0) return cudaSuccess;
   if constexpr (sizeof(TW) == 4) {
-    const int nt64 = (ns + 63) / 64;
-    const dim3 grid(W.n_w, nt64 * nt64);
-    k_refine_residual<TW><<<grid, kThreads, 0, st>>>(S, W, spin);
+    if (part == 1) {
+      const int nt64 = (ns + 63) / 64;
+      k_refine_update<TW><<<dim3(W.n_w, nt64 * nt64), kThreads, 0, st>>>(S, W, spin);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      k_refine_commit<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
+      return cudaGetLastError();
+    }
+    // error-free residual on the tensor cores (power-of-two row scales first)
+    k_refine_scales<TW><<<dim3(W.n_w, 2), kThreads, 0, st>>>(S, W, spin);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_refine_update<TW><<<grid, kThreads, 0, st>>>(S, W, spin);
-    e = cudaGetLastError();
+    const size_t smem = refine_tc_smem_bytes();
+    e = cudaFuncSetAttribute(k_refine_residual_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_refine_commit<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
+    const int nt = (ns + kRsRows - 1) / kRsRows;
+    k_refine_residual_tc<<<dim3(W.n_w, nt * nt), kThreads, smem, st>>>(S, W, spin);
     return cudaGetLastError();
   } else {
     // double precision needs no refinement: FP64 Gauss-Jordan of that spin block

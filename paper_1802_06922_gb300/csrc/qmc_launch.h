@@ -18,7 +18,8 @@ struct TwLaunch {
   cudaError_t (*invert_batch)(const void* A, void* Binv, double* logdet, double* sign, int n,
                               int batch, double* work, cudaStream_t);
   cudaError_t (*flush)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
-  cudaError_t (*refine)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
+  // part 0: row scales + error-free residual; part 1: X <- X + X R, commit or FP64 fallback
+  cudaError_t (*refine)(const SysParams&, const WalkParams&, int spin, int part, cudaStream_t);
   cudaError_t (*dmc_branch)(const SysParams&, const WalkParams&, const DmcParams&, int parity,
                             uint32_t step, cudaStream_t);
   cudaError_t (*dmc_copy)(const SysParams&, const WalkParams& src, const WalkParams& dst,

@@ -325,4 +325,273 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   if (warp == 0) tc::tmem_dealloc(tmem, kTcCols);
 }
 
+// =============================================================================
+// Error-free residual R = I - A X of the single-precision inverse on the tensor cores.
+//
+// The re-inversion of the single-precision forms is one Newton step X <- X + X R (see
+// refine_inverse). R must be accurate to about 2^-24 although the sums sum_j A_ej X_jf
+// run through terms up to ~10^4 times larger than their result (random plane-wave
+// Slater matrices have condition numbers 10^3..10^5), so FP32 or 3xTF32 products are not
+// enough. Here each row of A (electron e) and each row of Binv (f; Binv[f][j] = X[j][f])
+// is scaled by a power of two 2^E so that |x| < 1 and cut into kRsSlices slices of
+// kRsBits bits (RN splitting; slice i holds an integer times 2^(-kRsBits i), exact in
+// BF16). The product of slice i of A with slice j of X is a sum of K products that are
+// integers in units of 2^(-kRsBits (i+j)) and bounded by K 2^(2 kRsBits) <= 2^23 for K <= 512,
+// so an FP32 accumulator sums it without rounding. The pairs of level i+j = 2 and 3 carry
+// the cancellation and get one exact accumulator each; the pairs of levels 4..kRsMaxLevel
+// (magnitude below 2^-14 of the first) share a third, ordinary FP32 accumulator. The
+// epilogue forms R = delta - 2^(E_e+F_f) (L2 + L3 + L4+) with error-free (TwoSum) steps.
+// This is an Ozaki-type splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication"), restated
+// for BF16 tcgen05 MMAs with FP32 accumulation.
+// =============================================================================
+constexpr int kRsRows = 128;      // M and N of the output tile
+constexpr int kRsK = 32;          // BF16 K elements staged per chunk
+constexpr int kRsSlices = 6;
+constexpr int kRsBits = 7;
+constexpr int kRsMaxLevel = 7;    // slice pairs (i, j) with i + j <= kRsMaxLevel
+constexpr int kRsTile = kRsRows * kRsK;            // BF16 elements of one slice tile
+
+__host__ __device__ inline size_t refine_tc_smem_bytes() {
+  return (size_t)2 * 2 * kRsSlices * kRsTile * 2 + 2 * kRsRows * sizeof(int) + 64;
+}
+
+// Power-of-two exponent E of every row of A (operand 0: orbital values of the spin
+// block's electrons) and of Binv (operand 1) with max_j |x_j| < 2^E; 0 for a zero row.
+// One warp per row. rscale[(2 w + spin) * 2 ld_v + operand * ld_v + row].
+template <class TW>
+__global__ void __launch_bounds__(256) k_refine_scales(SysParams S, WalkParams Wk, int spin) {
+  const int w = blockIdx.x, op = blockIdx.y;
+  if (Wk.n_live && w >= *Wk.n_live) return;
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int first = spin ? S.n_up : 0;
+  const int ld5 = 5 * Wk.ld_v;
+  const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
+  const float* B = static_cast<const float*>(Wk.binv) +
+                   (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  int* out = Wk.rscale + (size_t)(2 * w + spin) * 2 * Wk.ld_v + op * Wk.ld_v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int r = warp; r < ns; r += nwarp) {
+    const float* row = op == 0 ? VG + (size_t)r * ld5 : B + (size_t)r * ns;
+    float mx = 0.f;
+    for (int j = lane; j < ns; j += 32) mx = fmaxf(mx, fabsf(row[j]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      int ex = 0;
+      if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);   // mx = m 2^ex, m in [0.5, 1)
+      out[r] = max(-60, min(60, ex));               // 2^(E_e + F_f) stays a normal float
+    }
+  }
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// Splits 16 consecutive K elements of one row into the kRsSlices BF16 slice tiles.
+__device__ __forceinline__ void stage_slices16(const float (&x)[16], float inv_scale,
+                                               __nv_bfloat16* tiles, int r, int k) {
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    float rem[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) rem[t] = x[8 * g + t] * inv_scale;   // exact: power of two
+    const uint32_t off = tc::tile_offset(r, k + 8 * g, kRsK * 2 / 16, 2) >> 1;
+#pragma unroll
+    for (int i = 1; i <= kRsSlices; ++i) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int t = 0; t < 8; t += 2) {
+        float q2[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float tt = rem[t + u] * float(1 << kRsBits);
+          const float q = rintf(tt);
+          rem[t + u] = tt - q;                                        // exact, |rem| <= 1/2
+          q2[u] = q * pow2f(-kRsBits * i);                            // exact
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(q2[0], q2[1]); // exact: <= 8 bits
+        pk[t / 2] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      *reinterpret_cast<uint4*>(tiles + (size_t)(i - 1) * kRsTile + off) =
+          make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+  }
+}
+
+// R[e][f] = delta_ef - sum_j A[e][j] X[j][f] for the 128 x 128 tile (blockIdx.y) of walker
+// w's spin block, into the walker's work area (as k_refine_residual), with max |R| into
+// refine_max[w]. Chunks of 32 K elements are loaded into registers one chunk ahead,
+// split into BF16 slices in one of two shared-memory stages, and multiplied (one thread
+// issues the 21 slice-pair products per 16-wide K step) while the next chunk is split.
+__global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, WalkParams Wk, int spin) {
+  extern __shared__ __align__(1024) char smem_rt[];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tbase;
+  const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int first = spin ? S.n_up : 0;
+  const int nt = (ns + kRsRows - 1) / kRsRows;
+  const int e0 = (blockIdx.y / nt) * kRsRows, f0 = (blockIdx.y % nt) * kRsRows;
+  const int ld5 = 5 * Wk.ld_v;
+  const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
+  const float* B = static_cast<const float*>(Wk.binv) +
+                   (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  float* Rg = reinterpret_cast<float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
+  const int* sc = Wk.rscale + (size_t)(2 * w + spin) * 2 * Wk.ld_v;
+  __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(smem_rt);   // [stage][operand][slice]
+  int* escA = reinterpret_cast<int*>(tiles + (size_t)2 * 2 * kRsSlices * kRsTile);
+  int* escB = escA + kRsRows;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < kRsRows; i += blockDim.x) {
+    escA[i] = (e0 + i < ns) ? sc[e0 + i] : 0;
+    escB[i] = (f0 + i < ns) ? sc[Wk.ld_v + f0 + i] : 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tbase;
+  // thread -> row lr of both operand tiles, 16 consecutive K elements lk..
+  const int lr = tid >> 1, lk = (tid & 1) * 16;
+  const float* arow = VG + (size_t)(e0 + lr) * ld5;
+  const float* brow = B + (size_t)(f0 + lr) * ns;
+  const bool a_ok = e0 + lr < ns, b_ok = f0 + lr < ns;
+  const bool bvec = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+  const bool avec = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(VG) & 15) == 0 && (ld5 & 3) == 0;
+  const float inv_a = pow2f(-escA[lr]), inv_b = pow2f(-escB[lr]);
+  float xa[16], xb[16];
+  auto load_row = [&](const float* row, bool ok, bool vec, int j, float (&x)[16]) {
+    if (vec) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok && j + 4 * t < ns) v = *reinterpret_cast<const float4*>(row + j + 4 * t);
+        x[4 * t] = v.x; x[4 * t + 1] = v.y; x[4 * t + 2] = v.z; x[4 * t + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) x[t] = (ok && j + t < ns) ? row[j + t] : 0.f;
+    }
+  };
+  const int nch = (ns + kRsK - 1) / kRsK;
+  const uint32_t idesc = tc::instr_desc(tc::kFmtBF16, kRsRows, kRsRows);
+  const int kcols = kRsK * 2 / 16;                   // 16-byte K columns per slice tile
+  bool ok = true;
+  load_row(arow, a_ok, avec, lk, xa);
+  load_row(brow, b_ok, bvec, lk, xb);
+  for (int c = 0; c < nch; ++c) {
+    const int st = c & 1;
+    if (c >= 2) {                                    // stage st was read by chunk c - 2
+      ok = tc::mbar_wait(&bar[st], (uint32_t)(((c - 2) >> 1) & 1), kTcWaitPolls) && ok;
+    }
+    __nv_bfloat16* ta = tiles + (size_t)(st * 2 + 0) * kRsSlices * kRsTile;
+    __nv_bfloat16* tb = tiles + (size_t)(st * 2 + 1) * kRsSlices * kRsTile;
+    stage_slices16(xa, inv_a, ta, lr, lk);
+    stage_slices16(xb, inv_b, tb, lr, lk);
+    tc::fence_async_smem();
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    if (c + 1 < nch) {
+      load_row(arow, a_ok, avec, (c + 1) * kRsK + lk, xa);
+      load_row(brow, b_ok, bvec, (c + 1) * kRsK + lk, xb);
+    }
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll 1
+      for (int i = 1; i <= kRsSlices; ++i)
+#pragma unroll 1
+        for (int j = 1; i + j <= kRsMaxLevel; ++j) {
+          const int lev = i + j;
+          const int acc = lev == 2 ? 0 : (lev == 3 ? 1 : 2);
+          // the first product into each accumulator, pairs (1,1), (1,2), (1,3), overwrites it
+          const bool first_pair = (i == 1) && (j == acc + 1);
+#pragma unroll
+          for (int ks = 0; ks < kRsK / 16; ++ks) {
+            // a 16-wide BF16 K step spans two 16-byte core-matrix columns (256 bytes)
+            const uint64_t da = tc::smem_desc(ta + (size_t)(i - 1) * kRsTile + ks * 128, 128, kcols * 128);
+            const uint64_t db = tc::smem_desc(tb + (size_t)(j - 1) * kRsTile + ks * 128, 128, kcols * 128);
+            const uint32_t accum = (c == 0 && ks == 0 && first_pair) ? 0u : 1u;
+            tc::mma_f16(tmem + (uint32_t)(acc * kRsRows), da, db, idesc, accum);
+          }
+        }
+      tc::mma_commit(&bar[st]);
+    }
+  }
+  if (ok) {
+    const int cl = nch - 1;                          // the last commit covers every MMA
+    ok = tc::mbar_wait(&bar[cl & 1], (uint32_t)((cl >> 1) & 1), kTcWaitPolls);
+  }
+  ok = __syncthreads_and(ok);
+  tc::fence_after();
+  float rmax = 0.f;
+  if (ok) {
+    const int q4 = warp & 3, h2 = warp >> 2;
+    const int r = q4 * 32 + lane, e = e0 + r;
+    const int ea = escA[r];
+    const bool rvec = (ns & 3) == 0;
+#pragma unroll 1
+    for (int g = 0; g < kRsRows / 2; g += 16) {
+      const int cb = h2 * (kRsRows / 2) + g;        // first column of this group in the tile
+      float v0[16], v1[16], v2[16];
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + cb;
+      tc::tmem_ld16(ta, v0);
+      tc::tmem_ld16(ta + kRsRows, v1);
+      tc::tmem_ld16(ta + 2 * kRsRows, v2);
+      float out[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int f = f0 + cb + t;
+        const float sc2 = pow2f(ea + escB[cb + t]);
+        float hi, lo, er;
+        two_sum(e == f ? 1.f : 0.f, -(sc2 * v0[t]), hi, lo);
+        two_sum(hi, -(sc2 * v1[t]), hi, er);
+        lo = __fadd_rn(lo, er);
+        two_sum(hi, -(sc2 * v2[t]), hi, er);
+        lo = __fadd_rn(lo, er);
+        out[t] = __fadd_rn(hi, lo);
+      }
+      if (e < ns) {
+        float* dst = Rg + (size_t)e * ns + f0 + cb;
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (f0 + cb + t < ns) rmax = fmaxf(rmax, isfinite(out[t]) ? fabsf(out[t]) : INFINITY);
+        if (rvec && f0 + cb + 16 <= ns) {
+#pragma unroll
+          for (int t = 0; t < 16; t += 4)
+            *reinterpret_cast<float4*>(dst + t) = make_float4(out[t], out[t + 1], out[t + 2], out[t + 3]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (f0 + cb + t < ns) dst[t] = out[t];
+        }
+      }
+    }
+  }
+  if (!ok) {
+    rmax = INFINITY;                                 // falls back to the FP64 re-inversion
+    if (tid == 0) atomicOr(Wk.err, kErrTimeout);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  if (lane == 0) atomicMax(reinterpret_cast<int*>(Wk.refine_max + w), __float_as_int(rmax));
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 }  // namespace qmcgb
