@@ -171,6 +171,8 @@ extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_
   P.n_ion = d.n_ion;
   P.L = d.L;
   P.Lf = (float)d.L;
+  P.invL = 1.0 / d.L;
+  P.invLf = (float)(1.0 / d.L);
   P.ion_Z = d.ion_Z;
   P.ion_Zf = (float)d.ion_Z;
   P.kappa = d.kappa;

@@ -61,6 +61,9 @@ __device__ __forceinline__ double trint(double x) { return rint(x); }
 __device__ __forceinline__ float trint(float x) { return rintf(x); }
 template <class T>
 __device__ __forceinline__ T min_image(T d, T L) { return d - L * trint(d / L); }
+// The same with the reciprocal of L precomputed (no division in the pair loops).
+template <class T>
+__device__ __forceinline__ T min_image(T d, T L, T invL) { return d - L * trint(d * invL); }
 
 // ------------------------------------------------------------------ B-spline weights
 // Uniform cubic B-spline weights of the nodes i-1..i+2 at fractional position t, and
@@ -92,6 +95,7 @@ template <> struct Cst<double> {
   __device__ static __forceinline__ double knot(const SysParams& S, int f, int m) { return S.jp[f][m]; }
   __device__ static __forceinline__ double rc(const SysParams& S, int f) { return S.jrc[f]; }
   __device__ static __forceinline__ double L(const SysParams& S) { return S.L; }
+  __device__ static __forceinline__ double invL(const SysParams& S) { return S.invL; }
   __device__ static __forceinline__ const double* ions(const SysParams& S) { return S.ions; }
   __device__ static __forceinline__ double invd(const SysParams& S, int d) { return S.inv_delta[d]; }
   __device__ static __forceinline__ double Z(const SysParams& S) { return S.ion_Z; }
@@ -101,6 +105,7 @@ template <> struct Cst<float> {
   __device__ static __forceinline__ float knot(const SysParams& S, int f, int m) { return S.jpf[f][m]; }
   __device__ static __forceinline__ float rc(const SysParams& S, int f) { return S.jrcf[f]; }
   __device__ static __forceinline__ float L(const SysParams& S) { return S.Lf; }
+  __device__ static __forceinline__ float invL(const SysParams& S) { return S.invLf; }
   __device__ static __forceinline__ const float* ions(const SysParams& S) { return S.ionsf; }
   __device__ static __forceinline__ float invd(const SysParams& S, int d) { return S.inv_deltaf[d]; }
   __device__ static __forceinline__ float Z(const SysParams& S) { return S.ion_Zf; }
@@ -138,7 +143,7 @@ __device__ __forceinline__ void jastrow_u(const SysParams& S, int f, T r, T& u, 
 template <class T>
 struct JastrowTab {
   int M[3];
-  T rc[3], scale[3];
+  T rc[3], rc2[3], scale[3];
   T p[3][kMaxKnots + 4];
 };
 
@@ -152,6 +157,7 @@ __device__ __forceinline__ void jastrow_tab_fill(const SysParams& S, JastrowTab<
     const int f = threadIdx.x;
     J.M[f] = S.jM[f];
     J.rc[f] = Cst<T>::rc(S, f);
+    J.rc2[f] = Cst<T>::rc(S, f) * Cst<T>::rc(S, f);
     J.scale[f] = S.jM[f] ? T(S.jM[f]) / Cst<T>::rc(S, f) : T(0);
   }
 }
@@ -177,6 +183,20 @@ __device__ __forceinline__ void jastrow_eval(const JastrowTab<T>& J, int f, T r,
   }
   du *= scale;
   d2u *= scale * scale;
+}
+
+// u(r) alone, from the squared distance: 0 at and beyond the cutoff without a square
+// root (a Metropolis ratio needs no derivatives).
+template <class T>
+__device__ __forceinline__ T jastrow_value_r2(const JastrowTab<T>& J, int f, T r2) {
+  if (!(r2 < J.rc2[f])) return T(0);
+  const T s = sqrt(r2) * J.scale[f];
+  int i = (int)tfloor(s);
+  if (i < 0) i = 0;
+  const T t = s - T(i), t2 = t * t, t3 = t2 * t, omt = T(1) - t;
+  const T* p = J.p[f] + i;
+  return (p[0] * (omt * omt * omt) + p[1] * (T(3) * t3 - T(6) * t2 + T(4)) +
+          p[2] * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + p[3] * t3) * T(1.0 / 6.0);
 }
 
 // Yukawa pair potential exp(-kappa r)/r for r < L/2 (stand-in for v_ee, v_eI).

@@ -35,6 +35,8 @@ struct SysParams {
   double inv_delta[3]; // grid points per bohr along x, y, z (n / L)
   float inv_deltaf[3];
   float Lf, ion_Zf, kappaf;
+  double invL;         // 1 / L
+  float invLf;
   double ion_Z, kappa;
   int with_potential;
   double v_ion_ion;    // Z^2 sum_{I<J} v(R_IJ), a constant

@@ -642,7 +642,7 @@ template <> __device__ __forceinline__ float texp<float>(float x) { return expf(
 // in the kernel (table type TT) because the proposal depends on the current inverse; the
 // acceptance includes the Green's-function ratio of Eq. pmc:g_driftdiffusion.
 template <class TW, class TT, bool kFixedNode, bool kDrift>
-__global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint32_t t, int e0,
+__global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, uint32_t t, int e0,
                                               int e1, int kc, const TW* __restrict__ Pv,
                                               const Prop* __restrict__ prop, int p_e0, int p_n,
                                               int reinv_period, int reinv_on_acc, int ext_flush) {
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
   const int spin = e0 >= S.n_up ? 1 : 0;
   const int first = spin ? S.n_up : 0;
   const int ns = spin ? S.n_dn : S.n_up;
-  const TW Lw = Cst<TW>::L(S);
+  const TW Lw = Cst<TW>::L(S), iLw = Cst<TW>::invL(S);
   const TW* ionw = Cst<TW>::ions(S);
   TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
           (spin ? S.n_up * S.n_up : 0);
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         if (jt.M[f] == 0) continue;
         TW dq[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dq[c] = min_image<TW>(ro[c] - q[c], Lw);
+        for (int c = 0; c < 3; ++c) dq[c] = min_image<TW>(ro[c] - q[c], Lw, iLw);
         const TW r = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
         TW u, du, d2u;
         jastrow_eval<TW>(jt, f, r, u, du, d2u);
@@ -813,7 +813,37 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       acc[0] = a0; acc[1] = a1; acc[2] = a2; acc[3] = a3; acc[4] = a4;
     }
     // Jastrow difference and gradient at r'
-    {
+    if (!kDrift && !Wk.trace) {
+      // Metropolis: the ratio needs Delta J only (no derivatives, no root beyond r_c)
+      const TW rn[3] = {sm.sc[0], sm.sc[1], sm.sc[2]};
+      const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+      TW dj = 0;
+      const int ntot = n_e + S.n_ion;
+      for (int j = tid; j < ntot; j += nt) {
+        if (j == e) continue;
+        TW q[3];
+        int f;
+        if (j < n_e) {
+          q[0] = sm.posw[j]; q[1] = sm.posw[n_e + j]; q[2] = sm.posw[2 * n_e + j];
+          f = ((j >= S.n_up) == (e >= S.n_up)) ? 1 : 2;
+        } else {
+          const int I = j - n_e;
+          q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
+          f = 0;
+        }
+        if (jt.M[f] == 0) continue;
+        TW rn2 = 0, ro2 = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const TW dn = min_image<TW>(rn[c] - q[c], Lw, iLw);
+          const TW dq = min_image<TW>(ro[c] - q[c], Lw, iLw);
+          rn2 += dn * dn;
+          ro2 += dq * dq;
+        }
+        dj += jastrow_value_r2<TW>(jt, f, rn2) - jastrow_value_r2<TW>(jt, f, ro2);
+      }
+      acc[5] = dj; acc[6] = 0; acc[7] = 0; acc[8] = 0;
+    } else {
       const TW rn[3] = {sm.sc[0], sm.sc[1], sm.sc[2]};
       const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
       TW dj = 0, gx = 0, gy = 0, gz = 0;
@@ -834,8 +864,8 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         TW dn[3], dq[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          dn[c] = min_image<TW>(rn[c] - q[c], Lw);
-          dq[c] = min_image<TW>(ro[c] - q[c], Lw);
+          dn[c] = min_image<TW>(rn[c] - q[c], Lw, iLw);
+          dq[c] = min_image<TW>(ro[c] - q[c], Lw, iLw);
         }
         const TW rnn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
         const TW roo = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
@@ -866,23 +896,24 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
       sm.red[warp * 11 + 10] = ac;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
+      // lane k < 9 adds slot k of the warp partials (lanes 0 and 4 with their compensation)
+      constexpr int kNW = kThreads / 32;
+      TW v = TW(0);
+      if (lane == 0 || lane == 4) {
+        const int kq = lane == 0 ? 9 : 10;
+        TW sv = sm.red[lane], cv = sm.red[kq];
+#pragma unroll
+        for (int q = 1; q < kNW; ++q) comp_merge(sv, cv, sm.red[q * 11 + lane], sm.red[q * 11 + kq]);
+        v = sv + cv;
+      } else if (lane < 9) {
+#pragma unroll
+        for (int q = 0; q < kNW; ++q) v += sm.red[q * 11 + lane];
+      }
       TW tot[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        TW v = TW(0);
-        for (int q = 0; q < nw; ++q) v += sm.red[q * 11 + k];
-        tot[k] = v;
-      }
-      {
-        TW s0 = sm.red[0], c0 = sm.red[9], s4 = sm.red[4], c4 = sm.red[10];
-        for (int q = 1; q < nw; ++q) {
-          comp_merge(s0, c0, sm.red[q * 11], sm.red[q * 11 + 9]);
-          comp_merge(s4, c4, sm.red[q * 11 + 4], sm.red[q * 11 + 10]);
-        }
-        tot[0] = s0 + c0;
-        tot[4] = s4 + c4;
-      }
+      for (int k = 0; k < 9; ++k) tot[k] = __shfl_sync(0xffffffffu, v, k);
+      if (lane == 0) {
       const TW R = tot[0], dJ = tot[5];
       const double u = sm.propb[4 * cur + 3];
       const bool ok = (R != TW(0)) && isfinite(R);
@@ -931,6 +962,7 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         sm.sc[3] = R;
         sm.sc[4] = tot[4];        // phi' . Binv0[e]: corner of the bordered C
       }
+      }
     }
     __syncthreads();
     const bool accept = sm.flag[0] != 0;
@@ -955,11 +987,16 @@ __global__ void __launch_bounds__(256) k_sweep(SysParams S, WalkParams Wk, uint3
         for (int l = 0; l < m; ++l) comp_fma(y, yc, sm.crow[l], sm.cinv[l * kc + tid]);
         sm.yvec[tid] = y + yc;
       }
-      if (tid == 0) {
+      if (warp == nw - 1) {
         // Schur complement of the bordered C from its own entries: a - crow . C^-1 d
-        TW sv = sm.sc[4], sc2 = TW(0);
-        for (int l = 0; l < m; ++l) comp_fma(sv, sc2, -sm.crow[l], sm.zvec[l]);
-        sm.sc[5] = sv + sc2;
+        TW sv = TW(0), sc2 = TW(0);
+        for (int l = lane; l < m; l += 32) comp_fma(sv, sc2, -sm.crow[l], sm.zvec[l]);
+        warp_sum_comp(sv, sc2);
+        if (lane == 0) {
+          TW a = sm.sc[4], ac2 = TW(0);
+          comp_merge(a, ac2, sv, sc2);
+          sm.sc[5] = a + ac2;
+        }
       }
       __syncthreads();
       // C^-1 of the bordered matrix
@@ -1309,7 +1346,7 @@ __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk
   const double* P = Wk.pos + (size_t)w * 3 * n_e;
   for (int i = threadIdx.x; i < 3 * n_e; i += blockDim.x) posw[i] = (TW)P[i];
   __syncthreads();
-  const TW Lw = Cst<TW>::L(S), kap = Cst<TW>::kappa(S), Zw = Cst<TW>::Z(S);
+  const TW Lw = Cst<TW>::L(S), iLw = Cst<TW>::invL(S), kap = Cst<TW>::kappa(S), Zw = Cst<TW>::Z(S);
   const TW* ionw = Cst<TW>::ions(S);
   const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
   const TW* Bw = static_cast<const TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn);
@@ -1350,7 +1387,7 @@ __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk
         }
         TW dd[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dd[c] = min_image<TW>(ri[c] - q[c], Lw);
+        for (int c = 0; c < 3; ++c) dd[c] = min_image<TW>(ri[c] - q[c], Lw, iLw);
         const TW r = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
         const bool once = (j >= n_e) || (j > i);
         if (S.with_potential && once) {
