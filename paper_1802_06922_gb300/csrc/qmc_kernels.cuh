@@ -1187,68 +1187,9 @@ static __global__ void k_window_reset(WalkParams Wk) {
 
 // =============================================================================
 // Batched single-precision re-inversion (the refinement of refine_inverse as separate
-// kernels over all walkers): residual tiles with Dot2, then X <- X + X R.
+// kernels over all walkers): the error-free residual R = I - A X comes from the tensor
+// cores (k_refine_residual_tc), then X <- X + X R and the commit below.
 // =============================================================================
-template <class TW>
-__global__ void __launch_bounds__(256) k_refine_residual(SysParams S, WalkParams Wk, int spin) {
-  __shared__ float As[32 * 64], Bs[32 * 64];
-  const int w = blockIdx.x;
-  if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
-  const int ns = spin ? S.n_dn : S.n_up;
-  const int first = spin ? S.n_up : 0;
-  const int nt64 = (ns + 63) / 64;
-  const int te = (blockIdx.y / nt64) * 64, tf = (blockIdx.y % nt64) * 64;
-  const int ld5 = 5 * Wk.ld_v;
-  const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
-  const float* B = static_cast<const float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-                   (spin ? S.n_up * S.n_up : 0);
-  float* Rg = reinterpret_cast<float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  float P[4][4], E[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) P[i][j] = E[i][j] = 0.f;
-  for (int k0 = 0; k0 < ns; k0 += 32) {
-    __syncthreads();
-    for (int i = tid; i < 64 * 32; i += blockDim.x) {
-      const int r = i & 63, kk = i >> 6, j = k0 + kk;
-      const int e = te + r, f = tf + r;
-      As[kk * 64 + r] = (e < ns && j < ns) ? VG[(size_t)e * ld5 + j] : 0.f;
-      Bs[kk * 64 + r] = (f < ns && j < ns) ? B[(size_t)f * ns + j] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < 32; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = As[kk * 64 + ty + 16 * i];
-        b[i] = Bs[kk * 64 + tx + 16 * i];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dot2_step(a[i], b[j], P[i][j], E[i][j]);
-    }
-  }
-  float rmax = 0.f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int e = te + ty + 16 * i, f = tf + tx + 16 * j;
-      if (e < ns && f < ns) {
-        const float r = __fsub_rn(__fsub_rn(e == f ? 1.f : 0.f, P[i][j]), E[i][j]);
-        Rg[(size_t)e * ns + f] = r;
-        rmax = fmaxf(rmax, isfinite(r) ? fabsf(r) : INFINITY);
-      }
-    }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-  if ((tid & 31) == 0) atomicMax(reinterpret_cast<int*>(Wk.refine_max + w), __float_as_int(rmax));
-}
-
 // X <- X + X R: Bn[e][j] = Binv[e][j] + sum_f R[f][e] Binv[f][j] into the second half of
 // the walker's work area; walkers whose residual exceeded kRefineMax are skipped (they
 // take the FP64 re-inversion).

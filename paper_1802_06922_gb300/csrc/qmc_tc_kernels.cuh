@@ -425,8 +425,8 @@ __device__ __forceinline__ void stage_slices16(const float (&x)[16], float inv_s
 }
 
 // R[e][f] = delta_ef - sum_j A[e][j] X[j][f] for the 128 x 128 tile (blockIdx.y) of walker
-// w's spin block, into the walker's work area (as k_refine_residual), with max |R| into
-// refine_max[w]. Chunks of 32 K elements are loaded into registers one chunk ahead,
+// w's spin block, row-major [e][f] into the first N_s^2 floats of the walker's FP64 work
+// area (read by k_refine_update), with max |R| into refine_max[w]. Chunks of 32 K elements are loaded into registers one chunk ahead,
 // split into BF16 slices in one of two shared-memory stages, and multiplied (one thread
 // issues the 21 slice-pair products per 16-wide K step) while the next chunk is split.
 __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, WalkParams Wk, int spin) {

@@ -158,9 +158,10 @@ def test_orbitals_and_inverse_at_setup(precision):
 
 
 def test_fp32_refinement_reaches_storage_accuracy():
-    """The single-precision re-inversion (one Newton step with a Dot2 residual) leaves an
-    inverse whose error is set by FP32 storage, not by the condition number or the number
-    of rank-k updates since the last re-inversion."""
+    """The single-precision re-inversion (one Newton step with the error-free residual
+    computed from BF16 slice products on the tensor cores) leaves an inverse whose error is
+    set by FP32 storage, not by the condition number or the number of rank-k updates since
+    the last re-inversion."""
     inputs = build_inputs(small_spec(64, 64, grid=12, n_orb=72), n_walkers=2)
     errs = {}
     for period in (0, 16):
