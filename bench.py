@@ -208,14 +208,14 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
                "per_unit": f"{pairs} slice pairs x 2*N_s^3 = {per} BF16 tensor flop per walker and "
                            f"spin block (peak: measured cuBLAS BF16 burst)"}
     elif name == "refine_update":
-        # X <- X + X R on the FP32 pipe: N_s^3 FMA = 2 N_s^3 flop
-        per = 2 * ns ** 3
-        peak = 2 * N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
-        out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+        # X <- X + X R on tcgen05 with 3xTF32 operands: 3 x 2 N_s^3 TF32 flop
+        per = 3 * 2 * ns ** 3
+        peak = peaks.get("bf16_tflops", 1899.6) * (1.1 / 2.25)
+        out = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                "achieved": per * spec.n_walkers / sec / 1e12,
-               "kernel": "k_refine_update + k_refine_commit",
-               "per_unit": f"2*N_s^3 = {per} FP32 flop per walker and spin block; peak = 2 x "
-                           f"{N_SM} SMs x {FP32_LANES} lanes x {sm_mhz:.0f} MHz median sampled SM clock"}
+               "kernel": "k_refine_update_tc + k_refine_commit",
+               "per_unit": f"3 x 2*N_s^3 = {per} TF32 tensor flop per walker and spin block (peak: "
+                           f"measured BF16 burst x the nominal TF32/BF16 ratio 1.1/2.25)"}
     elif name == "energy":
         per = spec.n_elec * 5 * ld * tw + (spec.n_up ** 2 + spec.n_dn ** 2) * tw + 24 * spec.n_elec
         out = {"bound": "hbm", "unit": "GB/s", "peak": hbm,

@@ -1190,59 +1190,6 @@ static __global__ void k_window_reset(WalkParams Wk) {
 // kernels over all walkers): the error-free residual R = I - A X comes from the tensor
 // cores (k_refine_residual_tc), then X <- X + X R and the commit below.
 // =============================================================================
-// X <- X + X R: Bn[e][j] = Binv[e][j] + sum_f R[f][e] Binv[f][j] into the second half of
-// the walker's work area; walkers whose residual exceeded kRefineMax are skipped (they
-// take the FP64 re-inversion).
-template <class TW>
-__global__ void __launch_bounds__(256) k_refine_update(SysParams S, WalkParams Wk, int spin) {
-  __shared__ float As[32 * 64], Bs[32 * 64];
-  const int w = blockIdx.x;
-  if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
-  if (!(Wk.refine_max[w] <= kRefineMax)) return;
-  const int ns = spin ? S.n_dn : S.n_up;
-  const int nt64 = (ns + 63) / 64;
-  const int te = (blockIdx.y / nt64) * 64, tj = (blockIdx.y % nt64) * 64;
-  const float* B = static_cast<const float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-                   (spin ? S.n_up * S.n_up : 0);
-  const float* Rg = reinterpret_cast<const float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
-  float* Bn = const_cast<float*>(Rg) + (size_t)ns * ns;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int f0 = 0; f0 < ns; f0 += 32) {
-    __syncthreads();
-    for (int i = tid; i < 64 * 32; i += blockDim.x) {
-      const int c = i & 63, kk = i >> 6, f = f0 + kk;
-      As[kk * 64 + c] = (f < ns && te + c < ns) ? Rg[(size_t)f * ns + te + c] : 0.f;
-      Bs[kk * 64 + c] = (f < ns && tj + c < ns) ? B[(size_t)f * ns + tj + c] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < 32; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = As[kk * 64 + ty + 16 * i];
-        b[i] = Bs[kk * 64 + tx + 16 * i];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int e = te + ty + 16 * i, c = tj + tx + 16 * j;
-      if (e < ns && c < ns) Bn[(size_t)e * ns + c] = B[(size_t)e * ns + c] + acc[i][j];
-    }
-}
-
 // Copies the refined inverse back (walkers that refined), and re-inverts in FP64 the
 // walkers whose residual was too large.
 template <class TW>

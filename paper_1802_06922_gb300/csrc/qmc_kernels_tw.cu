@@ -66,9 +66,13 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
   if (ns == 0) return cudaSuccess;
   if constexpr (sizeof(TW) == 4) {
     if (part == 1) {
-      const int nt64 = (ns + 63) / 64;
-      k_refine_update<TW><<<dim3(W.n_w, nt64 * nt64), kThreads, 0, st>>>(S, W, spin);
-      cudaError_t e = cudaGetLastError();
+      // X <- X + X R on the tensor cores (3xTF32), then the commit
+      const size_t smem = refine_update_tc_smem_bytes();
+      cudaError_t e = cudaFuncSetAttribute(k_refine_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const int nt = (ns + kTcRows - 1) / kTcRows;
+      k_refine_update_tc<<<dim3(W.n_w, nt * nt), kThreads, smem, st>>>(S, W, spin);
+      e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       k_refine_commit<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
       return cudaGetLastError();

@@ -425,8 +425,8 @@ __device__ __forceinline__ void stage_slices16(const float (&x)[16], float inv_s
 }
 
 // R[e][f] = delta_ef - sum_j A[e][j] X[j][f] for the 128 x 128 tile (blockIdx.y) of walker
-// w's spin block, row-major [e][f] into the first N_s^2 floats of the walker's FP64 work
-// area (read by k_refine_update), with max |R| into refine_max[w]. Chunks of 32 K elements are loaded into registers one chunk ahead,
+// w's spin block, stored transposed (Rg[f][e]) in the first N_s^2 floats of the walker's
+// FP64 work area (read by k_refine_update_tc), with max |R| into refine_max[w]. Chunks of 32 K elements are loaded into registers one chunk ahead,
 // split into BF16 slices in one of two shared-memory stages, and multiplied (one thread
 // issues the 21 slice-pair products per 16-wide K step) while the next chunk is split.
 __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, WalkParams Wk, int spin) {
@@ -543,7 +543,6 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
     const int q4 = warp & 3, h2 = warp >> 2;
     const int r = q4 * 32 + lane, e = e0 + r;
     const int ea = escA[r];
-    const bool rvec = (ns & 3) == 0;
 #pragma unroll 1
     for (int g = 0; g < kRsRows / 2; g += 16) {
       const int cb = h2 * (kRsRows / 2) + g;        // first column of this group in the tile
@@ -566,19 +565,14 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
         out[t] = __fadd_rn(hi, lo);
       }
       if (e < ns) {
-        float* dst = Rg + (size_t)e * ns + f0 + cb;
+        // stored transposed, Rg[f][e] = R[e][f]: lanes hold consecutive e (coalesced), and
+        // row e of R^T is contiguous for the update X <- X + X R
 #pragma unroll
         for (int t = 0; t < 16; ++t)
-          if (f0 + cb + t < ns) rmax = fmaxf(rmax, isfinite(out[t]) ? fabsf(out[t]) : INFINITY);
-        if (rvec && f0 + cb + 16 <= ns) {
-#pragma unroll
-          for (int t = 0; t < 16; t += 4)
-            *reinterpret_cast<float4*>(dst + t) = make_float4(out[t], out[t + 1], out[t + 2], out[t + 3]);
-        } else {
-#pragma unroll
-          for (int t = 0; t < 16; ++t)
-            if (f0 + cb + t < ns) dst[t] = out[t];
-        }
+          if (f0 + cb + t < ns) {
+            rmax = fmaxf(rmax, isfinite(out[t]) ? fabsf(out[t]) : INFINITY);
+            Rg[(size_t)(f0 + cb + t) * ns + e] = out[t];
+          }
       }
     }
   }
@@ -592,6 +586,152 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// =============================================================================
+// X <- X + X R of the Newton step on the tensor cores: with Binv = X^T the update reads
+// Bn[e][j] = Binv[e][j] + sum_f R^T[e][f] Binv[f][j], a product of two N_s x N_s matrices per
+// walker and spin. |R| <= 10^-2 (walkers above take the FP64 re-inversion), so 3xTF32
+// operands (error ~2^-22 |R| |X|) keep the result at FP32 storage accuracy. Block
+// (w, y) computes the 128 x 128 tile (e0, j0) into the second half of the walker's work
+// area. A operand: rows e of R^T (K = f contiguous, as the residual kernel stores R).
+// B operand: Binv[f][j0..j0+127], staged transposed into K-major tiles (thread = column j,
+// 16 consecutive f packed into float4 stores). Two shared-memory stages, loads one
+// chunk ahead in registers, MMAs issued by one thread with bounded mbarrier waits.
+// =============================================================================
+constexpr int kUpK = 32;                         // K (f) elements per chunk
+__host__ __device__ inline size_t refine_update_tc_smem_bytes() {
+  return (size_t)2 * 4 * kTcRows * kUpK * 4 + 64;   // 2 stages x {A, B} x {hi, lo}
+}
+
+__global__ void __launch_bounds__(256, 1) k_refine_update_tc(SysParams S, WalkParams Wk, int spin) {
+  extern __shared__ __align__(1024) char smem_u[];
+  __shared__ uint64_t bar[2];
+  __shared__ uint32_t tbase;
+  const int w = blockIdx.x;
+  if (Wk.n_live && w >= *Wk.n_live) return;
+  if (!(Wk.refine_max[w] <= kRefineMax)) return;   // FP64 re-inversion in the commit
+  const int ns = spin ? S.n_dn : S.n_up;
+  const int nt = (ns + kTcRows - 1) / kTcRows;
+  const int e0 = (blockIdx.y / nt) * kTcRows, j0 = (blockIdx.y % nt) * kTcRows;
+  const float* B = static_cast<const float*>(Wk.binv) +
+                   (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  const float* Rt = reinterpret_cast<const float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
+  float* Bn = const_cast<float*>(Rt) + (size_t)ns * ns;
+  float* tiles = reinterpret_cast<float*>(smem_u);  // [stage][Ah, Al, Bh, Bl][128 x 32]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, kTcRows);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tbase;
+  const bool vec = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(Rt) & 15) == 0;
+  // A staging: thread -> row lr (= e0 + lr), 16 consecutive f
+  const int lr = tid >> 1, lk = (tid & 1) * 16;
+  const float* arow = Rt + (size_t)(e0 + lr) * ns;
+  const bool a_ok = e0 + lr < ns;
+  // B staging: thread -> column bj (= j0 + bj), 16 consecutive f starting at bk
+  const int bj = tid & 127, bk = (tid >> 7) * 16;
+  const bool b_ok = j0 + bj < ns;
+  float xa[16], xb[16];
+  auto load = [&](int k0) {
+    const int f = k0 + lk;
+    if (vec) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a_ok && f + 4 * t < ns) v = *reinterpret_cast<const float4*>(arow + f + 4 * t);
+        xa[4 * t] = v.x; xa[4 * t + 1] = v.y; xa[4 * t + 2] = v.z; xa[4 * t + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) xa[t] = (a_ok && f + t < ns) ? arow[f + t] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int fb = k0 + bk + t;
+      xb[t] = (b_ok && fb < ns) ? B[(size_t)fb * ns + j0 + bj] : 0.f;
+    }
+  };
+  const int nch = (ns + kUpK - 1) / kUpK;
+  const int kc1 = kUpK * 4 / 16;
+  const uint32_t idesc = tc::instr_desc(tc::kFmtTF32, kTcRows, kTcRows);
+  bool ok = true;
+  load(0);
+  for (int c = 0; c < nch; ++c) {
+    const int st = c & 1;
+    if (c >= 2) ok = tc::mbar_wait(&bar[st], (uint32_t)(((c - 2) >> 1) & 1), kTcWaitPolls) && ok;
+    float* ah = tiles + (size_t)st * 4 * kTcRows * kUpK;
+    float* al = ah + kTcRows * kUpK;
+    float* bh = al + kTcRows * kUpK;
+    float* bl = bh + kTcRows * kUpK;
+    stage_split16(xa, ah, al, lr, lk, kc1);
+    stage_split16(xb, bh, bl, bj, bk, kc1);
+    tc::fence_async_smem();
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    if (c + 1 < nch) load((c + 1) * kUpK);
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int s = 0; s < kUpK / 8; ++s) {
+        const uint64_t dah = tc::smem_desc(ah + s * 64, 128, kc1 * 128);
+        const uint64_t dal = tc::smem_desc(al + s * 64, 128, kc1 * 128);
+        const uint64_t dbh = tc::smem_desc(bh + s * 64, 128, kc1 * 128);
+        const uint64_t dbl = tc::smem_desc(bl + s * 64, 128, kc1 * 128);
+        tc::mma_tf32(tmem, dah, dbh, idesc, (c == 0 && s == 0) ? 0u : 1u);
+        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
+        tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+      }
+      tc::mma_commit(&bar[st]);
+    }
+  }
+  if (ok) {
+    const int cl = nch - 1;
+    ok = tc::mbar_wait(&bar[cl & 1], (uint32_t)((cl >> 1) & 1), kTcWaitPolls);
+  }
+  ok = __syncthreads_and(ok);
+  tc::fence_after();
+  if (ok) {
+    const int q4 = warp & 3, h2 = warp >> 2;
+    const int e = e0 + q4 * 32 + lane;
+#pragma unroll 1
+    for (int g = 0; g < kTcRows / 2; g += 16) {
+      const int jb = j0 + h2 * (kTcRows / 2) + g;
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + h2 * (kTcRows / 2) + g, v);
+      if (e < ns) {
+        const float* src = B + (size_t)e * ns + jb;
+        float* dst = Bn + (size_t)e * ns + jb;
+        if (vec && jb + 16 <= ns) {
+#pragma unroll
+          for (int t = 0; t < 16; t += 4) {
+            const float4 b4 = *reinterpret_cast<const float4*>(src + t);
+            *reinterpret_cast<float4*>(dst + t) =
+                make_float4(b4.x + v[t], b4.y + v[t + 1], b4.z + v[t + 2], b4.w + v[t + 3]);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 16; ++t)
+            if (jb + t < ns) dst[t] = src[t] + v[t];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(Wk.err, kErrTimeout);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTcRows);
 }
 
 }  // namespace qmcgb
