@@ -199,6 +199,13 @@ __device__ __forceinline__ T jastrow_value_r2(const JastrowTab<T>& J, int f, T r
           p[2] * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + p[3] * t3) * T(1.0 / 6.0);
 }
 
+// 1/sqrt(x) and e^x in the pair loops of the local energy: the hardware approximations
+// (a few ulp) in single precision, the correctly rounded functions in double.
+__device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_w(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float exp_w(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_w(double x) { return exp(x); }
+
 // Yukawa pair potential exp(-kappa r)/r for r < L/2 (stand-in for v_ee, v_eI).
 template <class T>
 __device__ __forceinline__ T yukawa(T r, T kappa, T L) {

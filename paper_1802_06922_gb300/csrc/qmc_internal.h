@@ -7,7 +7,8 @@ namespace qmcgb {
 
 constexpr int kMaxKnots = 32;       // largest Jastrow M
 constexpr int kMaxDelay = 64;       // largest delay rank k
-constexpr int kThreads = 256;       // threads of the per-walker kernels
+constexpr int kThreads = 256;
+constexpr int kEnergyThreads = 512;   // local energy: 16 warps per walker       // threads of the per-walker kernels
 
 // One proposed move: new position and acceptance variate.
 struct alignas(32) Prop {

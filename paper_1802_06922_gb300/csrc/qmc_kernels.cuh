@@ -1222,7 +1222,7 @@ __global__ void __launch_bounds__(256) k_refine_commit(SysParams S, WalkParams W
 // One block per walker, one warp per electron; per-electron terms summed in FP64.
 // =============================================================================
 template <class TW>
-__global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk) {
+__global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, WalkParams Wk) {
   extern __shared__ __align__(16) char smem_e[];
   __shared__ JastrowTab<TW> jt;
   jastrow_tab_fill<TW>(S, jt);
@@ -1235,6 +1235,7 @@ __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk
   for (int i = threadIdx.x; i < 3 * n_e; i += blockDim.x) posw[i] = (TW)P[i];
   __syncthreads();
   const TW Lw = Cst<TW>::L(S), iLw = Cst<TW>::invL(S), kap = Cst<TW>::kappa(S), Zw = Cst<TW>::Z(S);
+  const TW hL2 = TW(0.25) * Lw * Lw;
   const TW* ionw = Cst<TW>::ions(S);
   const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
   const TW* Bw = static_cast<const TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn);
@@ -1276,21 +1277,24 @@ __global__ void __launch_bounds__(256) k_local_energy(SysParams S, WalkParams Wk
         TW dd[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) dd[c] = min_image<TW>(ri[c] - q[c], Lw, iLw);
-        const TW r = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const TW r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
         const bool once = (j >= n_e) || (j > i);
-        if (S.with_potential && once) {
-          const TW y = yukawa<TW>(r, kap, Lw);
+        // pairs beyond both cutoffs (Jastrow r_c, potential L/2) contribute nothing
+        const bool in_v = S.with_potential && once && r2 < hL2;
+        const bool in_j = jt.M[f] != 0 && r2 < jt.rc2[f];
+        if (!(in_v || in_j) || !(r2 > TW(0))) continue;
+        const TW rinv = rsqrt_w(r2), r = r2 * rinv;
+        if (in_v) {
+          const TW y = exp_w(-kap * r) * rinv;        // Yukawa e^{-kappa r} / r
           pv += (j < n_e) ? y : -Zw * y;
         }
-        if (jt.M[f] == 0) continue;
+        if (!in_j) continue;
         TW u, du, d2u;
         jastrow_eval<TW>(jt, f, r, u, du, d2u);
         if (once) jj += u;
-        if (r > TW(0)) {
-          const TW g = du / r;
-          gx += g * dd[0]; gy += g * dd[1]; gz += g * dd[2];
-          lj += d2u + TW(2) * g;
-        }
+        const TW g = du * rinv;
+        gx += g * dd[0]; gy += g * dd[1]; gz += g * dd[2];
+        lj += d2u + TW(2) * g;
       }
       s[4] = gx; s[5] = gy; s[6] = gz; s[7] = lj; s[8] = pv; s[9] = jj;
     }

@@ -99,7 +99,7 @@ cudaError_t local_energy(const SysParams& S, const WalkParams& W, cudaStream_t s
   cudaError_t e = cudaFuncSetAttribute(k_local_energy<TW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_local_energy<TW><<<W.n_w, kThreads, smem, st>>>(S, W);
+  k_local_energy<TW><<<W.n_w, kEnergyThreads, smem, st>>>(S, W);
   return cudaGetLastError();
 }
 
