@@ -40,7 +40,9 @@ def parse_args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--preset", default="sj512")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
-    p.add_argument("--delay-k", type=int, default=16)
+    p.add_argument("--delay-k", default="auto",
+                   help="delay rank k, or 'auto': the fastest of 8, 16, 32 on this workload "
+                        "(timed by the package's tuner before the timed region)")
     p.add_argument("--reinv-period", type=int, default=128)
     p.add_argument("--fp64-steps", type=int, default=4)
     p.add_argument("--e2e-steps", type=int, default=None)
@@ -52,6 +54,8 @@ def parse_args():
     p.add_argument("--workload", default="vmc", choices=["vmc", "dmc"],
                    help="dmc: the batched uneven drift-diffusion/branching workload "
                         "(64/192/384 electrons with 768/512/256 target walkers)")
+    p.add_argument("--walkers", type=int, default=0,
+                   help="walker count (default: the preset's); smaller counts serve profiling")
     p.add_argument("--dmc-vmc-sweeps", type=int, default=4,
                    help="drift-diffusion VMC sweeps that equilibrate the walkers before DMC")
     return p.parse_args()
@@ -303,6 +307,16 @@ def run_ours(args, spec, rank, world, local_rank):
             ms = float(t.item())
         return ms, prof, launches, clocks, e_loc
 
+    tuning = None
+    if args.delay_k == "auto":
+        k_best, k_times = q.tune_delay(inputs, pos, candidates=(8, 16, 32),
+                                       precision=args.precision, reinv_period=args.reinv_period,
+                                       reinv_on_accepted=args.reinv_on_accepted)
+        args.delay_k = k_best
+        tuning = {"candidates_ms_per_sweep": {str(k): round(v, 3) for k, v in k_times.items()},
+                  "chosen": k_best}
+    else:
+        args.delay_k = int(args.delay_k)
     sysm = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
                                 reinv_period=args.reinv_period,
                                 reinv_on_accepted=args.reinv_on_accepted)
@@ -379,7 +393,8 @@ def run_ours(args, spec, rank, world, local_rank):
                        "moves_per_step": moves_per_step * world,
                        "l2": f"inputs larger than L2: {table_bytes(spec, args.precision) / 1e6:.0f} MB "
                              f"coefficient table gathered at random",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "delay_k_autotune": tuning},
             "roofline": roof, "gpu_launches": launches, "kernels": kernels, "clocks": clocks,
             "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
@@ -405,12 +420,13 @@ def run_dmc(args, rank, world, local_rank):
     import paper_1802_06922_gb300 as q
     from synthetic import build_inputs, spec_for
     stream = torch.cuda.current_stream()
+    dmc_k = 16 if args.delay_k == "auto" else int(args.delay_k)
     systems, pos, et, specs = [], [], [], []
     for name in DMC_SYSTEMS:
         spec = spec_for(name)
         inputs = build_inputs(spec, seed=0)
         inputs["seed"] = rank
-        s = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+        s = q.system_from_inputs(inputs, precision=args.precision, delay_k=dmc_k,
                                  reinv_period=args.reinv_period, move="drift", step=spec.step)
         # equilibrate with drift-diffusion VMC sweeps before branching starts (uniform
         # random starting points put some walkers next to a node, where E_L is extreme)
@@ -462,7 +478,7 @@ def run_dmc(args, rank, world, local_rank):
                            f"{sp.name}: {sp.n_elec} electrons, {sp.grid}^3 table, {sp.n_orb} "
                            f"orbitals, {sp.n_walkers} target walkers" for sp in specs)
                        + f"; drift-diffusion tau={specs[0].step}, branching, E_T feedback, "
-                         f"delayed rank-{args.delay_k}, re-inversion every {args.reinv_period} moves; "
+                         f"delayed rank-{dmc_k}, re-inversion every {args.reinv_period} moves; "
                          f"walkers equilibrated by {args.dmc_vmc_sweeps} VMC sweeps, E_T from "
                          f"their median E_L",
                        "parallelism": f"replicas x{world}; systems on concurrent streams"},
@@ -475,8 +491,11 @@ def run_dmc(args, rank, world, local_rank):
 
 def main():
     args = parse_args()
+    import dataclasses
     from synthetic import spec_for
     spec = spec_for(args.preset)
+    if args.walkers > 0:
+        spec = dataclasses.replace(spec, n_walkers=args.walkers)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
