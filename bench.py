@@ -161,6 +161,29 @@ def run_reference(args, spec, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+def replica_seeds(rank: int):
+    """(Philox seed, initial-position seed) of replica `rank`: every rank runs an independent
+    set of Markov chains (weak scaling; walkers never move between ranks)."""
+    return rank, 1000 + rank
+
+
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The slowest rank's value of a timing (one MAX all-reduce); x itself without a process
+    group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ GPU arm
 N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 
@@ -271,8 +294,9 @@ def run_ours(args, spec, rank, world, local_rank):
             dist.barrier()
 
     inputs = build_inputs(spec, seed=0)
-    inputs["seed"] = rank                                   # Philox stream of this replica
-    rng = np.random.default_rng(1000 + rank)
+    philox_seed, pos_seed = replica_seeds(rank)
+    inputs["seed"] = philox_seed                            # Philox stream of this replica
+    rng = np.random.default_rng(pos_seed)
     pos = rng.uniform(0, spec.L, size=(spec.n_walkers, spec.n_elec, 3))
     stream = torch.cuda.current_stream()
     moves_per_step = spec.n_walkers * spec.n_elec
@@ -301,10 +325,7 @@ def run_ours(args, spec, rank, world, local_rank):
         w.check(stream)
         e_loc, _ = w.measure()
         w.close()
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
         return ms, prof, launches, clocks, e_loc
 
     tuning = None
@@ -321,7 +342,7 @@ def run_ours(args, spec, rank, world, local_rank):
                                 reinv_period=args.reinv_period,
                                 reinv_on_accepted=args.reinv_on_accepted)
     ms, prof, launches, clocks, e_loc = timed(sysm, args.steps, args.warmup, profile=True)
-    value = world * moves_per_step * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, moves_per_step * args.steps, ms / 1e3)
 
     # end to end through the public API with pinned host buffers: walker creation from
     # host positions, every sweep followed by a device->host read of E_L and ln|Psi|,
@@ -341,11 +362,8 @@ def run_ours(args, spec, rank, world, local_rank):
     barrier()
     e2e_s = time.perf_counter() - t0
     w.close()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * moves_per_step * e2e_steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, dist)
+    e2e = {"value": whole_job_rate(world, moves_per_step * e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": pos.nbytes / e2e_steps,
            "d2h_bytes_per_step": 2 * 8 * spec.n_walkers + pos.nbytes / e2e_steps,
            "steps": e2e_steps,
@@ -359,7 +377,7 @@ def run_ours(args, spec, rank, world, local_rank):
         s64 = q.system_from_inputs(inputs, precision="fp64", delay_k=1, reinv_period=0)
         ms64, _, _, _, e64 = timed(s64, args.fp64_steps, 1)
         s64.close()
-        v64 = world * moves_per_step * args.fp64_steps / (ms64 / 1e3)
+        v64 = whole_job_rate(world, moves_per_step * args.fp64_steps, ms64 / 1e3)
         fp64 = {"value": v64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
                 "dtype": "f64", "update": "Sherman-Morrison rank-1, no re-inversion"}
 
@@ -425,7 +443,7 @@ def run_dmc(args, rank, world, local_rank):
     for name in DMC_SYSTEMS:
         spec = spec_for(name)
         inputs = build_inputs(spec, seed=0)
-        inputs["seed"] = rank
+        inputs["seed"] = replica_seeds(rank)[0]
         s = q.system_from_inputs(inputs, precision=args.precision, delay_k=dmc_k,
                                  reinv_period=args.reinv_period, move="drift", step=spec.step)
         # equilibrate with drift-diffusion VMC sweeps before branching starts (uniform
@@ -458,16 +476,13 @@ def run_dmc(args, rank, world, local_rank):
         moves += sum(sp.n_elec * int(x["population_before"]) for sp, x in zip(specs, st))
     launches = d.launch_count() - l0
     final = [d.read(i) for i in range(len(systems))]
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     d.close()
     for s in systems:
         s.close()
     if rank != 0:
         return
-    value = world * moves / (total_ms / 1e3)
+    value = whole_job_rate(world, moves, total_ms / 1e3)
     line = {"metric": "electron moves/sec, batched uneven DMC (sum over systems of N_e x N_w per step)",
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
