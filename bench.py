@@ -187,6 +187,19 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 # ------------------------------------------------------------------ GPU arm
 N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of each kernel
+# class, from one ncu capture of the 512-electron FP32 workload at 200 walkers and k = 16
+# (profiles/kernels_sj512_200walkers_ncu_full.md), scaled to a full launch by the units it
+# processes: (bytes per unit, unit)
+TRAFFIC_SJ512_FP32 = {
+    "vgl": (2.645e9 / 51200, "move"),        # k_vgl_proposals: 51,200 moves per launch
+    "sweep": (22.374e6 / 3200, "move"),      # k_sweep: 16 moves x 200 walkers
+    "flush": (62.85e6 / 200, "walker"),      # k_flush_tc: one spin block of 200 walkers
+    "refine": (186.2e6 / 200, "walker"),     # k_refine_residual_tc
+    "refine_update": (174.4e6 / 200, "walker"),  # k_refine_update_tc
+    "energy": (530.1e6 / 200, "walker"),     # k_local_energy
+}
+
 
 def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, delay_k,
                    reinv_period, sm_mhz):
@@ -251,6 +264,13 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
     if out is not None:
         out["frac"] = out["achieved"] / out["peak"]
         out["traffic"] = None
+        t = TRAFFIC_SJ512_FP32.get(name) if (spec.name == "sj512" and precision == "fp32") else None
+        if t is not None:
+            per_unit, unit = t
+            units = moves if unit == "move" else spec.n_walkers
+            out["traffic"] = per_unit * units
+            out["traffic_note"] = (f"ncu DRAM bytes per {unit} at 200 walkers, k = 16, "
+                                   f"scaled to this launch's {units:.0f} {unit}s")
         out["avg_launch_ms"] = sec * 1e3
     return out
 
