@@ -77,6 +77,12 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
       k_refine_commit<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
       return cudaGetLastError();
     }
+    if (ns > kRsMaxK) {
+      // beyond the exactness bound of the slice products: every walker of this spin block
+      // takes the FP64 re-inversion (refine_max set to NaN makes the update skip them and
+      // the commit re-invert them)
+      return cudaMemsetAsync(W.refine_max, 0xFF, sizeof(float) * W.n_w, st);
+    }
     // error-free residual on the tensor cores (power-of-two row scales first)
     k_refine_scales<TW><<<dim3(W.n_w, 2), kThreads, 0, st>>>(S, W, spin);
     cudaError_t e = cudaGetLastError();

@@ -351,6 +351,7 @@ constexpr int kRsSlices = 6;
 constexpr int kRsBits = 7;
 constexpr int kRsMaxLevel = 7;    // slice pairs (i, j) with i + j <= kRsMaxLevel
 constexpr int kRsTile = kRsRows * kRsK;            // BF16 elements of one slice tile
+constexpr int kRsMaxK = 512;      // K <= 512 keeps every exact accumulator below 2^23
 
 __host__ __device__ inline size_t refine_tc_smem_bytes() {
   return (size_t)2 * 2 * kRsSlices * kRsTile * 2 + 2 * kRsRows * sizeof(int) + 64;

@@ -180,3 +180,43 @@ def test_fp32_refinement_reaches_storage_accuracy():
         s.close()
     assert errs[16] < 64 * 2.0 ** -24, errs
     assert errs[16] <= errs[0], errs
+
+
+@pytest.mark.parametrize("precision,delay_k", [("fp32", 8), ("bf16", 4)])
+def test_mixed_precision_lockstep_odd_sizes(precision, delay_k):
+    """Spin blocks of 37 and 35 electrons (not multiples of 4): the scalar load paths of the
+    batched flush, the error-free residual and the Newton update, with the refinement every
+    16 moves; same gates as the even-sized lockstep test."""
+    inputs = build_inputs(small_spec(37, 35, grid=16), n_walkers=3)
+    ids = np.arange(3)
+    coef = bf16_round(inputs["coef"]) if precision == "bf16" else None
+    _, ref, ref_en = oracle_vmc(inputs, ids, 2, coef=coef)
+    forced = ref[..., 7]
+    tr, en, _ = _gpu_run(inputs, ids, 2, precision=precision, delay_k=delay_k,
+                         reinv_period=16, reinv_on_accepted=False, forced=forced, coef=coef)
+    r = rel_err(tr[..., 0], ref[..., 0], 1e-3)
+    print(f"{precision} k={delay_k} 37/35: ratio rel err median {np.median(r):.2e} "
+          f"p90 {np.quantile(r, 0.9):.2e} max {r.max():.2e}")
+    assert np.quantile(r, 0.9) < 1e-4, (r.max(), np.quantile(r, 0.9))
+    assert r.max() < 1e-3
+    ne = inputs["spec"].n_elec
+    assert np.max(np.abs(en[:, 0, :].T - ref_en[..., 0])) / ne < 1e-5
+
+
+def test_refinement_beyond_the_exact_slice_bound_falls_back_to_fp64():
+    """A spin block of 520 electrons exceeds the 512 for which the BF16 slice products of
+    the error-free residual sum exactly; its re-inversion takes the FP64 Gauss-Jordan path and
+    leaves an inverse at single-precision storage accuracy."""
+    inputs = build_inputs(small_spec(520, 1, grid=8, n_orb=520), n_walkers=2)
+    s = q.system_from_inputs(inputs, precision="fp32", delay_k=16, reinv_period=32)
+    w = q.Walkers(s, inputs["pos"])
+    w.sweep(1)
+    w.check()
+    for wk in range(2):
+        orb = w.orbitals(wk)
+        A = orb[:520, 0, :520]
+        ref = np.linalg.inv(A).T
+        err = np.abs(w.inverse(wk, 0) - ref).max() / np.abs(ref).max()
+        assert err < 1e-4 * max(1.0, np.linalg.cond(A) * 2.0 ** -24 / 1e-4), err
+    w.close()
+    s.close()
