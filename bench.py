@@ -62,16 +62,21 @@ def parse_args():
 
 
 # ------------------------------------------------------------------ workload description
+def system_desc(spec):
+    """The workload both arms run: system, walker count and move type."""
+    return (f"{spec.name}: {spec.n_elec} electrons ({spec.n_up} up/{spec.n_dn} down), "
+            f"{spec.n_orb} orbitals on a {spec.grid}^3 tricubic B-spline table, "
+            f"{spec.n_ion} ions, J1/J2 B-spline M={spec.jastrow_M}, {spec.n_walkers} walkers, "
+            f"Metropolis sigma={spec.step}")
+
+
 def workload(spec, precision, delay_k, reinv_period, on_accepted=False):
     tab = {"fp32": "FP32", "bf16": "BF16", "fp64": "FP64"}[precision]
     upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
     what = "accepted moves" if on_accepted else "moves"
     re = (("FP64 re-inversion" if precision == "fp64" else "re-inversion (error-free Newton step)")
           + f" every {reinv_period} {what}") if reinv_period else "no re-inversion"
-    return (f"{spec.name}: {spec.n_elec} electrons ({spec.n_up} up/{spec.n_dn} down), "
-            f"{spec.n_orb} orbitals on a {spec.grid}^3 {tab} tricubic B-spline table, "
-            f"{spec.n_ion} ions, J1/J2 B-spline M={spec.jastrow_M}, {spec.n_walkers} walkers, "
-            f"Metropolis sigma={spec.step}, {upd}, {re}")
+    return f"{system_desc(spec)}; GPU: {tab} table, {upd}, {re}"
 
 
 def table_bytes(spec, precision):
@@ -151,7 +156,8 @@ def run_reference(args, spec, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload(spec, "fp64", 1, 0) + " (FP64 oracle: LU per move)",
+            "config": {"workload": f"{system_desc(spec)}; oracle: FP64 table, determinant "
+                                   f"ratio by LU of the full Slater matrix every move",
                        "walkers": spec.n_walkers, "electrons": spec.n_elec},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: {per_step} consecutive moves of each of "
