@@ -6,7 +6,7 @@ import pytest
 
 from synthetic import build_inputs, small_spec, spec_for
 
-from parity_util import assert_trace_close, rel_err
+from parity_util import assert_trace_close, bf16_round, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -152,3 +152,53 @@ def test_dmc_uneven_systems_with_refinement():
     d.close()
     for s in systems:
         s.close()
+
+
+@pytest.mark.parametrize("precision,delay_k", [("fp32", 4), ("bf16", 8)])
+def test_drift_vmc_mixed_precision_lockstep(precision, delay_k):
+    """Drift-diffusion VMC in the single-precision forms (the DMC workload's arithmetic) with
+    the error-free refinement every 16 moves, replaying the oracle's decisions: ratio error
+    below 1e-4 at the 90th percentile and 1e-3 at the maximum; E_L at the GPU's positions
+    within 1e-5 Ha per electron, or within the single-precision storage bound
+    cond(A) 2^-24 |T_L| of a near-node configuration. The proposal r' uses the GPU's own
+    gradient, which differs from the oracle's by ~1e-5 relative, far below these gates."""
+    inputs = _drift_inputs(20, 18, 0.05, 3, grid=12)
+    ids = np.arange(3)
+    coef = bf16_round(inputs["coef"]) if precision == "bf16" else None
+    osys = OracleSystem(inputs, coef=coef)
+    _, ref, ref_en = run_vmc(osys, inputs["pos"], ids, 2)
+    d = dict(inputs)
+    if coef is not None:
+        d["coef"] = coef
+    s = q.system_from_inputs(d, precision=precision, delay_k=delay_k, reinv_period=16)
+    w = q.Walkers(s, inputs["pos"])
+    ne = s.n_up + s.n_dn
+    buf = torch.zeros((2, 3, ne, 8), dtype=torch.float64, device="cuda")
+    w.trace_enable(buf)
+    bits = np.ascontiguousarray(ref[..., 7].reshape(3, 2, ne).transpose(1, 0, 2).astype(np.uint8))
+    w.replay(bits, 2)
+    el_err = []
+    for _ in range(2):
+        w.sweep(1)
+        e_gpu, _ = w.measure()
+        pos = w.positions()
+        # E_L against the oracle at the GPU's own positions. Gate: 1e-5 Ha per electron, or
+        # the single-precision storage bound cond(A) 2^-24 |T_L| where that is larger (a
+        # configuration next to a node: E_L an outlier, A ill-conditioned)
+        for i in range(3):
+            e_ref, t_ref = osys.wf.local_energy(pos[i])
+            cond = max(np.linalg.cond(osys.wf.slater_matrix(pos[i], sp)) for sp in (0, 1))
+            bound = max(1e-5, cond * 2.0 ** -24 * abs(t_ref) / ne)
+            el_err.append(abs(e_gpu[i] - e_ref) / ne / bound)
+    tr = buf.cpu().numpy().transpose(1, 0, 2, 3).reshape(3, 2 * ne, 8)
+    r = rel_err(tr[..., 0], ref[..., 0], 1e-3)
+    print(f"drift {precision} k={delay_k}: ratio rel err median {np.median(r):.2e} "
+          f"p90 {np.quantile(r, 0.9):.2e} max {r.max():.2e}; E_L error / gate {np.round(el_err, 3)}")
+    assert np.quantile(r, 0.9) < 1e-4, (r.max(), np.quantile(r, 0.9))
+    assert r.max() < 1e-3
+    assert max(el_err) < 1.0
+    # the trajectories agree closely: same decisions, proposals from nearly equal gradients
+    ref_pos = np.array([wk.R for wk in run_vmc(osys, inputs["pos"], ids, 2)[0]])
+    assert np.abs(pos - ref_pos).max() < 1e-3
+    w.close()
+    s.close()
