@@ -64,7 +64,9 @@ typedef enum {
 
 typedef enum {
   QMC_FP64 = 0,          /* table, orbital values, inverse and ratios in double */
-  QMC_FP32 = 1,          /* FP32 table and inverse; FP64 re-inversion and reductions */
+  QMC_FP32 = 1,          /* FP32 table, orbital values, inverse and ratios; re-inversion by a
+                            Newton step with an error-free residual (see reinv_period);
+                            FP64 ln|det| accumulation, energy sums and reductions */
   QMC_FP32_BF16TAB = 2   /* BF16 coefficient table, FP32 accumulation, else as QMC_FP32 */
 } qmc_precision;
 
@@ -86,7 +88,13 @@ typedef struct {
   qmc_move move;
   double step;             /* sigma (Metropolis) or tau (drift), bohr or 1/Ha */
   int delay_k;             /* 1 = Sherman-Morrison rank-1; 2..64 = delayed rank-k */
-  int reinv_period;        /* re-invert each Slater matrix in FP64 every this many moves (0 = never) */
+  int reinv_period;        /* re-invert each Slater matrix every this many moves (0 = never):
+                              QMC_FP64 by FP64 Gauss-Jordan; the single-precision forms by one
+                              Newton step X <- X + X R whose residual R = I - A X is computed
+                              error-free on the tensor cores, with FP64 Gauss-Jordan for a
+                              walker whose |R| exceeds 1e-2 and for spin blocks above 512
+                              electrons (the in-sweep variant used with reinv_on_accepted
+                              sums R with compensated arithmetic) */
   int reinv_on_accepted;   /* 1: count accepted moves of the determinant; 0: proposed moves */
   uint64_t seed;           /* Philox4x32-10 key of every draw */
 } qmc_system_desc;
