@@ -212,6 +212,11 @@ __device__ __forceinline__ T yukawa(T r, T kappa, T L) {
   return (r < T(0.5) * L) ? exp(-kappa * r) / r : T(0);
 }
 
+// Barrier over `count` threads (a multiple of 32) of the block, id 1..15 (0 is the block).
+__device__ __forceinline__ void named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+
 // ------------------------------------------------------------------ reductions
 template <int N, class T>
 __device__ __forceinline__ void warp_sum(T (&v)[N]) {

@@ -963,6 +963,29 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
         sm.sc[4] = tot[4];        // phi' . Binv0[e]: corner of the bordered C
       }
       }
+    } else {
+      // While warp 0 decides, the other warps border C for an acceptance (wasted on a
+      // rejection, but in time they would spend waiting): crow[l'] = phi' . U_l', then
+      // y = C^-T crow and crow . z for the Schur complement (all compensated).
+      for (int l = warp - 1; l < m; l += nw - 1) {
+        TW s = TW(0), c = TW(0);
+        for (int j = lane; j < ns; j += 32) comp_fma(s, c, phi[j], sm.wu[(size_t)l * ld_v + j]);
+        warp_sum_comp(s, c);
+        if (lane == 0) sm.crow[l] = s + c;
+      }
+      named_barrier(1, nt - 32);
+      const int t1 = tid - 32;
+      if (t1 < m) {
+        TW y = TW(0), yc = TW(0);
+        for (int l = 0; l < m; ++l) comp_fma(y, yc, sm.crow[l], sm.cinv[l * kc + t1]);
+        sm.yvec[t1] = y + yc;
+      }
+      if (warp == nw - 1) {
+        TW sv = TW(0), sc2 = TW(0);
+        for (int l = lane; l < m; l += 32) comp_fma(sv, sc2, -sm.crow[l], sm.zvec[l]);
+        warp_sum_comp(sv, sc2);
+        if (lane == 0) { sm.sc[6] = sv; sm.sc[7] = sc2; }
+      }
     }
     __syncthreads();
     const bool accept = sm.flag[0] != 0;
@@ -974,33 +997,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
         sm.wphi[(size_t)m * ld_v + j] = phi[j];
         sm.wu[(size_t)m * ld_v + j] = row0[j];
       }
-      // border of C: crow[l'] = phi' . U_l'  (compensated)
-      for (int l = warp; l < m; l += nw) {
-        TW s = TW(0), c = TW(0);
-        for (int j = lane; j < ns; j += 32) comp_fma(s, c, phi[j], sm.wu[(size_t)l * ld_v + j]);
-        warp_sum_comp(s, c);
-        if (lane == 0) sm.crow[l] = s + c;
-      }
-      __syncthreads();
-      if (tid < m) {
-        TW y = TW(0), yc = TW(0);
-        for (int l = 0; l < m; ++l) comp_fma(y, yc, sm.crow[l], sm.cinv[l * kc + tid]);
-        sm.yvec[tid] = y + yc;
-      }
-      if (warp == nw - 1) {
-        // Schur complement of the bordered C from its own entries: a - crow . C^-1 d
-        TW sv = TW(0), sc2 = TW(0);
-        for (int l = lane; l < m; l += 32) comp_fma(sv, sc2, -sm.crow[l], sm.zvec[l]);
-        warp_sum_comp(sv, sc2);
-        if (lane == 0) {
-          TW a = sm.sc[4], ac2 = TW(0);
-          comp_merge(a, ac2, sv, sc2);
-          sm.sc[5] = a + ac2;
-        }
-      }
-      __syncthreads();
+      // Schur complement of the bordered C from its own entries, a - crow . C^-1 d, formed
+      // by every thread from the values bordered during the decision
+      TW a = sm.sc[4], ac2 = TW(0);
+      comp_merge(a, ac2, sm.sc[6], sm.sc[7]);
       // C^-1 of the bordered matrix
-      const TW sinv = TW(1) / sm.sc[5];
+      const TW sinv = TW(1) / (a + ac2);
       for (int i = tid; i < (m + 1) * (m + 1); i += nt) {
         const int a = i / (m + 1), b = i % (m + 1);
         TW v;
@@ -1015,11 +1017,13 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
         sm.cinv[a * kc + b] = v;
       }
       ++m;
-      __syncthreads();
-      if (m == kc && !ext_flush) {
-        flush_window<TW>(B, ns, m, kc, sm, ld_v);
-        m = 0;
-        changed = true;
+      if (!ext_flush) {
+        __syncthreads();       // the in-kernel flush and re-inversion read the new window
+        if (m == kc) {
+          flush_window<TW>(B, ns, m, kc, sm, ld_v);
+          m = 0;
+          changed = true;
+        }
       }
     }
     if (reinv_period > 0) {
