@@ -199,7 +199,6 @@ N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 # processes: (bytes per unit, unit)
 TRAFFIC_SJ512_FP32 = {
     "vgl": (2.645e9 / 51200, "move"),        # k_vgl_proposals: 51,200 moves per launch
-    "sweep": (22.374e6 / 3200, "move"),      # k_sweep: 16 moves x 200 walkers
     "flush": (62.85e6 / 200, "walker"),      # k_flush_tc: one spin block of 200 walkers
     "refine": (186.2e6 / 200, "walker"),     # k_refine_residual_tc
     "refine_update": (174.4e6 / 200, "walker"),  # k_refine_update_tc

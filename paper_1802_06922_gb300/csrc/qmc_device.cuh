@@ -157,7 +157,7 @@ __device__ __forceinline__ void jastrow_tab_fill(const SysParams& S, JastrowTab<
     const int f = threadIdx.x;
     J.M[f] = S.jM[f];
     J.rc[f] = Cst<T>::rc(S, f);
-    J.rc2[f] = Cst<T>::rc(S, f) * Cst<T>::rc(S, f);
+    J.rc2[f] = S.jM[f] ? Cst<T>::rc(S, f) * Cst<T>::rc(S, f) : T(0);   // a term switched off: no pair inside
     J.scale[f] = S.jM[f] ? T(S.jM[f]) / Cst<T>::rc(S, f) : T(0);
   }
 }
@@ -185,18 +185,20 @@ __device__ __forceinline__ void jastrow_eval(const JastrowTab<T>& J, int f, T r,
   d2u *= scale * scale;
 }
 
-// u(r) alone, from the squared distance: 0 at and beyond the cutoff without a square
-// root (a Metropolis ratio needs no derivatives).
+// u(r) alone, from the squared distance (a Metropolis ratio needs no derivatives): 0 at
+// and beyond the cutoff. Without a branch, so that the pair loop's iterations overlap;
+// beyond the cutoff the spline is evaluated at r = 0 and discarded.
 template <class T>
 __device__ __forceinline__ T jastrow_value_r2(const JastrowTab<T>& J, int f, T r2) {
-  if (!(r2 < J.rc2[f])) return T(0);
-  const T s = sqrt(r2) * J.scale[f];
+  const bool in = r2 < J.rc2[f];
+  const T s = sqrt(in ? r2 : T(0)) * J.scale[f];
   int i = (int)tfloor(s);
   if (i < 0) i = 0;
   const T t = s - T(i), t2 = t * t, t3 = t2 * t, omt = T(1) - t;
   const T* p = J.p[f] + i;
-  return (p[0] * (omt * omt * omt) + p[1] * (T(3) * t3 - T(6) * t2 + T(4)) +
-          p[2] * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + p[3] * t3) * T(1.0 / 6.0);
+  const T u = (p[0] * (omt * omt * omt) + p[1] * (T(3) * t3 - T(6) * t2 + T(4)) +
+               p[2] * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + p[3] * t3) * T(1.0 / 6.0);
+  return in ? u : T(0);
 }
 
 // 1/sqrt(x) and e^x in the pair loops of the local energy: the hardware approximations

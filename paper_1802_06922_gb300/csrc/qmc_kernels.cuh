@@ -494,7 +494,7 @@ struct SweepSmem {
   TW* wphi;      // [k][ld_v]   window: new orbital rows
   TW* wu;        // [k][ld_v]   window: Binv0 rows of the moved electrons
   TW* rowbuf;    // [nwarps][2][ld_v]  flush: double-buffered rows
-  TW* cinv;      // [k][k]
+  TW* cinv;      // [k][k + 1]  rows padded by one: both row and column walks are conflict-free
   TW* dvec;      // [k]
   TW* zvec;      // [k]
   TW* crow;      // [k]
@@ -516,7 +516,7 @@ __host__ __device__ inline size_t sweep_smem_bytes(int n_e, int ld_v, int k, int
                                                    bool internal = true) {
   const int nrb = internal ? nwarps : 0;
   size_t b = sizeof(double) * (3 * (size_t)n_e + 16 + ld_v + 32 + 8);
-  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 3 + 2 * k + 2 * nrb) + (size_t)k * k +
+  b += sizeof(TW) * (3 * (size_t)n_e + (size_t)ld_v * (10 + 3 + 2 * k + 2 * nrb) + (size_t)k * (k + 1) +
                      4 * k + 2 * k * nrb + 32 * 12 + 8);
   b += sizeof(int) * (k + ld_v + 32 + 4);
   b = (b + 15) & ~size_t(15);
@@ -546,7 +546,7 @@ __device__ __forceinline__ SweepSmem<TW> carve(char* base, int n_e, int ld_v, in
   s.wphi = t; t += (size_t)k * ld_v;
   s.wu = t; t += (size_t)k * ld_v;
   s.rowbuf = t; t += (size_t)nwarps * 2 * ld_v;
-  s.cinv = t; t += k * k;
+  s.cinv = t; t += k * (k + 1);
   s.dvec = t; t += k;
   s.zvec = t; t += k;
   s.crow = t; t += k;
@@ -619,7 +619,7 @@ __device__ void flush_window(TW* __restrict__ B, int ns, int m, int kc,
     __syncwarp();
     for (int l = lane; l < m; l += 32) {
       TW z = TW(0);
-      for (int lp = 0; lp < m; ++lp) z += sm.cinv[l * kc + lp] * dw[lp];
+      for (int lp = 0; lp < m; ++lp) z += sm.cinv[l * (kc + 1) + lp] * dw[lp];
       zw[l] = z;
     }
     __syncwarp();
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   if (Wk.n_live && w >= *Wk.n_live) return;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = nt >> 5;
-  const int n_e = S.n_e, ld_v = Wk.ld_v;
+  const int n_e = S.n_e, ld_v = Wk.ld_v, kcp = kc + 1;
   SweepSmem<TW> sm = carve<TW>(smem_s, n_e, ld_v, kc, nw, !ext_flush);
   jastrow_tab_fill<TW>(S, jt);
   const int spin = e0 >= S.n_up ? 1 : 0;
@@ -707,25 +707,97 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       sm.sc[1] = (TW)sm.propb[4 * cur + 1];
       sm.sc[2] = (TW)sm.propb[4 * cur + 2];
     }
-    // d_l = Phi_l . Binv0[e]  (compensated)
-    for (int l = warp; l < m; l += nw) {
-      TW s = TW(0), c = TW(0);
-      for (int j = lane; j < ns; j += 32) comp_fma(s, c, sm.wphi[(size_t)l * ld_v + j], row0[j]);
-      warp_sum_comp(s, c);
-      if (lane == 0) sm.dvec[l] = s + c;
-    }
-    __syncthreads();
-    if (tid < m) {
-      TW z = TW(0), zc = TW(0);
-      for (int lp = 0; lp < m; ++lp) comp_fma(z, zc, sm.cinv[tid * kc + lp], sm.dvec[lp]);
-      sm.zvec[tid] = z + zc;
-    }
-    __syncthreads();
-    // x = Binv0[e] - sum_l z_l U_l (column e of the current inverse), compensated
-    for (int j = tid; j < ns; j += nt) {
-      TW xv = row0[j], xc = TW(0);
-      for (int l = 0; l < m; ++l) comp_fma(xv, xc, -sm.zvec[l], sm.wu[(size_t)l * ld_v + j]);
-      sm.xs[j] = xv + xc;
+    // Metropolis moves split the block: the determinant chain (d, z, x, ratio) runs on the
+    // upper half of the warps while the lower half evaluates the Jastrow terms, which
+    // depend on the positions only. Drift moves need x for the proposal and keep every
+    // warp on each step.
+    constexpr bool kSplit = !kDrift;
+    const int nJ = kSplit ? nw / 2 : 0;              // Jastrow warps
+    const bool det_grp = warp >= nJ;
+    const int dt = tid - 32 * nJ, dnt = nt - 32 * nJ, dw = warp - nJ, dnw = nw - nJ;
+    auto det_sync = [&]() {
+      if constexpr (kSplit) named_barrier(2, dnt); else __syncthreads();
+    };
+    // With the block split, the bordering of C for an acceptance (crow_l = phi' . U_l,
+    // a = phi' . Binv0[e], y = C^-T crow and a - crow . z, all compensated) rides along with
+    // d and z: r' and its orbital row are known before the move starts. The Schur
+    // complement a - crow . C^-1 d of the bordered C is the ratio itself (det of the
+    // bordered C over det C), so x is formed only where the gradient is wanted. Drift
+    // moves border C during the decision.
+    const int nzy = kSplit ? 2 * m : m, nb = kSplit ? 2 * m + 1 : m;
+    const bool need_x = !kSplit || Wk.trace;
+    if (det_grp) {
+      // d_l = Phi_l . Binv0[e] (compensated); with the split also crow_l and a.
+      // A warp keeps four dots in flight so that their reductions overlap.
+      constexpr int G = 4;
+      for (int l0 = dw; l0 < nb; l0 += G * dnw) {
+        const TW* a[G];
+        const TW* b[G];
+        TW s[G], c[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int l = min(l0 + g * dnw, nb - 1);     // a slot past the end repeats a dot
+          a[g] = l < m ? sm.wphi + (size_t)l * ld_v : phi;
+          b[g] = (l < m || l == 2 * m) ? row0 : sm.wu + (size_t)(l - m) * ld_v;
+          s[g] = TW(0);
+          c[g] = TW(0);
+        }
+        for (int j = lane; j < ns; j += 32)
+#pragma unroll
+          for (int g = 0; g < G; ++g) comp_fma(s[g], c[g], a[g][j], b[g][j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const TW s2 = __shfl_xor_sync(0xffffffffu, s[g], o);
+            const TW c2 = __shfl_xor_sync(0xffffffffu, c[g], o);
+            comp_merge(s[g], c[g], s2, c2);
+          }
+        if (lane == 0)
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int l = l0 + g * dnw;
+            if (l < m) sm.dvec[l] = s[g] + c[g];
+            else if (l < 2 * m) sm.crow[l - m] = s[g] + c[g];
+            else if (l < nb) { sm.sc[4] = s[g]; sm.sc[5] = c[g]; }   // a, kept as a pair
+          }
+      }
+      det_sync();
+      // z = C^-1 d (row i of C^-1) and y = C^-T crow (column i - m), two partial sums each
+      for (int i = dt; i < nzy; i += dnt) {
+        const bool zi = i < m;
+        const TW* ca = zi ? sm.cinv + i * kcp : sm.cinv + (i - m);
+        const int cs = zi ? 1 : kcp;
+        const TW* v = zi ? sm.dvec : sm.crow;
+        TW z0 = TW(0), c0 = TW(0), z1 = TW(0), c1 = TW(0);
+        int l = 0;
+        for (; l + 1 < m; l += 2) {
+          comp_fma(z0, c0, ca[l * cs], v[l]);
+          comp_fma(z1, c1, ca[(l + 1) * cs], v[l + 1]);
+        }
+        if (l < m) comp_fma(z0, c0, ca[l * cs], v[l]);
+        comp_merge(z0, c0, z1, c1);
+        (zi ? sm.zvec[i] : sm.yvec[i - m]) = z0 + c0;
+      }
+      det_sync();
+      if (kSplit && dw == dnw - 1) {
+        // the ratio a - crow . z, also the corner of the bordered C
+        TW sv = TW(0), sc2 = TW(0);
+        for (int l = lane; l < m; l += 32) comp_fma(sv, sc2, -sm.crow[l], sm.zvec[l]);
+        warp_sum_comp(sv, sc2);
+        if (lane == 0) {
+          TW a = sm.sc[4], ac2 = sm.sc[5];
+          comp_merge(a, ac2, sv, sc2);
+          sm.sc[6] = a;
+          sm.sc[7] = ac2;
+        }
+      }
+      // x = Binv0[e] - sum_l z_l U_l (column e of the current inverse), compensated
+      for (int j = dt; need_x && j < ns; j += dnt) {
+        TW xv = row0[j], xc = TW(0);
+        for (int l = 0; l < m; ++l) comp_fma(xv, xc, -sm.zvec[l], sm.wu[(size_t)l * ld_v + j]);
+        sm.xs[j] = xv + xc;
+      }
     }
     if constexpr (kDrift) {
       // grad ln|Psi| at the current position: grad phi(r_e) . x + grad J(r_e)
@@ -796,59 +868,79 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       }
       __syncthreads();
     }
-    // ratio (compensated), its companion phi'.Binv0[e] (compensated) and the gradient
+    // drift moves: the ratio phi' . x (compensated) and its companion phi' . Binv0[e]
+    // (compensated); the gradient wherever x is formed
     TW acc[9];
     TW rc = TW(0), ac = TW(0);     // compensation parts of acc[0] and acc[4]
     {
       TW a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-      for (int j = tid; j < ns; j += nt) {
-        const TW r0 = row0[j];
+      for (int j = dt; det_grp && need_x && j < ns; j += dnt) {   // the thread that wrote xs[j]
         const TW xv = sm.xs[j];
-        comp_fma(a0, rc, phi[j], xv);
+        if (!kSplit) {
+          comp_fma(a0, rc, phi[j], xv);
+          comp_fma(a4, ac, phi[j], row0[j]);
+        }
         a1 += phi[ld_v + j] * xv;
         a2 += phi[2 * ld_v + j] * xv;
         a3 += phi[3 * ld_v + j] * xv;
-        comp_fma(a4, ac, phi[j], r0);
       }
       acc[0] = a0; acc[1] = a1; acc[2] = a2; acc[3] = a3; acc[4] = a4;
     }
-    // Jastrow difference and gradient at r'
-    if (!kDrift && !Wk.trace) {
+    // Jastrow difference and gradient at r' (the lower warps when the block is split)
+    const int jtid = tid, jnt = kSplit ? 32 * nJ : nt;
+    const bool jas_grp = !kSplit || !det_grp;
+    if (!jas_grp) {
+      acc[5] = 0; acc[6] = 0; acc[7] = 0; acc[8] = 0;
+    } else if (!kDrift && !Wk.trace) {
       // Metropolis: the ratio needs Delta J only (no derivatives, no root beyond r_c)
-      const TW rn[3] = {sm.sc[0], sm.sc[1], sm.sc[2]};
+      const TW rn[3] = {(TW)sm.propb[4 * cur], (TW)sm.propb[4 * cur + 1],
+                        (TW)sm.propb[4 * cur + 2]};
       const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
-      TW dj = 0;
-      const int ntot = n_e + S.n_ion;
-      for (int j = tid; j < ntot; j += nt) {
-        if (j == e) continue;
-        TW q[3];
-        int f;
-        if (j < n_e) {
-          q[0] = sm.posw[j]; q[1] = sm.posw[n_e + j]; q[2] = sm.posw[2 * n_e + j];
-          f = ((j >= S.n_up) == (e >= S.n_up)) ? 1 : 2;
-        } else {
-          const int I = j - n_e;
-          q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
-          f = 0;
-        }
-        if (jt.M[f] == 0) continue;
+      TW dj = 0, dj2 = 0;
+      // electron pairs, two per iteration; the pair j = e is evaluated and dropped
+      const bool e_up = e < S.n_up;
+      const auto pair_e = [&](int j) -> TW {
+        const int f = ((j < S.n_up) == e_up) ? 1 : 2;
         TW rn2 = 0, ro2 = 0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const TW dn = min_image<TW>(rn[c] - q[c], Lw, iLw);
-          const TW dq = min_image<TW>(ro[c] - q[c], Lw, iLw);
+          const TW q = sm.posw[c * n_e + j];
+          const TW dn = min_image<TW>(rn[c] - q, Lw, iLw);
+          const TW dq = min_image<TW>(ro[c] - q, Lw, iLw);
           rn2 += dn * dn;
           ro2 += dq * dq;
         }
-        dj += jastrow_value_r2<TW>(jt, f, rn2) - jastrow_value_r2<TW>(jt, f, ro2);
+        const TW v = jastrow_value_r2<TW>(jt, f, rn2) - jastrow_value_r2<TW>(jt, f, ro2);
+        return j != e ? v : TW(0);
+      };
+      int j = jtid;
+      for (; j + jnt < n_e; j += 2 * jnt) {
+        dj += pair_e(j);
+        dj2 += pair_e(j + jnt);
       }
+      if (j < n_e) dj += pair_e(j);
+      // electron-ion pairs
+      for (int I = jtid; I < S.n_ion; I += jnt) {
+        TW rn2 = 0, ro2 = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const TW q = ionw[c * S.n_ion + I];
+          const TW dn = min_image<TW>(rn[c] - q, Lw, iLw);
+          const TW dq = min_image<TW>(ro[c] - q, Lw, iLw);
+          rn2 += dn * dn;
+          ro2 += dq * dq;
+        }
+        dj2 += jastrow_value_r2<TW>(jt, 0, rn2) - jastrow_value_r2<TW>(jt, 0, ro2);
+      }
+      dj += dj2;
       acc[5] = dj; acc[6] = 0; acc[7] = 0; acc[8] = 0;
     } else {
-      const TW rn[3] = {sm.sc[0], sm.sc[1], sm.sc[2]};
+      const TW rn[3] = {(TW)sm.propb[4 * cur], (TW)sm.propb[4 * cur + 1],
+                        (TW)sm.propb[4 * cur + 2]};
       const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
       TW dj = 0, gx = 0, gy = 0, gz = 0;
       const int ntot = n_e + S.n_ion;
-      for (int j = tid; j < ntot; j += nt) {
+      for (int j = jtid; j < ntot; j += jnt) {
         if (j == e) continue;
         TW q[3];
         int f;
@@ -914,7 +1006,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
 #pragma unroll
       for (int k = 0; k < 9; ++k) tot[k] = __shfl_sync(0xffffffffu, v, k);
       if (lane == 0) {
-      const TW R = tot[0], dJ = tot[5];
+      const TW R = kSplit ? sm.sc[6] + sm.sc[7] : tot[0], dJ = tot[5];
       const double u = sm.propb[4 * cur + 3];
       const bool ok = (R != TW(0)) && isfinite(R);
       TW A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
@@ -960,10 +1052,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
         sm.posw[e] = sm.sc[0]; sm.posw[n_e + e] = sm.sc[1]; sm.posw[2 * n_e + e] = sm.sc[2];
         sm.wrow[m] = row;
         sm.sc[3] = R;
-        sm.sc[4] = tot[4];        // phi' . Binv0[e]: corner of the bordered C
+        if (kDrift) sm.sc[4] = tot[4];   // phi' . Binv0[e]: corner of the bordered C
       }
       }
-    } else {
+    } else if (kDrift) {
       // While warp 0 decides, the other warps border C for an acceptance (wasted on a
       // rejection, but in time they would spend waiting): crow[l'] = phi' . U_l', then
       // y = C^-T crow and crow . z for the Schur complement (all compensated).
@@ -977,7 +1069,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       const int t1 = tid - 32;
       if (t1 < m) {
         TW y = TW(0), yc = TW(0);
-        for (int l = 0; l < m; ++l) comp_fma(y, yc, sm.crow[l], sm.cinv[l * kc + t1]);
+        for (int l = 0; l < m; ++l) comp_fma(y, yc, sm.crow[l], sm.cinv[l * kcp + t1]);
         sm.yvec[t1] = y + yc;
       }
       if (warp == nw - 1) {
@@ -998,23 +1090,30 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
         sm.wu[(size_t)m * ld_v + j] = row0[j];
       }
       // Schur complement of the bordered C from its own entries, a - crow . C^-1 d, formed
-      // by every thread from the values bordered during the decision
-      TW a = sm.sc[4], ac2 = TW(0);
-      comp_merge(a, ac2, sm.sc[6], sm.sc[7]);
+      // by every thread from the values bordered before or during the decision
+      TW a, ac2;
+      if constexpr (kSplit) {
+        a = sm.sc[6];
+        ac2 = sm.sc[7];
+      } else {
+        a = sm.sc[4];
+        ac2 = TW(0);
+        comp_merge(a, ac2, sm.sc[6], sm.sc[7]);
+      }
       // C^-1 of the bordered matrix
       const TW sinv = TW(1) / (a + ac2);
       for (int i = tid; i < (m + 1) * (m + 1); i += nt) {
         const int a = i / (m + 1), b = i % (m + 1);
         TW v;
         if (a < m && b < m)
-          v = sm.cinv[a * kc + b] + sm.zvec[a] * sm.yvec[b] * sinv;
+          v = sm.cinv[a * kcp + b] + sm.zvec[a] * sm.yvec[b] * sinv;
         else if (a < m)
           v = -sm.zvec[a] * sinv;
         else if (b < m)
           v = -sm.yvec[b] * sinv;
         else
           v = sinv;
-        sm.cinv[a * kc + b] = v;
+        sm.cinv[a * kcp + b] = v;
       }
       ++m;
       if (!ext_flush) {
@@ -1071,7 +1170,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       gphi[i] = sm.wphi[i];
       gu[i] = sm.wu[i];
     }
-    for (int i = tid; i < kc * kc; i += nt) gc[i] = sm.cinv[i];
+    for (int i = tid; i < kc * kc; i += nt) gc[i] = sm.cinv[(i / kc) * (kc + 1) + i % kc];
     for (int i = tid; i < m; i += nt) Wk.win_row[(size_t)w * kc + i] = sm.wrow[i];
     if (tid == 0) Wk.win_m[w] = m;
   } else if (m > 0) {
