@@ -140,11 +140,15 @@ __device__ __forceinline__ void jastrow_u(const SysParams& S, int f, T r, T& u, 
 // The three radial functors staged in shared memory: reading knots through a per-thread
 // index from kernel parameters would serialise the constant-bank accesses of a warp.
 // p is zero-padded beyond M so the four-point stencil needs no bounds test.
+// pw holds the same spline in power form per knot interval, u = a0 + a1 t + a2 t^2 + a3 t^3
+// (the cubic B-spline basis expanded and summed with the interval's four knots, in FP64),
+// so that a value costs one 16-byte load and three FMAs.
 template <class T>
 struct JastrowTab {
   int M[3];
   T rc[3], rc2[3], scale[3];
   T p[3][kMaxKnots + 4];
+  alignas(16) T pw[3][kMaxKnots + 1][4];
 };
 
 template <class T>
@@ -152,6 +156,16 @@ __device__ __forceinline__ void jastrow_tab_fill(const SysParams& S, JastrowTab<
   for (int i = threadIdx.x; i < 3 * (kMaxKnots + 4); i += blockDim.x) {
     const int f = i / (kMaxKnots + 4), m = i % (kMaxKnots + 4);
     J.p[f][m] = (m <= S.jM[f]) ? Cst<T>::knot(S, f, m) : T(0);
+  }
+  for (int i = threadIdx.x; i < 3 * (kMaxKnots + 1); i += blockDim.x) {
+    const int f = i / (kMaxKnots + 1), m = i % (kMaxKnots + 1);
+    double q[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = (m + c <= S.jM[f]) ? S.jp[f][m + c] : 0.0;
+    J.pw[f][m][0] = T((q[0] + 4.0 * q[1] + q[2]) / 6.0);
+    J.pw[f][m][1] = T(0.5 * (q[2] - q[0]));
+    J.pw[f][m][2] = T(0.5 * (q[0] - 2.0 * q[1] + q[2]));
+    J.pw[f][m][3] = T((q[3] - q[0] + 3.0 * (q[1] - q[2])) / 6.0);
   }
   if (threadIdx.x < 3) {
     const int f = threadIdx.x;
@@ -185,19 +199,32 @@ __device__ __forceinline__ void jastrow_eval(const JastrowTab<T>& J, int f, T r,
   d2u *= scale * scale;
 }
 
+// r from r^2 in the value-only pair loop: in single precision x * rsqrt(x) (a few ulp, the
+// hardware reciprocal root), in double precision the correctly rounded root.
+__device__ __forceinline__ float sqrt_pair(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double sqrt_pair(double x) { return sqrt(x); }
+__device__ __forceinline__ void load_pw(const float* c, float (&a)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(c);
+  a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+}
+__device__ __forceinline__ void load_pw(const double* c, double (&a)[4]) {
+  const double2 v0 = reinterpret_cast<const double2*>(c)[0], v1 = reinterpret_cast<const double2*>(c)[1];
+  a[0] = v0.x; a[1] = v0.y; a[2] = v1.x; a[3] = v1.y;
+}
+
 // u(r) alone, from the squared distance (a Metropolis ratio needs no derivatives): 0 at
 // and beyond the cutoff. Without a branch, so that the pair loop's iterations overlap;
 // beyond the cutoff the spline is evaluated at r = 0 and discarded.
 template <class T>
 __device__ __forceinline__ T jastrow_value_r2(const JastrowTab<T>& J, int f, T r2) {
   const bool in = r2 < J.rc2[f];
-  const T s = sqrt(in ? r2 : T(0)) * J.scale[f];
-  int i = (int)tfloor(s);
-  if (i < 0) i = 0;
-  const T t = s - T(i), t2 = t * t, t3 = t2 * t, omt = T(1) - t;
-  const T* p = J.p[f] + i;
-  const T u = (p[0] * (omt * omt * omt) + p[1] * (T(3) * t3 - T(6) * t2 + T(4)) +
-               p[2] * (T(-3) * t3 + T(3) * t2 + T(3) * t + T(1)) + p[3] * t3) * T(1.0 / 6.0);
+  const T s = sqrt_pair(in ? r2 : T(0)) * J.scale[f];
+  const T fl = tfloor(s);
+  const int i = min(max((int)fl, 0), kMaxKnots);
+  const T t = s - fl;
+  T a[4];
+  load_pw(&J.pw[f][i][0], a);
+  const T u = ((a[3] * t + a[2]) * t + a[1]) * t + a[0];
   return in ? u : T(0);
 }
 

@@ -6,6 +6,7 @@
 namespace qmcgb {
 
 constexpr int kMaxKnots = 32;       // largest Jastrow M
+constexpr size_t kMaxDynSmem = 227 * 1024;   // largest dynamic shared memory of one block (sm_103a)
 constexpr int kMaxDelay = 64;       // largest delay rank k
 constexpr int kThreads = 256;
 constexpr int kEnergyThreads = 512;   // local energy: 16 warps per walker       // threads of the per-walker kernels

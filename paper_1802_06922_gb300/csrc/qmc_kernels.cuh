@@ -8,6 +8,7 @@
 // re-inversion.
 #pragma once
 #include "qmc_device.cuh"
+#include "tc_sm100.cuh"
 
 namespace qmcgb {
 
@@ -480,6 +481,8 @@ static __device__ float refine_inverse(const SysParams& S, const WalkParams& Wk,
 // with d_n[l] = Phi_l . Binv0[n] - delta(n, e_l); a full window is applied to every row
 // of Binv0 (the flush) and emptied.
 // =============================================================================
+constexpr long long kSweepWaitPolls = 20000000;   // bounded wait for a prefetch (polls)
+
 template <class TW>
 struct SweepSmem {
   double* posd;  // [3][n_e] exact positions
@@ -581,6 +584,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_wait_1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
 
 // Apply the window (m rows) to every row of Binv0 (B, ns x ns) and empty it:
 // Binv0[n] -= sum_l z_l U_l with z = C^-1 d_n, d_n[l] = Phi_l . Binv0[n] - delta(n, e_l).
@@ -632,6 +638,99 @@ __device__ void flush_window(TW* __restrict__ B, int ns, int m, int kc,
   }
 }
 
+// Jastrow difference of a move of electron e to r' (Sec. "Jastrow factor"): the sum over the
+// other electrons j and the ions I of u(|r' - r_j|) - u(|r_e - r_j|), minimum image. Each
+// returns the share of thread jtid of a group of jnt threads; posw is [3][n_e].
+// Value only (a Metropolis ratio): electron pairs two per iteration, the pair j = e
+// evaluated and dropped, no branches.
+template <class TW>
+__device__ __forceinline__ TW jastrow_delta_value(const SysParams& S, const JastrowTab<TW>& jt,
+                                                  const TW* posw, const TW* ionw, int e,
+                                                  const TW (&rn)[3], TW Lw, TW iLw, int jtid,
+                                                  int jnt) {
+  const int n_e = S.n_e;
+  const TW ro[3] = {posw[e], posw[n_e + e], posw[2 * n_e + e]};
+  TW dj = 0, dj2 = 0;
+  const bool e_up = e < S.n_up;
+  const auto pair_e = [&](int j) -> TW {
+    const int f = ((j < S.n_up) == e_up) ? 1 : 2;
+    TW rn2 = 0, ro2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const TW q = posw[c * n_e + j];
+      const TW dn = min_image<TW>(rn[c] - q, Lw, iLw);
+      const TW dq = min_image<TW>(ro[c] - q, Lw, iLw);
+      rn2 += dn * dn;
+      ro2 += dq * dq;
+    }
+    const TW v = jastrow_value_r2<TW>(jt, f, rn2) - jastrow_value_r2<TW>(jt, f, ro2);
+    return j != e ? v : TW(0);
+  };
+  int j = jtid;
+  for (; j + jnt < n_e; j += 2 * jnt) {
+    dj += pair_e(j);
+    dj2 += pair_e(j + jnt);
+  }
+  if (j < n_e) dj += pair_e(j);
+  for (int I = jtid; I < S.n_ion; I += jnt) {
+    TW rn2 = 0, ro2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const TW q = ionw[c * S.n_ion + I];
+      const TW dn = min_image<TW>(rn[c] - q, Lw, iLw);
+      const TW dq = min_image<TW>(ro[c] - q, Lw, iLw);
+      rn2 += dn * dn;
+      ro2 += dq * dq;
+    }
+    dj2 += jastrow_value_r2<TW>(jt, 0, rn2) - jastrow_value_r2<TW>(jt, 0, ro2);
+  }
+  return dj + dj2;
+}
+
+// The same difference with the gradient of J at r' in g (drift moves and traces).
+template <class TW>
+__device__ __forceinline__ TW jastrow_delta_grad(const SysParams& S, const JastrowTab<TW>& jt,
+                                                 const TW* posw, const TW* ionw, int e,
+                                                 const TW (&rn)[3], TW Lw, TW iLw, int jtid,
+                                                 int jnt, TW (&g)[3]) {
+  const int n_e = S.n_e;
+  const TW ro[3] = {posw[e], posw[n_e + e], posw[2 * n_e + e]};
+  TW dj = 0, gx = 0, gy = 0, gz = 0;
+  const int ntot = n_e + S.n_ion;
+  for (int j = jtid; j < ntot; j += jnt) {
+    if (j == e) continue;
+    TW q[3];
+    int f;
+    if (j < n_e) {
+      q[0] = posw[j]; q[1] = posw[n_e + j]; q[2] = posw[2 * n_e + j];
+      f = ((j >= S.n_up) == (e >= S.n_up)) ? 1 : 2;
+    } else {
+      const int I = j - n_e;
+      q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
+      f = 0;
+    }
+    if (jt.M[f] == 0) continue;
+    TW dn[3], dq[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dn[c] = min_image<TW>(rn[c] - q[c], Lw, iLw);
+      dq[c] = min_image<TW>(ro[c] - q[c], Lw, iLw);
+    }
+    const TW rnn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
+    const TW roo = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
+    TW un, dun, d2n, uo, duo, d2o;
+    jastrow_eval<TW>(jt, f, rnn, un, dun, d2n);
+    jastrow_eval<TW>(jt, f, roo, uo, duo, d2o);
+    dj += un - uo;
+    if (rnn > TW(0)) {
+      const TW gg = dun / rnn;
+      gx += gg * dn[0]; gy += gg * dn[1]; gz += gg * dn[2];
+    }
+  }
+  g[0] = gx; g[1] = gy; g[2] = gz;
+  return dj;
+}
+
 template <class TW>
 __device__ __forceinline__ TW texp(TW x);
 template <> __device__ __forceinline__ double texp<double>(double x) { return exp(x); }
@@ -664,22 +763,43 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
           (spin ? S.n_up * S.n_up : 0);
   TW* VG = static_cast<TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
   double* gpos = Wk.pos + (size_t)w * 3 * n_e;
-  const int vec = 16 / (int)sizeof(TW);            // TW elements per 16-byte copy
-  // prefetch of move index e (orbital row, proposal, inverse row) into buffer b
-  auto prefetch = [&](int e, int b, bool with_row) {
+  // Prefetch of move index e (orbital rows, proposal, inverse row) into buffer b: one
+  // thread hands the contiguous pieces to the bulk-copy unit, which completes them on the
+  // buffer's mbarrier. An inverse row that is not 16-byte aligned (N_s * sizeof(TW) not a
+  // multiple of 16) is fetched element-wise by every thread instead.
+  __shared__ __align__(8) uint64_t pf_bar[2];
+  const bool row_bulk = (ns * sizeof(TW)) % 16 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+  auto prefetch = [&](int e, int b) {
     const size_t mvi = (size_t)w * p_n + (e - p_e0);
-    const TW* src = kDrift ? VG + (size_t)e * 5 * ld_v : Pv + mvi * 5 * ld_v;
-    TW* dst = sm.phib + (size_t)b * 5 * ld_v;
-    for (int i = tid * vec; i < 5 * ld_v; i += nt * vec) cp_async16(dst + i, src + i);
-    if (!kDrift && tid < 2)
-      cp_async16(sm.propb + 4 * b + 2 * tid, reinterpret_cast<const double*>(prop + mvi) + 2 * tid);
-    if (with_row) {
-      const TW* rs = B + (size_t)(e - first) * ns;
-      TW* rd = sm.rowb + (size_t)b * ld_v;
-      for (int j = tid; j < ns; j += nt) cp_async_elem(rd + j, rs + j);
+    const TW* rs = B + (size_t)(e - first) * ns;
+    TW* rd = sm.rowb + (size_t)b * ld_v;
+    if (tid == 0) {
+      // the block's reads of this buffer (ordered by the barrier before) precede the copies
+      tc::fence_async_smem();
+      const uint32_t nphi = 5u * ld_v * sizeof(TW), nrow = row_bulk ? ns * sizeof(TW) : 0u;
+      tc::mbar_arrive_expect_tx(&pf_bar[b], nphi + (kDrift ? 0u : (uint32_t)sizeof(Prop)) + nrow);
+      tc::bulk_g2s(sm.phib + (size_t)b * 5 * ld_v, kDrift ? VG + (size_t)e * 5 * ld_v : Pv + mvi * 5 * ld_v,
+                   nphi, &pf_bar[b]);
+      if (!kDrift) tc::bulk_g2s(sm.propb + 4 * b, prop + mvi, sizeof(Prop), &pf_bar[b]);
+      if (row_bulk && nrow) tc::bulk_g2s(rd, rs, nrow, &pf_bar[b]);
     }
-    cp_async_commit();
+    if (!row_bulk) {
+      for (int j = tid; j < ns; j += nt) cp_async_elem(rd + j, rs + j);
+      cp_async_commit();
+    }
   };
+  // bounded wait for the prefetch of move index it (buffer it & 1, its (it >> 1)-th use)
+  auto prefetch_wait = [&](int it) {
+    if (!row_bulk) cp_async_wait_all();
+    if (!tc::mbar_wait(&pf_bar[it & 1], (uint32_t)((it >> 1) & 1), kSweepWaitPolls) && lane == 0)
+      atomicOr(Wk.err, kErrTimeout);
+  };
+  if (tid == 0) {
+    tc::mbar_init(&pf_bar[0], 1);
+    tc::mbar_init(&pf_bar[1], 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
   for (int i = tid; i < 3 * n_e; i += nt) {
     const double p = gpos[i];
     sm.posd[i] = p;
@@ -693,13 +813,13 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   }
   int since = Wk.acc_since[2 * w + spin];
   int m = 0;
-  prefetch(e0, 0, true);
+  if (e0 < e1) prefetch(e0, 0);      // every prefetch issued is waited for inside the loop
   for (int e = e0; e < e1; ++e) {
     const int row = e - first;
     const int cur = (e - e0) & 1;
-    cp_async_wait_all();
+    prefetch_wait(e - e0);
     __syncthreads();
-    if (e + 1 < e1) prefetch(e + 1, cur ^ 1, true);
+    if (e + 1 < e1) prefetch(e + 1, cur ^ 1);
     TW* phi = sm.phib + (size_t)cur * 5 * ld_v;
     const TW* row0 = sm.rowb + (size_t)cur * ld_v;
     if (!kDrift && tid == 0) {
@@ -895,82 +1015,14 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       // Metropolis: the ratio needs Delta J only (no derivatives, no root beyond r_c)
       const TW rn[3] = {(TW)sm.propb[4 * cur], (TW)sm.propb[4 * cur + 1],
                         (TW)sm.propb[4 * cur + 2]};
-      const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
-      TW dj = 0, dj2 = 0;
-      // electron pairs, two per iteration; the pair j = e is evaluated and dropped
-      const bool e_up = e < S.n_up;
-      const auto pair_e = [&](int j) -> TW {
-        const int f = ((j < S.n_up) == e_up) ? 1 : 2;
-        TW rn2 = 0, ro2 = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const TW q = sm.posw[c * n_e + j];
-          const TW dn = min_image<TW>(rn[c] - q, Lw, iLw);
-          const TW dq = min_image<TW>(ro[c] - q, Lw, iLw);
-          rn2 += dn * dn;
-          ro2 += dq * dq;
-        }
-        const TW v = jastrow_value_r2<TW>(jt, f, rn2) - jastrow_value_r2<TW>(jt, f, ro2);
-        return j != e ? v : TW(0);
-      };
-      int j = jtid;
-      for (; j + jnt < n_e; j += 2 * jnt) {
-        dj += pair_e(j);
-        dj2 += pair_e(j + jnt);
-      }
-      if (j < n_e) dj += pair_e(j);
-      // electron-ion pairs
-      for (int I = jtid; I < S.n_ion; I += jnt) {
-        TW rn2 = 0, ro2 = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const TW q = ionw[c * S.n_ion + I];
-          const TW dn = min_image<TW>(rn[c] - q, Lw, iLw);
-          const TW dq = min_image<TW>(ro[c] - q, Lw, iLw);
-          rn2 += dn * dn;
-          ro2 += dq * dq;
-        }
-        dj2 += jastrow_value_r2<TW>(jt, 0, rn2) - jastrow_value_r2<TW>(jt, 0, ro2);
-      }
-      dj += dj2;
-      acc[5] = dj; acc[6] = 0; acc[7] = 0; acc[8] = 0;
+      acc[5] = jastrow_delta_value<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, jtid, jnt);
+      acc[6] = 0; acc[7] = 0; acc[8] = 0;
     } else {
       const TW rn[3] = {(TW)sm.propb[4 * cur], (TW)sm.propb[4 * cur + 1],
                         (TW)sm.propb[4 * cur + 2]};
-      const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
-      TW dj = 0, gx = 0, gy = 0, gz = 0;
-      const int ntot = n_e + S.n_ion;
-      for (int j = jtid; j < ntot; j += jnt) {
-        if (j == e) continue;
-        TW q[3];
-        int f;
-        if (j < n_e) {
-          q[0] = sm.posw[j]; q[1] = sm.posw[n_e + j]; q[2] = sm.posw[2 * n_e + j];
-          f = ((j >= S.n_up) == (e >= S.n_up)) ? 1 : 2;
-        } else {
-          const int I = j - n_e;
-          q[0] = ionw[I]; q[1] = ionw[S.n_ion + I]; q[2] = ionw[2 * S.n_ion + I];
-          f = 0;
-        }
-        if (jt.M[f] == 0) continue;
-        TW dn[3], dq[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          dn[c] = min_image<TW>(rn[c] - q[c], Lw, iLw);
-          dq[c] = min_image<TW>(ro[c] - q[c], Lw, iLw);
-        }
-        const TW rnn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
-        const TW roo = sqrt(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
-        TW un, dun, d2n, uo, duo, d2o;
-        jastrow_eval<TW>(jt, f, rnn, un, dun, d2n);
-        jastrow_eval<TW>(jt, f, roo, uo, duo, d2o);
-        dj += un - uo;
-        if (rnn > TW(0)) {
-          const TW g = dun / rnn;
-          gx += g * dn[0]; gy += g * dn[1]; gz += g * dn[2];
-        }
-      }
-      acc[5] = dj; acc[6] = gx; acc[7] = gy; acc[8] = gz;
+      TW g[3];
+      acc[5] = jastrow_delta_grad<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, jtid, jnt, g);
+      acc[6] = g[0]; acc[7] = g[1]; acc[8] = g[2];
     }
     // block sums; warp partials added by thread 0 in working precision, R and a compensated
     warp_sum_comp(acc[0], rc);
@@ -1152,11 +1204,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
     }
     if (changed && e + 1 < e1) {
       // the inverse changed after the next row was prefetched: fetch it again
-      cp_async_wait_all();
+      prefetch_wait(e + 1 - e0);
       __syncthreads();
       const int nrow = e + 1 - first;
       TW* rd = sm.rowb + (size_t)(cur ^ 1) * ld_v;
       for (int j = tid; j < ns; j += nt) rd[j] = B[(size_t)nrow * ns + j];
+      tc::fence_async_smem();   // ordered before the bulk copy that refills this buffer later
     }
   }
   cp_async_wait_all();

@@ -3,6 +3,7 @@
 #include "qmc_launch.h"
 #include "qmc_tc_kernels.cuh"
 #include "qmc_dmc.cuh"
+#include "qmc_sweep_win.cuh"
 
 namespace qmcgb {
 namespace {
@@ -22,6 +23,18 @@ template <class TW>
 cudaError_t sweep(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1, int k,
                   const void* P, const void* prop, int p_e0, int p_n, int reinv_period,
                   int reinv_on_acc, int ext_flush, bool fixed_node, cudaStream_t st) {
+  const size_t smem_win = sweep_win_smem_bytes<TW>(S.n_e, W.ld_v);
+  if (ext_flush && reinv_period == 0 && k <= kWinMaxK && W.kc <= kWinMaxK && e1 - e0 <= k &&
+      smem_win <= kMaxDynSmem) {
+    // a launch of the batched delayed update: the pair-matrix form of the sweep
+    const size_t smem = smem_win;
+    auto kern = fixed_node ? k_sweep_win<TW, true> : k_sweep_win<TW, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<W.n_w, kWinThreads, smem, st>>>(S, W, e0, e1, static_cast<const TW*>(P),
+                                           static_cast<const Prop*>(prop), p_e0, p_n);
+    return cudaGetLastError();
+  }
   const size_t smem = sweep_smem_bytes<TW>(S.n_e, W.ld_v, k, kThreads / 32, !ext_flush);
   auto kern = fixed_node ? k_sweep<TW, TW, true, false> : k_sweep<TW, TW, false, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -44,6 +44,42 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long lo
   return false;
 }
 
+// Arrival of one thread that also announces `bytes` of asynchronous copies for this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// ------------------------------------------------------------------ bulk copies
+// One contiguous global -> shared copy by the bulk-copy (TMA) unit, counted against the
+// mbarrier's transaction bytes. Both addresses 16-byte aligned, `bytes` a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One contiguous shared -> global copy by the bulk-copy unit in the thread's current bulk
+// group (same alignment rules); commit closes the group, wait_read<N> returns once at most N
+// of the thread's groups still read shared memory, wait_all<N> once at most N are unfinished.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ------------------------------------------------------------------ tensor memory
 // Allocation and release are executed by one whole warp; the address lands in smem.
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
