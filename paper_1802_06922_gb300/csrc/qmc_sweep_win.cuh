@@ -16,6 +16,13 @@
 // O(m N_s), and the product that forms D runs at full parallelism before the sequential
 // part starts. All dots are compensated (TwoProduct and TwoSum); the diagonal keeps its pair.
 //
+// The Jastrow difference is regrouped the same way (Sec. "Jastrow factor"). Positions change
+// within the launch only through its accepted moves, so
+//   Delta J(t) = base[t] + sum over accepted t' < t of Q[t][t'],
+// base[t] = sum_j u(|r'_t - r_j|) - u(|r_e_t - r_j|) with the positions at the launch start,
+// Q[t][t'] = u(|r'_t - r'_t'|) - u(|r'_t - r_e_t'|) - u(|r_e_t - r'_t'|) + u(|r_e_t - r_e_t'|)
+// (the pair of the two moved electrons, same spin). Both are formed before the moves.
+//
 // Roles within a move: the determinant warps form z = C^-1 d (one warp) and y with the
 // ratio (the other) while the remaining warps evaluate the Jastrow difference; warp 0
 // decides while the other warps border C^-1 into a second buffer (kept on acceptance). One thread moves each accepted move's rows with the bulk-copy unit, one move
@@ -50,6 +57,8 @@ struct WinSmem {
   TW* WD;         // [kWinMaxK][kWinP] WD[l][t] = D[t_l][t]: d_l of move t
   TW* WC;         // [kWinMaxK][kWinP] WC[t][l] = D[t][t_l]: crow_l of move t
   TW* dlo;        // [kWinMaxK] compensation of D's diagonal
+  TW* jb;         // [kWinMaxK] Jastrow difference of each move at the launch-start positions
+  TW* Q;          // [kWinMaxK][kWinP] pair corrections of the Jastrow difference
   TW* zvec;       // [kWinMaxK]
   TW* yvec;       // [kWinMaxK]
   TW* stA;        // [2][kWinMaxK][kWinKs] staged proposal value rows
@@ -64,8 +73,8 @@ template <class TW>
 __host__ __device__ inline size_t sweep_win_smem_bytes(int n_e, int ld_v) {
   size_t b = sizeof(double) * (4 * (size_t)kWinMaxK + 3 * (size_t)n_e);
   b = (b + 15) & ~size_t(15);
-  b += sizeof(TW) * (12 * (size_t)ld_v + 3 * (size_t)n_e + 5 * (size_t)kWinMaxK * kWinP + 4 * kWinMaxK +
-                     3 * kWinMaxK + 4 * (size_t)kWinMaxK * kWinKs + 32 * 8 + 8);
+  b += sizeof(TW) * (12 * (size_t)ld_v + 3 * (size_t)n_e + 6 * (size_t)kWinMaxK * kWinP + 4 * kWinMaxK +
+                     4 * kWinMaxK + 4 * (size_t)kWinMaxK * kWinKs + 32 * 8 + 8);
   b += sizeof(int) * (kWinMaxK + 4);
   return b + 32;
 }
@@ -89,6 +98,8 @@ __device__ __forceinline__ WinSmem<TW> carve_win(char* base, int n_e, int ld_v) 
   s.WD = t; t += kWinMaxK * kWinP;
   s.WC = t; t += kWinMaxK * kWinP;
   s.dlo = t; t += kWinMaxK;
+  s.jb = t; t += kWinMaxK;
+  s.Q = t; t += kWinMaxK * kWinP;
   s.zvec = t; t += kWinMaxK;
   s.yvec = t; t += kWinMaxK;
   s.red = t; t += 32 * 8;
@@ -197,6 +208,40 @@ __global__ void __launch_bounds__(kWinThreads, 2)
   for (int i = tid; i < 3 * n_e; i += nt) sm.posw[i] = (TW)sm.posd[i];   // positions landed
   for (int i = tid; i < 4 * kk; i += nt)
     sm.propw[i] = (i & 3) == 3 ? round_down_w(sm.prop[i], TW(0)) : (TW)sm.prop[i];
+  __syncthreads();
+
+  // ---- the Jastrow difference of every move at the launch-start positions (8 threads per
+  // move) and the pair corrections Q
+  {
+    static_assert(kWinThreads / 8 >= kWinMaxK, "one group of 8 threads per move");
+    const int t = tid >> 3, gl = tid & 7;      // every lane takes part in the group sums
+    TW v = TW(0);
+    if (t < kk) {
+      const TW rn[3] = {sm.propw[4 * t], sm.propw[4 * t + 1], sm.propw[4 * t + 2]};
+      v = jastrow_delta_value<TW>(S, jt, sm.posw, ionw, e0 + t, rn, Lw, iLw, gl, 8);
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (t < kk && gl == 0) sm.jb[t] = v;
+    for (int i = tid; i < kk * kk; i += nt) {
+      const int ta = i / kk, tb = i - ta * kk;
+      TW q = TW(0);
+      if (ta != tb) {
+        TW d2[4] = {0, 0, 0, 0};   // (r'_a, r'_b), (r'_a, r_b), (r_a, r'_b), (r_a, r_b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const TW pa = sm.propw[4 * ta + c], pb = sm.propw[4 * tb + c];
+          const TW oa = sm.posw[c * n_e + e0 + ta], ob = sm.posw[c * n_e + e0 + tb];
+          const TW x0 = min_image<TW>(pa - pb, Lw, iLw), x1 = min_image<TW>(pa - ob, Lw, iLw);
+          const TW x2 = min_image<TW>(oa - pb, Lw, iLw), x3 = min_image<TW>(oa - ob, Lw, iLw);
+          d2[0] += x0 * x0; d2[1] += x1 * x1; d2[2] += x2 * x2; d2[3] += x3 * x3;
+        }
+        q = (jastrow_value_r2<TW>(jt, 1, d2[0]) - jastrow_value_r2<TW>(jt, 1, d2[1])) -
+            (jastrow_value_r2<TW>(jt, 1, d2[2]) - jastrow_value_r2<TW>(jt, 1, d2[3]));
+      }
+      sm.Q[ta * kWinP + tb] = q;
+    }
+  }
 
   // ---- the moves
   double logdet = 0.0, sgn = 1.0, lprod = 1.0;   // ln|det| = logdet + ln lprod + lexp ln 2
@@ -253,12 +298,11 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     TW v[7] = {0, 0, 0, 0, 0, 0, 0};
     if (!det) {
       if (tid == kCopier) copy_step(pend, m - 1);
-      const TW rn[3] = {sm.propw[4 * t], sm.propw[4 * t + 1], sm.propw[4 * t + 2]};
-      if (!trace) {
-        v[0] = jastrow_delta_value<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, tid, jn);
-      } else {
+      if (trace) {
+        // the gradient of J at r' for the trace (Delta J itself comes from jb and Q)
+        const TW rn[3] = {sm.propw[4 * t], sm.propw[4 * t + 1], sm.propw[4 * t + 2]};
         TW g[3];
-        v[0] = jastrow_delta_grad<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, tid, jn, g);
+        (void)jastrow_delta_grad<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, tid, jn, g);
         v[1] = g[0]; v[2] = g[1]; v[3] = g[2];
       }
     } else {
@@ -315,28 +359,27 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     }
     if (trace) {
       warp_sum<7, TW>(v);
-    } else {
+      if (lane == 0)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        for (int k = 0; k < 7; ++k) sm.red[warp * 8 + k] = v[k];
     }
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 7; ++k) sm.red[warp * 8 + k] = v[k];
     __syncthreads();
     if (warp == 0) {
       TW tot[7] = {0, 0, 0, 0, 0, 0, 0};
-      if (!trace) {
-        TW tv = lane < nw ? sm.red[lane * 8] : TW(0);
-#pragma unroll
-        for (int o = nw / 2; o > 0; o >>= 1) tv += __shfl_xor_sync(0xffffffffu, tv, o);
-        tot[0] = tv;
-      } else {
+      if (trace) {
         TW tv = TW(0);
         if (lane < 7)
 #pragma unroll
           for (int q = 0; q < nw; ++q) tv += sm.red[q * 8 + lane];
 #pragma unroll
         for (int k = 0; k < 7; ++k) tot[k] = __shfl_sync(0xffffffffu, tv, k);
+      }
+      {
+        // Delta J = jb[t] + sum over the window's moves of Q[t][t_l]
+        TW dj = lane < m ? sm.Q[t * kWinP + sm.wt[lane]] : TW(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dj += __shfl_xor_sync(0xffffffffu, dj, o);
+        tot[0] = sm.jb[t] + dj;
       }
       if (lane == 0) {
         const TW R = sm.sc[6] + sm.sc[7], dJ = tot[0];
