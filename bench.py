@@ -194,15 +194,18 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of each kernel
-# class, from one ncu capture of the 512-electron FP32 workload at 200 walkers and k = 16
+# class, from ncu captures of the 512-electron FP32 workload at 200 walkers
 # (profiles/kernels_sj512_200walkers_ncu_full.md), scaled to a full launch by the units it
-# processes: (bytes per unit, unit)
+# processes: [(bytes per unit, unit, delay rank of the capture or None where the kernel does
+# not depend on it)]. A k-dependent entry is used only at its own k.
 TRAFFIC_SJ512_FP32 = {
-    "vgl": (2.645e9 / 51200, "move"),        # k_vgl_proposals: 51,200 moves per launch
-    "flush": (62.85e6 / 200, "walker"),      # k_flush_tc: one spin block of 200 walkers
-    "refine": (186.2e6 / 200, "walker"),     # k_refine_residual_tc
-    "refine_update": (174.4e6 / 200, "walker"),  # k_refine_update_tc
-    "energy": (530.1e6 / 200, "walker"),     # k_local_energy
+    "vgl": [(2.645e9 / 51200, "move", None)],      # k_vgl_proposals: 51,200 moves per launch
+    "sweep": [(37.585e6 / 6400, "move", 32)],      # k_sweep_win: 32 moves x 200 walkers
+    "flush": [(62.85e6 / 200, "walker", 16),       # k_flush_tc<16>: one spin block of 200 walkers
+              (67.978e6 / 200, "walker", 32)],     # k_flush_tc<32>
+    "refine": [(186.2e6 / 200, "walker", None)],   # k_refine_residual_tc
+    "refine_update": [(174.4e6 / 200, "walker", None)],  # k_refine_update_tc
+    "energy": [(530.1e6 / 200, "walker", None)],   # k_local_energy
 }
 
 
@@ -231,8 +234,12 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
                            f"VGL written = {per} B per move"}
     elif name == "sweep":
         per = 5 * ld * tw + 3 * ns * tw
+        # batched Metropolis launches (k >= 4, flushed between launches, k <= 32) run the
+        # pair-matrix kernel; drift moves and in-kernel flushes the original one
+        batched = (spec.move == "metropolis" and 4 <= delay_k <= 32 and
+                   not (reinv_period > 0 and precision == "fp64"))
         out = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "achieved": per * moves / sec / 1e9,
-               "kernel": "k_sweep",
+               "kernel": "k_sweep_win" if batched else "k_sweep",
                "per_unit": f"proposal VGL row 5*N_orb*{tw} B + inverse row and the window rows "
                            f"Phi, U 3*N_s*{tw} B = {per} B per move"}
     elif name == "flush":
@@ -269,13 +276,15 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
     if out is not None:
         out["frac"] = out["achieved"] / out["peak"]
         out["traffic"] = None
-        t = TRAFFIC_SJ512_FP32.get(name) if (spec.name == "sj512" and precision == "fp32") else None
+        cands = TRAFFIC_SJ512_FP32.get(name, []) if (spec.name == "sj512" and precision == "fp32") else []
+        t = next((c for c in cands if c[2] in (None, delay_k)), None)
         if t is not None:
-            per_unit, unit = t
+            per_unit, unit, kcap = t
             units = moves if unit == "move" else spec.n_walkers
             out["traffic"] = per_unit * units
-            out["traffic_note"] = (f"ncu DRAM bytes per {unit} at 200 walkers, k = 16, "
-                                   f"scaled to this launch's {units:.0f} {unit}s")
+            out["traffic_note"] = (f"ncu DRAM bytes per {unit} at 200 walkers"
+                                   + (f", k = {kcap}" if kcap else "")
+                                   + f", scaled to this launch's {units:.0f} {unit}s")
         out["avg_launch_ms"] = sec * 1e3
     return out
 
