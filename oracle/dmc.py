@@ -7,7 +7,10 @@ weight is multiplied by the branching Green's function of Eq. pmc:g_growth,
 averages are weighted (Eq. pmc:weighted_average), and the walker is replaced by
 M = INT(w + xi) copies with xi uniform in (0, 1); M = 0 removes it.
 
-Adopted readings (the paper leaves them open; parity unpinned, self-consistency only):
+Adopted readings (the paper leaves them open, so no value of the paper can pin them; the
+tests pin the invariants any population control must keep: an exact fixed point when E_T
+equals a constant E_L at the target population, a negative feedback that returns an
+off-target population to the target, and unique walker IDs under branching):
 * copies are renormalised to weight 1;
 * the first copy keeps the parent's walker ID and every further copy takes the next
   value of a per-system counter, copies being appended in parent order;
@@ -15,8 +18,8 @@ Adopted readings (the paper leaves them open; parity unpinned, self-consistency 
 * E_T <- E_w - ln(N_w / N_target) / (10 tau), E_w being this step's weighted mean E_L
   (population control by trial-energy feedback, Sec. "Diffusion Monte Carlo").
 
-Pin: with E_L constant (plane-wave determinant without Jastrow or potential) every
-weight equals exp(-tau (E - E_T)) exactly.
+Pins: with E_L constant (plane-wave determinant without Jastrow or potential) every
+weight equals exp(-tau (E - E_T)) exactly; the invariants above.
 """
 from __future__ import annotations
 

@@ -107,3 +107,57 @@ def test_fixed_node_rejects_sign_changes():
             s.sweep(w, t, fixed_node=True, trace=rows)
         rows = np.array(rows)
         assert not np.any((rows[:, 0] < 0) & (rows[:, 7] == 1))
+
+
+def _constant_el_population(offset, n=8, capacity=64, tau=0.05):
+    """Plane-wave determinant without Jastrow or potential: E_L is the same constant for
+    every configuration, so the branching weights depend on E_T alone."""
+    spec = dataclasses.replace(spec_for("pw14"), move="drift", step=tau)
+    d = build_inputs(spec, n_walkers=n)
+    s = OracleSystem(d, orbitals="planewave")
+    e_kin = 2 * 6 * (2 * np.pi / 10) ** 2 / 2
+    return DMCPopulation(s, d["pos"], list(range(n)), E_T=e_kin + offset,
+                         capacity=capacity), e_kin
+
+
+def test_dmc_population_control_fixed_point():
+    # E_T equal to the constant E_L and the population at its target: every weight is one,
+    # each walker survives exactly once under its own ID, and E_T stays put
+    pop, E = _constant_el_population(0.0)
+    ids0 = [x.wid for x in pop.walkers]
+    for t in range(6):
+        sum_w, e_mean, w = pop.step(t)
+        assert np.allclose(w, 1.0, rtol=0, atol=1e-12)
+        assert [x.wid for x in pop.walkers] == ids0
+        assert abs(pop.E_T - E) < 1e-10
+
+
+def test_dmc_population_control_is_negative_feedback():
+    # twelve walkers against a target of eight, E_T at the constant E_L: the trial-energy
+    # feedback must lower E_T and bring the population back to the target instead of letting
+    # it run away (a feedback of the wrong sign reaches the capacity within about 20 steps)
+    pop, E = _constant_el_population(0.0, n=12, capacity=64)
+    pop.n_target = 8
+    sizes, e_t = [], []
+    for t in range(60):
+        pop.step(t)
+        sizes.append(len(pop.walkers))
+        e_t.append(pop.E_T)
+    assert 0 < min(sizes) and max(sizes) < 24, sizes
+    assert 4 <= np.mean(sizes[-30:]) <= 12, sizes
+    assert e_t[0] < E                         # above the target: E_T drops below E_L
+    assert abs(np.mean(e_t[-30:]) - E) < 1.0
+    ids = [x.wid for x in pop.walkers]
+    assert len(set(ids)) == len(ids)
+
+
+def test_dmc_branching_ids_stay_unique_under_growth():
+    # weights near 2.5: every walker leaves two or three copies; the IDs of the population
+    # stay unique and the copies stay within the capacity
+    pop, E = _constant_el_population(math.log(2.5) / 0.05, n=6, capacity=40)
+    for t in range(3):
+        pop.step(t)
+        ids = [x.wid for x in pop.walkers]
+        assert len(set(ids)) == len(ids)
+        assert len(ids) <= 40
+    assert len(pop.walkers) > 6
