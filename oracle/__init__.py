@@ -13,7 +13,8 @@ scratch, and the Jastrow factor is recomputed over all pairs. Each module cites 
 section or equation of the paper it follows.
 
 Parity status of every function is listed in the module docstrings; the pins are the
-``-m "not gpu"`` tests in ``tests/test_oracle_*.py``. Parity unpinned: the DMC
-trial-energy feedback constant and the walker-ID assignment of branched walkers only
-have self-consistency checks (they are adopted readings, not physics the paper fixes).
+``-m "not gpu"`` tests in ``tests/test_oracle_*.py``. The DMC trial-energy feedback
+constant and the walker-ID assignment of branched walkers are adopted readings the paper
+gives no values for; they are pinned by the invariants any population control keeps (an
+exact fixed point at the target, a negative feedback, unique IDs), not by values.
 """
