@@ -17,9 +17,11 @@ and accepts with a uniform variate. The counter layout below is an adopted readi
 * DMC branching of walker w at step t: block (t, 0xB, w, 2) word 0;
 * a word w maps to the open interval (0, 1) as (w + 0.5) * 2**-32.
 
-Pins: uniformity and independence statistics (CPU tests) and bit-exact agreement with
-the Philox4_32_10 generator of the CUDA toolkit's cuRAND library at matching key and
-counter (GPU test).
+Pins: bit-exact agreement with an independent implementation, the Philox4_32_10 generator
+of NVIDIA's cuRAND library, run (never disassembled) at matching key and counter: its host
+generator on the CPU covers counter words 0-2 and the key schedule
+(tests/test_oracle_philox_curand.py), its device API on the GPU covers counter word 3
+(tests/test_gpu_philox_curand_device.py); plus uniformity and independence statistics.
 """
 from __future__ import annotations
 

@@ -1,7 +1,9 @@
-"""Pins of the oracle's Philox4x32-10 generator and move draws (CPU).
+"""Statistical checks of the oracle's Philox4x32-10 generator and move draws (CPU).
 
-The bit-exact pin against an independent implementation (cuRAND's Philox4_32_10) is the
-GPU test ``test_gpu_philox_vs_curand``; here: statistics, avalanche and structure.
+The bit-exact pins against an independent implementation (cuRAND's Philox4_32_10) are in
+``test_oracle_philox_curand.py`` (host generator, CPU) and
+``test_gpu_philox_curand_device.py`` (device API); here: statistics, avalanche and
+structure.
 """
 import numpy as np
 
