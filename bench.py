@@ -44,7 +44,13 @@ def parse_args():
                    help="delay rank k, or 'auto': the fastest of 8, 16, 32 on this workload "
                         "(timed by the package's tuner before the timed region)")
     p.add_argument("--reinv-period", type=int, default=128)
-    p.add_argument("--fp64-steps", type=int, default=4)
+    p.add_argument("--logdet-period", type=int, default=1024,
+                   help="moves of a spin block between log-determinant anchors (a multiple of "
+                        "--reinv-period; 0 = never)")
+    p.add_argument("--fp64-steps", type=int, default=10)
+    p.add_argument("--fp64-warmup", type=int, default=3)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the extra lines (BF16 table, batched DMC) after the headline")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--cpu-cores", type=int, default=0)
     p.add_argument("--no-cpu", action="store_true")
@@ -70,13 +76,15 @@ def system_desc(spec):
             f"Metropolis sigma={spec.step}")
 
 
-def workload(spec, precision, delay_k, reinv_period, on_accepted=False):
+def workload(spec, precision, delay_k, reinv_period, on_accepted=False, logdet_period=0):
     tab = {"fp32": "FP32", "bf16": "BF16", "fp64": "FP64"}[precision]
     upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
     what = "accepted moves" if on_accepted else "moves"
     re = (("FP64 re-inversion" if precision == "fp64" else "re-inversion (error-free Newton step)")
           + f" every {reinv_period} {what}") if reinv_period else "no re-inversion"
-    return f"{system_desc(spec)}; GPU: {tab} table, {upd}, {re}"
+    ld = (f", ln|det| anchored (error-free FP32 LU) every {logdet_period} moves"
+          if logdet_period and precision != "fp64" else "")
+    return f"{system_desc(spec)}; GPU: {tab} table, {upd}, {re}{ld}"
 
 
 def table_bytes(spec, precision):
@@ -194,8 +202,8 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of each kernel
-# class, from ncu captures of the 512-electron FP32 workload at 200 walkers
-# (profiles/kernels_sj512_200walkers_ncu_full.md), scaled to a full launch by the units it
+# class, from ncu captures of the 512-electron FP32 workload at 200 walkers (the kernel
+# summaries committed beside this file), scaled to a full launch by the units it
 # processes: [(bytes per unit, unit, delay rank of the capture or None where the kernel does
 # not depend on it)]. A k-dependent entry is used only at its own k.
 TRAFFIC_SJ512_FP32 = {
@@ -256,6 +264,9 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
         peak = peaks.get("bf16_tflops", 1899.6)
         out = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                "achieved": per * spec.n_walkers / sec / 1e12,
+               "method_achieved": 2 * ns ** 3 * spec.n_walkers / sec / 1e12,
+               "method_note": "the method's own work, one 2*N_s^3 residual product per walker "
+                              "and spin block, over the same time",
                "kernel": "k_refine_scales + k_refine_residual_tc",
                "per_unit": f"{pairs} slice pairs x 2*N_s^3 = {per} BF16 tensor flop per walker and "
                            f"spin block (peak: measured cuBLAS BF16 burst)"}
@@ -265,9 +276,21 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
         peak = peaks.get("bf16_tflops", 1899.6) * (1.1 / 2.25)
         out = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
                "achieved": per * spec.n_walkers / sec / 1e12,
-               "kernel": "k_refine_update_tc + k_refine_commit",
+               "kernel": "k_refine_update_tc + k_refine_fallback",
                "per_unit": f"3 x 2*N_s^3 = {per} TF32 tensor flop per walker and spin block (peak: "
                            f"measured BF16 burst x the nominal TF32/BF16 ratio 1.1/2.25)"}
+    elif name == "logdet":
+        # the LU of the log-determinant anchor: (2/3) N_s^3 flops of the method per walker and
+        # spin block, on the FP32 pipe (the error-free transformations cost ~10 FP32
+        # operations per update: the implementation's own count is reported beside it)
+        per = 2.0 / 3.0 * ns ** 3
+        peak = peaks.get("fp32_tflops") or 2 * N_SM * FP32_LANES * sm_mhz * 1e6 / 1e12
+        out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+               "achieved": per * spec.n_walkers / sec / 1e12,
+               "kernel": "k_logdet_anchor",
+               "implementation_tflops": 10 * (per / 2) * spec.n_walkers / sec / 1e12,
+               "per_unit": f"(2/3)*N_s^3 = {per:.0f} FP32 flop of the LU per walker and spin block "
+                           f"(peak: FP32 FMA rate measured by qmc_measure_rates)"}
     elif name == "energy":
         per = spec.n_elec * 5 * ld * tw + (spec.n_up ** 2 + spec.n_dn ** 2) * tw + 24 * spec.n_elec
         out = {"bound": "hbm", "unit": "GB/s", "peak": hbm,
@@ -327,6 +350,7 @@ def run_ours(args, spec, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
+    rates = q.measure_rates()                                # FP32/FP64 FMA, L2 read
     inputs = build_inputs(spec, seed=0)
     philox_seed, pos_seed = replica_seeds(rank)
     inputs["seed"] = philox_seed                            # Philox stream of this replica
@@ -372,9 +396,11 @@ def run_ours(args, spec, rank, world, local_rank):
                   "chosen": k_best}
     else:
         args.delay_k = int(args.delay_k)
+    logdet_period = 0 if (args.reinv_on_accepted or args.precision == "fp64") else args.logdet_period
     sysm = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
                                 reinv_period=args.reinv_period,
-                                reinv_on_accepted=args.reinv_on_accepted)
+                                reinv_on_accepted=args.reinv_on_accepted,
+                                logdet_period=logdet_period)
     ms, prof, launches, clocks, e_loc = timed(sysm, args.steps, args.warmup, profile=True)
     value = whole_job_rate(world, moves_per_step * args.steps, ms / 1e3)
 
@@ -404,16 +430,63 @@ def run_ours(args, spec, rank, world, local_rank):
            "includes": "walker creation from pinned host positions (orbitals + FP64 inversion "
                        "of every Slater matrix), per-sweep E_L and ln|Psi| read-back, final "
                        "positions read-back"}
+    # the same with the walkers already resident (steady state): each sweep followed by the
+    # device->host read of E_L and ln|Psi|; no positions move over the bus
+    w = q.Walkers(sysm, pos_h)
+    for _ in range(args.warmup):
+        w.sweep(1, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        w.sweep(1, stream)
+        w.measure(e_h, l_h, stream)
+    barrier()
+    e2s_s = max_over_ranks(time.perf_counter() - t0, dist)
+    w.close()
+    e2e_steady = {"value": whole_job_rate(world, moves_per_step * e2e_steps, e2s_s), "unit": UNIT,
+                  "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 2 * 8 * spec.n_walkers,
+                  "steps": e2e_steps,
+                  "includes": "resident walkers after warm-up sweeps; every sweep followed by the "
+                              "pinned read-back of E_L and ln|Psi| (host clock)"}
     sysm.close()
 
     fp64 = None
     if not args.no_fp64:
         s64 = q.system_from_inputs(inputs, precision="fp64", delay_k=1, reinv_period=0)
-        ms64, _, _, _, e64 = timed(s64, args.fp64_steps, 1)
+        ms64, _, _, _, e64 = timed(s64, args.fp64_steps, args.fp64_warmup)
         s64.close()
         v64 = whole_job_rate(world, moves_per_step * args.fp64_steps, ms64 / 1e3)
         fp64 = {"value": v64, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                "warmup": args.fp64_warmup,
                 "dtype": "f64", "update": "Sherman-Morrison rank-1, no re-inversion"}
+
+    # extra lines the driver's record keeps beside the headline: the BF16-table form at the
+    # same k, and the batched uneven DMC workload
+    extras = None
+    if not args.no_extras and world == 1:
+        extras = {}
+        sb = q.system_from_inputs(inputs, precision="bf16", delay_k=args.delay_k,
+                                  reinv_period=args.reinv_period, logdet_period=logdet_period)
+        msb, profb, _, _, _ = timed(sb, 10, args.warmup, profile=True)
+        sb.close()
+        vb = whole_job_rate(world, moves_per_step * 10, msb / 1e3)
+        extras["bf16_table"] = {"value": vb, "unit": UNIT, "ms_per_step": msb / 10, "steps": 10,
+                                "workload": workload(spec, "bf16", args.delay_k, args.reinv_period,
+                                                     logdet_period=logdet_period),
+                                "prof": profb}
+        if args.reinv_period > 0 and logdet_period != args.reinv_period and args.precision != "fp64":
+            # the log-determinant anchor at every re-inversion (the 128-move cadence the
+            # 512-electron workload names for re-inversion and log-det)
+            sa = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+                                      reinv_period=args.reinv_period,
+                                      logdet_period=args.reinv_period)
+            msa, profa, _, _, _ = timed(sa, 10, args.warmup, profile=True)
+            sa.close()
+            extras["anchor_every_reinversion"] = {
+                "value": whole_job_rate(world, moves_per_step * 10, msa / 1e3), "unit": UNIT,
+                "ms_per_step": msa / 10, "steps": 10, "logdet_period": args.reinv_period,
+                "prof": profa}
+        extras["dmc"] = dmc_measure(args, rank, world, 10, dist)
 
     if rank != 0:
         return
@@ -421,6 +494,7 @@ def run_ours(args, spec, rank, world, local_rank):
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
         peaks = json.load(open(pk))
+    peaks.update({k: v for k, v in rates.items() if v})
     prof_ms, prof_n = prof
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     roof, per_class = roofline(prof_ms, prof_n, spec, args.precision, moves_per_step, args.steps,
@@ -429,6 +503,14 @@ def run_ours(args, spec, rank, world, local_rank):
     kernels = {n: {"ms_per_step": float(prof_ms[i]) / args.steps, "launches": int(prof_n[i]),
                    "roofline": per_class.get(n)}
                for i, n in enumerate(qb.KERNEL_CLASSES) if prof_n[i]}
+    for key, prec in (("bf16_table", "bf16"), ("anchor_every_reinversion", args.precision)):
+        if extras is None or key not in extras:
+            continue
+        pm, pn = extras[key].pop("prof")
+        rb, _ = roofline(pm, pn, spec, prec, moves_per_step, 10, peaks, args.delay_k,
+                         args.reinv_period, sm_mhz)
+        extras[key]["roofline"] = rb
+        extras[key]["kernels"] = {n: float(pm[i]) / 10 for i, n in enumerate(qb.KERNEL_CLASSES) if pn[i]}
     cpu = None
     if pool is not None:
         nw = min(spec.n_walkers, 2 * cores)
@@ -440,7 +522,7 @@ def run_ours(args, spec, rank, world, local_rank):
             "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload(spec, args.precision, args.delay_k, args.reinv_period,
-                                            args.reinv_on_accepted),
+                                            args.reinv_on_accepted, logdet_period),
                        "walkers_per_gpu": spec.n_walkers, "electrons": spec.n_elec,
                        "moves_per_step": moves_per_step * world,
                        "l2": f"inputs larger than L2: {table_bytes(spec, args.precision) / 1e6:.0f} MB "
@@ -448,7 +530,8 @@ def run_ours(args, spec, rank, world, local_rank):
                        "parallelism": f"replicas x{world}",
                        "delay_k_autotune": tuning},
             "roofline": roof, "gpu_launches": launches, "kernels": kernels, "clocks": clocks,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64,
+            "e2e": e2e, "e2e_steady": e2e_steady, "cpu_baseline": cpu, "fp64_form": fp64,
+            "measured_rates": rates, "extras": extras,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "e_local_mean": float(np.mean(e_loc))}
     print(json.dumps(line), flush=True)
@@ -457,29 +540,27 @@ def run_ours(args, spec, rank, world, local_rank):
 DMC_SYSTEMS = ("dmc64", "dmc192", "dmc384")
 
 
-def run_dmc(args, rank, world, local_rank):
-    """Batched uneven DMC: three systems advance together each step (drift-diffusion sweep,
-    local energy, branching and compaction; one stream per system). moves/s counts
-    sum_s N_e(s) * N_w(s, step) over the timed steps, each step bracketed by CUDA events on
-    the caller's stream (the systems' streams join it)."""
+def dmc_measure(args, rank, world, n_steps, dist=None):
+    """Batched uneven DMC: three systems advance together each step (drift-diffusion sweep
+    with the drift rescaled near nodes, local energy, branching with the effective time step,
+    compaction; one stream per system). moves/s counts sum_s N_e(s) * N_w(s, step) over the
+    timed steps, each step bracketed by CUDA events on the caller's stream (the systems'
+    streams join it). Returns the measurement as a dictionary (every rank)."""
     import numpy as np
     import torch
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import paper_1802_06922_gb300 as q
     from synthetic import build_inputs, spec_for
     stream = torch.cuda.current_stream()
     dmc_k = 16 if args.delay_k == "auto" else int(args.delay_k)
+    precision = "fp32" if args.precision == "fp64" and args.workload == "vmc" else args.precision
     systems, pos, et, specs = [], [], [], []
     for name in DMC_SYSTEMS:
         spec = spec_for(name)
         inputs = build_inputs(spec, seed=0)
         inputs["seed"] = replica_seeds(rank)[0]
-        s = q.system_from_inputs(inputs, precision=args.precision, delay_k=dmc_k,
-                                 reinv_period=args.reinv_period, move="drift", step=spec.step)
+        s = q.system_from_inputs(inputs, precision=precision, delay_k=dmc_k,
+                                 reinv_period=args.reinv_period, move="drift", step=spec.step,
+                                 drift_a=1.0)
         # equilibrate with drift-diffusion VMC sweeps before branching starts (uniform
         # random starting points put some walkers next to a node, where E_L is extreme)
         w = q.Walkers(s, inputs["pos"])
@@ -492,6 +573,7 @@ def run_dmc(args, rank, world, local_rank):
         et.append(float(np.median(e)))
         specs.append(spec)
     d = q.DMC(systems, pos, et, capacity_factor=2)
+    d.set_mode(effective_tau=True, reconfigure=False)
     d.step(args.warmup, stream)
     torch.cuda.synchronize()
     l0 = d.launch_count()
@@ -499,7 +581,7 @@ def run_dmc(args, rank, world, local_rank):
     pops = []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
+    for _ in range(n_steps):
         e0.record(stream)
         d.step(1, stream)
         e1.record(stream)
@@ -514,27 +596,44 @@ def run_dmc(args, rank, world, local_rank):
     d.close()
     for s in systems:
         s.close()
-    if rank != 0:
-        return
-    value = whole_job_rate(world, moves, total_ms / 1e3)
-    line = {"metric": "electron moves/sec, batched uneven DMC (sum over systems of N_e x N_w per step)",
-            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": "; ".join(
-                           f"{sp.name}: {sp.n_elec} electrons, {sp.grid}^3 table, {sp.n_orb} "
-                           f"orbitals, {sp.n_walkers} target walkers" for sp in specs)
-                       + f"; drift-diffusion tau={specs[0].step}, branching, E_T feedback, "
-                         f"delayed rank-{dmc_k}, re-inversion every {args.reinv_period} moves; "
-                         f"walkers equilibrated by {args.dmc_vmc_sweeps} VMC sweeps, E_T from "
-                         f"their median E_L",
-                       "parallelism": f"replicas x{world}; systems on concurrent streams"},
+    return {"metric": "electron moves/sec, batched uneven DMC (sum over systems of N_e x N_w per step)",
+            "value": whole_job_rate(world, moves, total_ms / 1e3), "unit": UNIT,
+            "ms_per_step": total_ms / n_steps, "steps": n_steps, "warmup": args.warmup,
+            "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[precision],
+            "workload": "; ".join(
+                f"{sp.name}: {sp.n_elec} electrons, {sp.grid}^3 table, {sp.n_orb} orbitals, "
+                f"{sp.n_walkers} target walkers" for sp in specs)
+            + f"; drift-diffusion tau={specs[0].step} with nodal drift rescaling (a = 1), "
+              f"branching with the effective time step, E_T feedback, delayed rank-{dmc_k}, "
+              f"re-inversion every {args.reinv_period} moves; walkers equilibrated by "
+              f"{args.dmc_vmc_sweeps} VMC sweeps, E_T from their median E_L; systems on "
+              f"concurrent streams",
             "populations_first_last": [pops[0], pops[-1]],
             "e_mean_last": [float(x["e_mean"]) for x in final],
             "e_trial_last": [float(x["e_trial_next"]) for x in final],
             "gpu_launches": launches}
+
+
+def run_dmc(args, rank, world, local_rank):
+    """The batched uneven DMC workload as its own bench line."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    r = dmc_measure(args, rank, world, args.steps, dist)
+    if rank != 0:
+        return
+    line = {"metric": r["metric"], "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": r["dtype"], "data": "synthetic",
+            "config": {"workload": r["workload"],
+                       "parallelism": f"replicas x{world}; systems on concurrent streams"},
+            "populations_first_last": r["populations_first_last"],
+            "e_mean_last": r["e_mean_last"], "e_trial_last": r["e_trial_last"],
+            "gpu_launches": r["gpu_launches"]}
     print(json.dumps(line), flush=True)
 
 

@@ -97,10 +97,25 @@ typedef struct {
                               sums R with compensated arithmetic) */
   int reinv_on_accepted;   /* 1: count accepted moves of the determinant; 0: proposed moves */
   uint64_t seed;           /* Philox4x32-10 key of every draw */
+  int logdet_period;       /* single-precision forms with batched re-inversion (delay_k >= 4,
+                              reinv_on_accepted = 0): every this many moves of a spin block,
+                              right after its re-inversion, ln|det A| is recomputed to FP64-class
+                              accuracy by an LU factorisation in FP32 whose rounding errors are
+                              captured exactly and folded back through the refined inverse;
+                              between anchors ln|det| is the FP64 sum of the moves' ln|R|.
+                              A positive multiple of reinv_period, or 0 = never. Ignored by
+                              QMC_FP64, whose accumulated ln|det| needs no anchor. */
+  double drift_a;          /* QMC_MOVE_DRIFT: > 0 rescales the drift near nodes of Psi
+                              (Umrigar, Nightingale and Runge; Sec. "Projector Monte Carlo"):
+                              the drift displacement tau v becomes
+                              tau v 2 / (1 + sqrt(1 + 2 a |v|^2 tau)), below sqrt(2 tau / a)
+                              for any v, in the proposal and in the Green's-function ratio of
+                              the acceptance; 0 = the plain drift. */
 } qmc_system_desc;
 
 /* Creates a system. Fails with QMC_EINVAL for n_up or n_dn outside [0, 1024], n_up+n_dn
- * = 0, L <= 0, step < 0, delay_k outside [1, 64] or an unknown precision/move. */
+ * = 0, L <= 0, step < 0, delay_k outside [1, 64], an unknown precision/move, or a
+ * logdet_period that is negative or not a multiple of a positive reinv_period. */
 qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out);
 
 /* Sets the B-spline orbital table (Sec. "B-spline basis sets"). coef is host memory
@@ -119,17 +134,21 @@ qmc_status qmc_system_set_spline(qmc_system_t sys, int nx, int ny, int nz, int n
 qmc_status qmc_system_set_jastrow(qmc_system_t sys, int which, int M, double rcut,
                                   const double* p, int cusp_set, double cusp);
 
-/* Creates n_walkers walkers with IDs 0..n_walkers-1 at positions pos (host
- * [n_walkers][n_up+n_dn][3], wrapped into the cell). Evaluates the orbitals at every
- * electron, inverts each Slater matrix in FP64 and records ln|det| and its sign.
- * Synchronous. QMC_ESINGULAR if a Slater matrix is singular. */
+/* Creates n_walkers walkers (the ensemble of independent Markov chains of Sec.
+ * "Variational Monte Carlo", each a configuration R of all electrons) with IDs
+ * 0..n_walkers-1 at positions pos (host or device [n_walkers][n_up+n_dn][3], wrapped into
+ * the cell). Evaluates the orbitals at every electron, inverts each Slater matrix in FP64
+ * (A[e][j] = phi_j(r_e), Sec. "Multi-Determinant Slater-Jastrow Form") and records ln|det|
+ * and its sign. Synchronous. QMC_ESINGULAR if a Slater matrix is singular. */
 qmc_status qmc_walkers_create(qmc_system_t sys, int n_walkers, const double* pos,
                               qmc_walkers_t* out);
 
-/* Advances every walker by n_sweeps sweeps; a sweep proposes one move for each electron
- * in index order. Uses (and then advances) the walker set's sweep counter, which is part
- * of every Philox counter, so the result depends only on the seed, the walker IDs, the
- * positions and the counter. Asynchronous on `stream`. */
+/* Advances every walker by n_sweeps sweeps of particle-by-particle moves (Sec. "Trial
+ * Moves": one electron at a time, a Gaussian or drift-diffusion proposal accepted with
+ * Eq. accept_reject); a sweep proposes one move for each electron in index order, then
+ * measures the local energy. Uses (and then advances) the walker set's sweep counter,
+ * which is part of every Philox counter, so the result depends only on the seed, the walker
+ * IDs, the positions and the counter. Asynchronous on `stream`. */
 qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream);
 
 /* Local energy and ln|Psi| of every walker's current configuration
@@ -160,7 +179,9 @@ qmc_status qmc_replay_decisions(qmc_walkers_t w, const uint8_t* accept_bits, int
 qmc_status qmc_get_positions(qmc_walkers_t w, double* pos, void* stream);
 
 /* Serialised walker state (positions, walker IDs, weights, sweep counter, seed) for
- * checkpoint/resume. qmc_get_state with buf = NULL stores the needed size in *len.
+ * checkpoint/resume: a walker of Sec. "Diffusion Monte Carlo" is its configuration and
+ * weight, and the Philox counters make the continuation reproducible. qmc_get_state with
+ * buf = NULL stores the needed size in *len.
  * qmc_set_state rebuilds the inverses by FP64 re-inversion; QMC_ESTATE if the buffer does
  * not match this walker set's sizes. Synchronous. */
 qmc_status qmc_get_state(qmc_walkers_t w, void* buf, size_t* len);
@@ -175,6 +196,25 @@ qmc_status qmc_set_state(qmc_walkers_t w, const void* buf, size_t len);
  * QMC_EINVAL for a walker index outside [0, n_walkers) or spin outside {0, 1}. */
 qmc_status qmc_get_inverse(qmc_walkers_t w, int walker, int spin, double* out);
 qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out);
+
+/* ln|det A| and the sign of det A of every walker's two Slater matrices (Sec.
+ * "Multi-Determinant Slater-Jastrow Form"), as the walker set carries them: logdet and sign
+ * are [n_walkers][2] doubles (spin up, spin down), host or device, either may be NULL (not
+ * both). In the single-precision forms ln|det A| is the FP64 running sum of the ln|R| of
+ * the accepted moves since the last FP64 value (walker creation, an FP64 re-inversion or a
+ * log-determinant anchor). Synchronous; reports deferred device errors. */
+qmc_status qmc_get_logdet(qmc_walkers_t w, double* logdet, double* sign);
+
+/* Numerical health of the single-precision forms, per walker and spin block ([n_walkers][2]
+ * doubles each, host or device, either may be NULL):
+ *   residual      max |I - A X| measured by the block's last batched re-inversion before
+ *                 its Newton step (X the inverse it corrected); above 1e-2 (or infinite)
+ *                 means that re-inversion fell back to FP64 Gauss-Jordan;
+ *   logdet_shift  the change the last log-determinant anchor made to ln|det A| (anchored
+ *                 value minus the accumulated one): the drift of the accumulated sum since
+ *                 the previous FP64-class value.
+ * NaN where nothing has run yet. Synchronous. */
+qmc_status qmc_get_precision_report(qmc_walkers_t w, double* residual, double* logdet_shift);
 
 /* Waits for the walkers' queued work on `stream` and reports deferred device errors. */
 qmc_status qmc_check_errors(qmc_walkers_t w, void* stream);
@@ -206,8 +246,10 @@ qmc_status qmc_slater_invert(qmc_precision prec, const void* A, void* Binv, doub
  *   exceed 2^21 (for example 32 matrices of 256 x 256, or 8 of 512 x 512); a larger request
  *   fails with QMC_EINVAL before anything is enqueued. No cudaMalloc, cudaFree or other
  *   allocating routine is called.
- *   The first call on each device looks up the work area's device address with that device
- *   current; make that first call before any stream capture.
+ *   Each call whose stream is not being captured looks up the work area's device address
+ *   on the current device (so a context re-created by cudaDeviceReset is served too); a
+ *   call under stream capture reuses the address of the last uncaptured call on the device,
+ *   and fails with QMC_EINVAL if there was none: make the first call before any capture.
  *   Every call uses the same work area, which keeps the last call's contents. A call
  *   overwrites each work element before reading it, so nothing needs clearing, but calls
  *   whose kernels overlap on the GPU (different streams or host threads) race on the work
@@ -240,11 +282,33 @@ qmc_status qmc_dmc_create(qmc_system_t const* systems, const int* n_walkers,
                           const double* const* positions, const double* e_trial, int n_systems,
                           int capacity_factor, qmc_dmc_t* out);
 qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream);
+/* Refinements of the DMC step (Sec. "Diffusion Monte Carlo"), both off after create:
+ *   effective_tau  1: a walker's branching factor uses tau_eff = tau * (sum of |r' - r|^2 of
+ *                  its accepted moves) / (sum over all its proposed moves) of the step's
+ *                  sweep instead of tau (Umrigar, Nightingale and Runge);
+ *   reconfigure    1: population control by stochastic reconfiguration at a fixed walker
+ *                  count (Assaraf, Caffarel and Khelif) instead of M = floor(w + xi)
+ *                  branching: one comb of N teeth at (k + xi) W / N, k = 0..N-1, over the
+ *                  cumulative weights in walker order (W the total weight, xi from Philox
+ *                  block (step, 0xC, 0, 2) word 0); walker i gets the teeth falling in its
+ *                  interval, the last walker the remainder, so the count stays N; copies are
+ *                  placed and numbered as in branching and carry weight one. With N at its
+ *                  target the E_T feedback reduces to E_T = E_w.
+ * Applies to every system of d from the next step on. QMC_EINVAL for a NULL driver. */
+qmc_status qmc_dmc_set_mode(qmc_dmc_t d, int effective_tau, int reconfigure);
 qmc_status qmc_dmc_read(qmc_dmc_t d, int system, double* out);
 qmc_status qmc_dmc_walkers(qmc_dmc_t d, int system, int max_walkers, double* pos, uint32_t* ids,
                            double* e_local, int* n_out);
 int64_t qmc_dmc_launch_count(qmc_dmc_t d);
 void qmc_dmc_destroy(qmc_dmc_t d);
+
+/* Rates of the current device that bound the kernels neither the tensor cores nor HBM
+ * do (roofline denominators; no counterpart in the paper): out[0] = FP32 FMA throughput
+ * (TFLOP/s, an FMA counted as 2 flops), out[1] = FP64 FMA throughput (TFLOP/s), out[2] =
+ * read bandwidth of a 48 MiB L2-resident buffer (GB/s). Best of a few runs of dedicated
+ * kernels timed with CUDA events; clocks are not touched. Synchronous; allocates and frees
+ * 48 MiB of device memory. */
+qmc_status qmc_measure_rates(double* out);
 
 /* Kernel classes reported by qmc_profile_read. */
 typedef enum {
@@ -257,8 +321,9 @@ typedef enum {
   QMC_K_ACCUMULATE = 6,   /* FP64 reductions over walkers */
   QMC_K_FLUSH = 7,        /* batched application of the delayed-update windows */
   QMC_K_REFINE = 8,       /* single-precision re-inversion: error-free residual R = I - A X */
-  QMC_K_REFINE_UPDATE = 9,/* single-precision re-inversion: X <- X + X R, commit or FP64 fallback */
-  QMC_NKERNELS = 10
+  QMC_K_REFINE_UPDATE = 9,/* single-precision re-inversion: X <- X + X R, FP64 fallback */
+  QMC_K_LOGDET = 10,      /* log-determinant anchor (error-free FP32 LU) */
+  QMC_NKERNELS = 11
 } qmc_kernel;
 
 /* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA

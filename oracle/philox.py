@@ -79,6 +79,13 @@ def move_draws(seed: int, sweep: int, electron, walker_id):
     return np.stack([gx, gy, gz], -1), to_unit(b0)
 
 
+def comb_draw(seed: int, step: int):
+    """Uniform offset of the comb of one stochastic reconfiguration step (Sec. "Diffusion
+    Monte Carlo"), one per system and step: block (step, 0xC, 0, 2) word 0."""
+    w0, _, _, _ = philox4x32_10((step, 0xC, 0, 2), seed_key(seed))
+    return to_unit(w0)
+
+
 def branch_draw(seed: int, step: int, walker_id):
     """Uniform variate of the branching decision M = floor(w + xi) (Sec. "Diffusion
     Monte Carlo")."""

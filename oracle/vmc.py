@@ -38,6 +38,28 @@ from .wavefunction import SlaterJastrow
 TRACE_FIELDS = ("ratio", "dJ", "gx", "gy", "gz", "u", "A", "accepted")
 
 
+def drift_displacement(v, tau: float, a: float = 0.0):
+    """Drift part of a drift-diffusion step for an electron whose drift velocity is
+    v = grad_e ln|Psi| (3,).
+
+    a = 0: the plain short-time step tau v (Eq. pmc:driftdiffusion_step, reading 1).
+    a > 0: the drift rescaled near nodes of Psi following Umrigar, Nightingale and Runge
+    (J. Chem. Phys. 99, 2865 (1993)), which Sec. "Projector Monte Carlo" and Sec. "Diffusion
+    Monte Carlo" name without formulas: v is replaced by
+        vbar = v (-1 + sqrt(1 + 2 a |v|^2 tau)) / (a |v|^2 tau),
+    which tends to v where |v|^2 tau << 1 (far from a node) and keeps the displacement
+    vbar tau below sqrt(2 tau / a) where |v| diverges (next to a node)."""
+    v = np.asarray(v, dtype=np.float64)
+    if a <= 0.0:
+        return tau * v
+    v2 = float(v @ v)
+    x = 2.0 * a * v2 * tau
+    if x < 1e-12:
+        return tau * v
+    # (-1 + sqrt(1 + x)) / (x / 2) written without the cancellation of -1 + sqrt(1 + x)
+    return tau * v * 2.0 / (1.0 + np.sqrt(1.0 + x))
+
+
 @dataclasses.dataclass
 class Walker:
     R: np.ndarray              # (N_e, 3)
@@ -51,7 +73,7 @@ class Walker:
 class OracleSystem:
     """The wavefunction and move parameters of one system built by ``synthetic``."""
 
-    def __init__(self, inputs: dict, orbitals: str = "spline", coef=None):
+    def __init__(self, inputs: dict, orbitals: str = "spline", coef=None, drift_a: float = 0.0):
         spec = inputs["spec"]
         self.spec = spec
         self.L = spec.L
@@ -69,6 +91,7 @@ class OracleSystem:
                                 spec.kappa, spec.L, spec.with_potential)
         self.move = spec.move
         self.step = spec.step
+        self.drift_a = float(drift_a)   # > 0: nodal drift rescaling (see drift_displacement)
 
     def walker(self, R, wid) -> Walker:
         R = np.mod(np.array(R, dtype=np.float64), self.L)
@@ -89,9 +112,14 @@ class OracleSystem:
     # --------------------------------------------------------------------- sweep
     def sweep(self, w: Walker, t: int, fixed_node: bool = False,
               forced: Optional[np.ndarray] = None, trace: Optional[list] = None,
-              electrons=None) -> None:
+              electrons=None, conds: Optional[list] = None,
+              r2: Optional[list] = None) -> None:
         """One sweep t of walker w, in place. ``forced`` (N_e bools) replaces the
-        acceptance decisions (lockstep replay); ``trace`` collects one row per move."""
+        acceptance decisions (lockstep replay); ``trace`` collects one row per move;
+        ``conds`` (a diagnostic for the tests' error bounds, no effect on the chain)
+        collects max(cond_2(A), cond_2(A')) of the moved spin block per move; ``r2``, a
+        two-element list, accumulates the squared proposed displacements |r' - r|^2 of all
+        moves and of the accepted ones (the effective time step of a DMC step)."""
         wf, L = self.wf, self.L
         ne = w.R.shape[0]
         drift = self.move == "drift"
@@ -103,7 +131,7 @@ class OracleSystem:
             r_old = w.R[e].copy()
             if drift:
                 g_old = wf.grad_log_psi(w.R, e, np.linalg.inv(w.A[spin]))
-                r_new = r_old + tau * g_old + np.sqrt(tau) * xi
+                r_new = r_old + drift_displacement(g_old, tau, self.drift_a) + np.sqrt(tau) * xi
             else:
                 r_new = r_old + sigma * xi
             r_new = np.mod(r_new, L)
@@ -118,13 +146,15 @@ class OracleSystem:
             else:
                 ratio = s_new * w.sign[spin] * np.exp(ld_new - w.logdet[spin])
                 g_new = wf.grad_log_psi(R_new, e, np.linalg.inv(A_new))
+            if conds is not None:
+                conds.append(max(np.linalg.cond(w.A[spin]), np.linalg.cond(A_new)))
             J_new = wf.jas.value(R_new) if wf.jas is not None else 0.0
             dJ = J_new - w.J
             t_ratio = 1.0
+            d = min_image(r_new - r_old, L)
             if drift:
-                d = min_image(r_new - r_old, L)
-                fwd = d - tau * g_old
-                rev = -d - tau * g_new
+                fwd = d - drift_displacement(g_old, tau, self.drift_a)
+                rev = -d - drift_displacement(g_new, tau, self.drift_a)
                 t_ratio = np.exp((fwd @ fwd - rev @ rev) / (2.0 * tau))
             acc_prob = min(1.0, ratio * ratio * np.exp(2.0 * dJ) * t_ratio) if ratio != 0 else 0.0
             accept = bool(u < acc_prob)
@@ -135,6 +165,10 @@ class OracleSystem:
             if trace is not None:
                 trace.append((ratio, dJ, g_new[0], g_new[1], g_new[2], u, acc_prob,
                               float(accept)))
+            if r2 is not None:
+                r2[0] += float(d @ d)
+                if accept:
+                    r2[1] += float(d @ d)
             if accept:
                 w.R[e] = r_new
                 w.A[spin] = A_new
@@ -149,9 +183,10 @@ class OracleSystem:
 
 
 def run_vmc(system: OracleSystem, positions, walker_ids, n_sweeps: int, first_sweep: int = 0,
-            forced=None):
+            forced=None, conds: Optional[np.ndarray] = None):
     """Run n_sweeps of every walker. Returns (walkers, trace [n_w][sweeps*N_e][8],
-    energies [n_w][sweeps][3] = (E_L, kinetic, ln|Psi|))."""
+    energies [n_w][sweeps][3] = (E_L, kinetic, ln|Psi|)). ``conds``, if given, is filled
+    with the per-move condition numbers of ``OracleSystem.sweep`` ([n_w][sweeps*N_e])."""
     walkers = [system.walker(R, wid) for R, wid in zip(positions, walker_ids)]
     ne = system.spec.n_elec
     tr = np.zeros((len(walkers), n_sweeps * ne, len(TRACE_FIELDS)))
@@ -159,8 +194,11 @@ def run_vmc(system: OracleSystem, positions, walker_ids, n_sweeps: int, first_sw
     for k, w in enumerate(walkers):
         for s in range(n_sweeps):
             rows: List = []
+            cl = [] if conds is not None else None
             fb = None if forced is None else forced[k][s * ne:(s + 1) * ne]
-            system.sweep(w, first_sweep + s, fixed_node=False, forced=fb, trace=rows)
+            system.sweep(w, first_sweep + s, fixed_node=False, forced=fb, trace=rows, conds=cl)
             tr[k, s * ne:(s + 1) * ne] = np.array(rows)
+            if conds is not None:
+                conds[k, s * ne:(s + 1) * ne] = cl
             en[k, s] = system.measure(w)
     return walkers, tr, en

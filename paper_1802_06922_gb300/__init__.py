@@ -5,9 +5,9 @@ B-spline Jastrow factors) behind the C ABI of ``include/qmcgb.h``.
 The Python layer is a thin ctypes binding (``qmcgb``); the work runs in the CUDA
 kernels of ``libqmcgb.so`` built from ``csrc/`` for sm_103a.
 """
-from .qmcgb import (DMC, QMCError, System, Walkers, load, slater_invert,  # noqa: F401
-                    slater_invert_noalloc, system_from_inputs)
+from .qmcgb import (DMC, QMCError, System, Walkers, load, measure_rates,  # noqa: F401
+                    slater_invert, slater_invert_noalloc, system_from_inputs)
 from .autotune import tune_delay  # noqa: F401
 
-__all__ = ["DMC", "QMCError", "System", "Walkers", "load", "slater_invert",
+__all__ = ["DMC", "QMCError", "System", "Walkers", "load", "measure_rates", "slater_invert",
            "slater_invert_noalloc", "system_from_inputs", "tune_delay"]

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqmcgb.so")
-SOURCES = ["qmc_api.cu", "qmc_kernels_tw.cu", "qmc_kernels_tt.cu", "qmc_noalloc.cu"]
+SOURCES = ["qmc_api.cu", "qmc_kernels_tw.cu", "qmc_kernels_tt.cu", "qmc_noalloc.cu", "qmc_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "1444"]
 

@@ -97,6 +97,7 @@ struct qmc_walkers_s {
   int64_t launches = 0;
   bool energy_valid = false;
   int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
+  int since_anchor[2] = {0, 0};// proposed moves per spin since the last log-det anchor
   bool profiling = false;
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> events;
@@ -157,10 +158,13 @@ extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_
   if (!(d.L > 0.0) || !std::isfinite(d.L)) return fail(QMC_EINVAL, "L must be positive");
   if (d.n_ion < 0 || (d.n_ion > 0 && !d.ion_pos)) return fail(QMC_EINVAL, "bad ion list");
   if (!(d.step >= 0.0)) return fail(QMC_EINVAL, "step must be >= 0");
+  if (!(d.drift_a >= 0.0) || !std::isfinite(d.drift_a)) return fail(QMC_EINVAL, "drift_a must be >= 0");
   if (d.delay_k < 1 || d.delay_k > kMaxDelay) return fail(QMC_EINVAL, "delay_k must be in [1, %d]", kMaxDelay);
   if (d.prec < QMC_FP64 || d.prec > QMC_FP32_BF16TAB) return fail(QMC_EINVAL, "unknown precision");
   if (d.move != QMC_MOVE_METROPOLIS && d.move != QMC_MOVE_DRIFT) return fail(QMC_EINVAL, "unknown move");
   if (d.reinv_period < 0) return fail(QMC_EINVAL, "reinv_period must be >= 0");
+  if (d.logdet_period < 0 || (d.logdet_period > 0 && (d.reinv_period <= 0 || d.logdet_period % d.reinv_period)))
+    return fail(QMC_EINVAL, "logdet_period must be 0 or a positive multiple of reinv_period");
   qmc_system_s* s = new qmc_system_s;
   s->d = d;
   s->d.ion_pos = nullptr;
@@ -180,6 +184,7 @@ extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_
   P.with_potential = d.with_potential;
   P.move = d.move;
   P.step = d.step;
+  P.drift_a = d.drift_a > 0.0 ? d.drift_a : 0.0;
   P.seed_lo = (uint32_t)(d.seed & 0xffffffffu);
   P.seed_hi = (uint32_t)(d.seed >> 32);
   // ions: wrapped, device copies in [3][n_ion] layout; ion-ion constant on the host
@@ -321,16 +326,18 @@ qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, w->W, st)); }
   QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
   w->since_moves[0] = w->since_moves[1] = 0;
+  w->since_anchor[0] = w->since_anchor[1] = 0;
   w->energy_valid = true;
   return check_err(w, st);
 }
 
 void free_walkers(qmc_walkers_s* w) {
   WalkParams& W = w->W;
-  void* ptrs[] = {W.pos, W.binv, W.vgl, W.logdet, W.sgn, W.wid, W.weight, W.e_loc, W.log_psi,
-                  W.n_acc, W.acc_since, W.scratch64, W.err, w->d_P, w->d_prop, w->d_out,
-                  w->d_nacc, w->d_forced, W.win_phi, W.win_u, W.win_cinv, W.win_row, W.win_m,
-                  W.refine_max, W.rscale};
+  void* ptrs[] = {W.pos, W.binv[0], W.binv[1], W.binv_alt[0], W.binv_alt[1], W.vgl, W.logdet,
+                  W.sgn, W.wid, W.weight, W.e_loc, W.log_psi, W.n_acc, W.acc_since, W.scratch64,
+                  W.err, w->d_P, w->d_prop, w->d_out, w->d_nacc, w->d_forced, W.win_phi,
+                  W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
+                  W.logdet_shift, W.rscale, W.r2};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -373,10 +380,16 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
   while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
   const size_t np = proposals ? nw * (size_t)w->chunk : 1;
-  const size_t nbinv = (size_t)P.n_up * P.n_up + (size_t)P.n_dn * P.n_dn;
+  const size_t nb_up = (size_t)std::max(P.n_up, 1) * std::max(P.n_up, 1);
+  const size_t nb_dn = (size_t)std::max(P.n_dn, 1) * std::max(P.n_dn, 1);
+  // the second inverse buffers serve the batched single-precision re-inversion
+  const bool alt = tw == sizeof(float);
   struct A { void** p; size_t bytes; } allocs[] = {
       {(void**)&W.pos, nw * 3 * ne * sizeof(double)},
-      {(void**)&W.binv, nw * nbinv * tw},
+      {(void**)&W.binv[0], nw * nb_up * tw},
+      {(void**)&W.binv[1], nw * nb_dn * tw},
+      {(void**)&W.binv_alt[0], alt ? nw * nb_up * tw : 0},
+      {(void**)&W.binv_alt[1], alt ? nw * nb_dn * tw : 0},
       {(void**)&W.vgl, nw * ne * 5 * W.ld_v * tw},
       {(void**)&W.logdet, nw * 2 * sizeof(double)},
       {(void**)&W.sgn, nw * 2 * sizeof(double)},
@@ -398,9 +411,14 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.win_row, nw * (size_t)s->d.delay_k * sizeof(int)},
       {(void**)&W.win_m, nw * sizeof(int)},
       {(void**)&W.refine_max, nw * sizeof(float)},
+      {(void**)&W.refine_last, nw * 2 * sizeof(float)},
+      {(void**)&W.logdet_shift, nw * 2 * sizeof(float)},
+      {(void**)&W.r2, nw * 2 * sizeof(double)},
       {(void**)&W.rscale, nw * 4 * (size_t)W.ld_v * sizeof(int)},
   };
   for (auto& a : allocs) {
+    *a.p = nullptr;
+    if (a.bytes == 0) continue;
     cudaError_t e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
       free_walkers(w);
@@ -416,6 +434,9 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   cudaMemset(W.acc_since, 0, nw * 2 * sizeof(int));
   cudaMemset(W.win_m, 0, nw * sizeof(int));
   cudaMemset(W.refine_max, 0, nw * sizeof(float));
+  cudaMemset(W.refine_last, 0xFF, nw * 2 * sizeof(float));   // NaN: no refinement yet
+  cudaMemset(W.logdet_shift, 0xFF, nw * 2 * sizeof(float));  // NaN: no anchor yet
+  cudaMemset(W.r2, 0, nw * 2 * sizeof(double));
   W.kc = s->d.delay_k;
   *out = w;
   return QMC_OK;
@@ -462,7 +483,7 @@ namespace {
 // The sweeps of one walker set: Metropolis moves from batched proposals, or drift moves
 // with in-kernel orbital evaluation; windows flushed in batches every k moves unless the
 // re-inversion cadence counts accepted moves.
-qmc_status sweep_once(qmc_walkers_s* w, const WalkParams& W, bool fixed_node, cudaStream_t st) {
+qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStream_t st) {
   qmc_system_s* s = w->sys;
   const SysParams& P = s->P;
   const int kc = s->d.delay_k, period = s->d.reinv_period;
@@ -505,9 +526,22 @@ qmc_status sweep_once(qmc_walkers_s* w, const WalkParams& W, bool fixed_node, cu
           w->since_moves[spin] += e1 - e0;
           if (w->since_moves[spin] >= period) {
             { Bracket b(w, st, QMC_K_REFINE); QMC_CUDA(s->tw->refine(P, W, spin, 0, st)); }
-            { Bracket b(w, st, QMC_K_REFINE_UPDATE); QMC_CUDA(s->tw->refine(P, W, spin, 1, st)); }
-            w->launches += 2;   // row scales + residual, update + commit
+            {
+              Bracket b(w, st, QMC_K_REFINE_UPDATE);
+              QMC_CUDA(s->tw->refine(P, W, spin, 1, st));
+              // the refined inverse is in the second buffer: it becomes the current one
+              std::swap(W.binv[spin], W.binv_alt[spin]);
+              std::swap(w->W.binv[spin], w->W.binv_alt[spin]);
+              QMC_CUDA(s->tw->refine(P, W, spin, 2, st));
+            }
+            w->launches += 2;   // row scales + residual, update + fallback
+            w->since_anchor[spin] += w->since_moves[spin];
             w->since_moves[spin] = 0;
+            if (s->d.logdet_period > 0 && w->since_anchor[spin] >= s->d.logdet_period) {
+              Bracket b(w, st, QMC_K_LOGDET);
+              QMC_CUDA(s->tw->logdet_anchor(P, W, spin, st));
+              w->since_anchor[spin] = 0;
+            }
           }
         }
         e0 = e1;
@@ -707,10 +741,9 @@ extern "C" qmc_status qmc_get_inverse(qmc_walkers_t w, int walker, int spin, dou
   qmc_status r = check_err(w, 0);
   if (r != QMC_OK) return r;
   const size_t ns = spin ? P.n_dn : P.n_up;
-  const size_t off = (size_t)walker * ((size_t)P.n_up * P.n_up + (size_t)P.n_dn * P.n_dn) +
-                     (spin ? (size_t)P.n_up * P.n_up : 0);
   std::vector<double> h;
-  r = fetch_tw(w, static_cast<const char*>(w->W.binv) + off * w->sys->tw->tw_size, ns * ns, h);
+  r = fetch_tw(w, static_cast<const char*>(w->W.binv[spin]) + (size_t)walker * ns * ns * w->sys->tw->tw_size,
+               ns * ns, h);
   if (r != QMC_OK) return r;
   QMC_CUDA(cudaMemcpy(out, h.data(), h.size() * sizeof(double), cudaMemcpyDefault));
   return QMC_OK;
@@ -732,6 +765,36 @@ extern "C" qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out)
     for (int c = 0; c < 5; ++c)
       for (int j = 0; j < nsm; ++j) o[((size_t)e * 5 + c) * nsm + j] = h[((size_t)e * 5 + c) * ld + j];
   QMC_CUDA(cudaMemcpy(out, o.data(), o.size() * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_get_logdet(qmc_walkers_t w, double* logdet, double* sign) {
+  if (!w || (!logdet && !sign)) return fail(QMC_EINVAL, "qmc_get_logdet: NULL argument");
+  qmc_status r = check_err(w, 0);
+  if (r != QMC_OK) return r;
+  const size_t b = sizeof(double) * 2 * (size_t)w->W.n_w;
+  if (logdet) QMC_CUDA(cudaMemcpy(logdet, w->W.logdet, b, cudaMemcpyDefault));
+  if (sign) QMC_CUDA(cudaMemcpy(sign, w->W.sgn, b, cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_get_precision_report(qmc_walkers_t w, double* residual,
+                                               double* logdet_shift) {
+  if (!w || (!residual && !logdet_shift))
+    return fail(QMC_EINVAL, "qmc_get_precision_report: NULL argument");
+  qmc_status r = check_err(w, 0);
+  if (r != QMC_OK) return r;
+  const size_t n = 2 * (size_t)w->W.n_w;
+  std::vector<float> f(n);
+  std::vector<double> h(n);
+  const float* src[2] = {w->W.refine_last, w->W.logdet_shift};
+  double* dst[2] = {residual, logdet_shift};
+  for (int k = 0; k < 2; ++k) {
+    if (!dst[k]) continue;
+    QMC_CUDA(cudaMemcpy(f.data(), src[k], n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) h[i] = f[i];
+    QMC_CUDA(cudaMemcpy(dst[k], h.data(), n * sizeof(double), cudaMemcpyDefault));
+  }
   return QMC_OK;
 }
 
@@ -900,6 +963,7 @@ extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
       W.trace = nullptr;
       W.forced = nullptr;
       w->sweep = d->step;
+      QMC_CUDA(cudaMemsetAsync(W.r2, 0, sizeof(double) * 2 * (size_t)W.n_w, y.st));
       qmc_status r = sweep_once(w, W, true, y.st);
       if (r != QMC_OK) return r;
       { Bracket b(w, y.st, QMC_K_ENERGY); QMC_CUDA(y.sys->tw->local_energy(y.sys->P, W, y.st)); }
@@ -916,6 +980,15 @@ extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
   for (size_t i = 0; i < d->sys.size(); ++i) {
     QMC_CUDA(cudaEventRecord(d->ev_out[i], d->sys[i].st));
     QMC_CUDA(cudaStreamWaitEvent(cs, d->ev_out[i], 0));
+  }
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_set_mode(qmc_dmc_t d, int effective_tau, int reconfigure) {
+  if (!d) return fail(QMC_EINVAL, "qmc_dmc_set_mode: NULL driver");
+  for (auto& y : d->sys) {
+    y.D.tau_eff = effective_tau != 0;
+    y.D.reconfigure = reconfigure != 0;
   }
   return QMC_OK;
 }

@@ -48,6 +48,21 @@ __device__ __forceinline__ void move_draws(const SysParams& S, uint32_t t, uint3
   u = unit_open(b.v[0]);
 }
 
+// Drift part of a drift-diffusion step for drift velocity v = grad_e ln|Psi|: tau v, or with
+// a > 0 the nodal rescaling of Umrigar, Nightingale and Runge (J. Chem. Phys. 99, 2865 (1993);
+// Sec. "Projector Monte Carlo"): tau v (-1 + sqrt(1 + 2 a |v|^2 tau)) / (a |v|^2 tau), written
+// as tau v 2 / (1 + sqrt(1 + 2 a |v|^2 tau)), which stays below sqrt(2 tau / a) next to a node.
+__device__ __forceinline__ void drift_disp(const double v[3], double tau, double a, double out[3]) {
+  double f = tau;
+  if (a > 0.0) {
+    const double x = 2.0 * a * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * tau;
+    if (!(x < 1e-12)) f = tau * 2.0 / (1.0 + sqrt(1.0 + x));
+  }
+  out[0] = f * v[0];
+  out[1] = f * v[1];
+  out[2] = f * v[2];
+}
+
 // ------------------------------------------------------------------ geometry
 // Wrap into [0, L): the sign-corrected remainder.
 __device__ __forceinline__ double wrap_box(double x, double L) {
@@ -143,11 +158,16 @@ __device__ __forceinline__ void jastrow_u(const SysParams& S, int f, T r, T& u, 
 // pw holds the same spline in power form per knot interval, u = a0 + a1 t + a2 t^2 + a3 t^3
 // (the cubic B-spline basis expanded and summed with the interval's four knots, in FP64),
 // so that a value costs one 16-byte load and three FMAs.
+// plo and scale_lo hold the rounding residues of the knots and of the scale M / r_c (zero
+// in double precision): the J value of ln|Psi| sums ~10^5 pair terms, and a constant
+// rounded once would shift every term the same way, moving J by ~2^-24 |J| (see
+// jastrow_value6).
 template <class T>
 struct JastrowTab {
   int M[3];
-  T rc[3], rc2[3], scale[3];
+  T rc[3], rc2[3], scale[3], scale_lo[3];
   T p[3][kMaxKnots + 4];
+  T plo[3][kMaxKnots + 4];
   alignas(16) T pw[3][kMaxKnots + 1][4];
 };
 
@@ -156,6 +176,7 @@ __device__ __forceinline__ void jastrow_tab_fill(const SysParams& S, JastrowTab<
   for (int i = threadIdx.x; i < 3 * (kMaxKnots + 4); i += blockDim.x) {
     const int f = i / (kMaxKnots + 4), m = i % (kMaxKnots + 4);
     J.p[f][m] = (m <= S.jM[f]) ? Cst<T>::knot(S, f, m) : T(0);
+    J.plo[f][m] = (m <= S.jM[f]) ? T(S.jp[f][m] - (double)Cst<T>::knot(S, f, m)) : T(0);
   }
   for (int i = threadIdx.x; i < 3 * (kMaxKnots + 1); i += blockDim.x) {
     const int f = i / (kMaxKnots + 1), m = i % (kMaxKnots + 1);
@@ -173,6 +194,32 @@ __device__ __forceinline__ void jastrow_tab_fill(const SysParams& S, JastrowTab<
     J.rc[f] = Cst<T>::rc(S, f);
     J.rc2[f] = S.jM[f] ? Cst<T>::rc(S, f) * Cst<T>::rc(S, f) : T(0);   // a term switched off: no pair inside
     J.scale[f] = S.jM[f] ? T(S.jM[f]) / Cst<T>::rc(S, f) : T(0);
+    const double sd = S.jM[f] ? (double)S.jM[f] / S.jrc[f] : 0.0;
+    J.scale_lo[f] = T(sd - (double)J.scale[f]);
+  }
+}
+
+// 6 u(r) as a pair (hi, lo) whose sum carries no rounding common to all pairs: the knot
+// interval coordinate uses the split scale (hi + lo), the basis is used without its
+// factor 1/6 (integer coefficients), and the knots' residues enter lo. J summed from these
+// and divided by 6 once is free of the systematic shifts a rounded M / r_c or 1/6 gives.
+template <class T>
+__device__ __forceinline__ void jastrow_value6(const JastrowTab<T>& J, int f, T r, T& hi, T& lo) {
+  hi = lo = T(0);
+  if (!(r < J.rc[f])) return;
+  const T s = fma(r, J.scale[f], r * J.scale_lo[f]);
+  int i = (int)tfloor(s);
+  if (i < 0) i = 0;
+  const T t = s - T(i);
+  const T t2 = t * t, t3 = t2 * t, omt = T(1) - t;
+  const T b[4] = {omt * omt * omt, T(3) * t3 - T(6) * t2 + T(4),
+                  T(-3) * t3 + T(3) * t2 + T(3) * t + T(1), t3};
+  const T* p = J.p[f] + i;
+  const T* pl = J.plo[f] + i;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    hi += p[q] * b[q];
+    lo += pl[q] * b[q];
   }
 }
 

@@ -17,16 +17,29 @@ __device__ __forceinline__ int dmc_copies(double wgt, double xi, int cap) {
   return mf >= (double)cap ? cap : (int)mf;
 }
 
-// One block: weights w = exp(-tau/2 (E_old + E_new - 2 E_T)) (Eq. pmc:g_growth, Eq.
-// pmc:walker_weight), copies M = floor(w + xi) with xi from Philox block (step, 0xB, ID, 2),
-// destinations by prefix sums in walker order (the first copy keeps the ID, further copies
-// take consecutive new IDs), population capped at `cap`, and
-// E_T <- E_w - ln(N / N_target) / (10 tau) with E_w the weighted mean E_L of this step.
+// Teeth of the reconfiguration comb (k + xi) W / N, k = 0..N-1, below the cumulative weight c.
+__device__ __forceinline__ int comb_teeth_below(double c, double W, int n, double xi) {
+  const double t = ceil(c * (double)n / W - xi);
+  return t <= 0.0 ? 0 : (t >= (double)n ? n : (int)t);
+}
+
+// One block. Weights w = exp(-tau_w/2 (E_old + E_new - 2 E_T)) (Eq. pmc:g_growth, Eq.
+// pmc:walker_weight), tau_w = tau, or with D.tau_eff the walker's effective time step
+// tau * (accepted |dr|^2) / (proposed |dr|^2) of this step's sweep (Umrigar, Nightingale and
+// Runge). Copies: M = floor(w + xi) with xi from Philox block (step, 0xB, ID, 2); or, with
+// D.reconfigure, a stochastic reconfiguration at a fixed count (Assaraf, Caffarel and
+// Khelif): one comb of N teeth at (k + xi) W / N over the cumulative weights, xi from
+// block (step, 0xC, 0, 2), walker i taking the teeth of [C_{i-1}, C_i) (the last walker
+// the rest, so the counts add up to N). Destinations by prefix sums in walker order (the
+// first copy keeps the ID, further copies take consecutive new IDs), population capped at
+// `cap`, and E_T <- E_w - ln(N / N_target) / (10 tau) with E_w the weighted mean E_L of
+// this step.
 __global__ void __launch_bounds__(1024) k_dmc_branch(SysParams S, WalkParams Wk, DmcParams D,
                                                     int parity, uint32_t step) {
   __shared__ int scan[1024];
   __shared__ int scan2[1024];
   __shared__ double red[2 * 32];
+  __shared__ double cscan[1024];
   const int n = D.n_live[parity];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const double et = *D.e_trial;
@@ -34,16 +47,53 @@ __global__ void __launch_bounds__(1024) k_dmc_branch(SysParams S, WalkParams Wk,
   const int per = (n + nt - 1) / nt;
   const int i0 = min(n, tid * per), i1 = min(n, i0 + per);
   double sw = 0.0, swe = 0.0;
-  int mloc = 0, xloc = 0;
   for (int i = i0; i < i1; ++i) {
-    const double wgt = exp(-0.5 * D.tau * (D.e_old[i] + Wk.e_loc[i] - 2.0 * et));
-    const U32x4 r = philox4x32_10(step, 0xBu, Wk.wid[i], 2u, S.seed_lo, S.seed_hi);
-    const int M = dmc_copies(wgt, unit_open(r.v[0]), D.cap);
+    double te = D.tau;
+    if (D.tau_eff) {
+      const double p = Wk.r2[2 * i], a = Wk.r2[2 * i + 1];
+      te = p > 0.0 ? D.tau * a / p : 0.0;
+    }
+    const double wgt = exp(-0.5 * (D.e_old[i] + Wk.e_loc[i] - 2.0 * et) * te);
     Wk.weight[i] = wgt;
     sw += wgt;
     swe += wgt * Wk.e_loc[i];
-    mloc = min(mloc + M, D.cap);                 // sums bounded by cap: no overflow
-    xloc = min(xloc + (M > 0 ? M - 1 : 0), D.cap);
+  }
+  // inclusive scan of the thread sums of the weights (the comb's cumulative weights)
+  cscan[tid] = sw;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    const double a = tid >= o ? cscan[tid - o] : 0.0;
+    __syncthreads();
+    cscan[tid] += a;
+    __syncthreads();
+  }
+  const double wtot = cscan[nt - 1];
+  double cum = tid > 0 ? cscan[tid - 1] : 0.0;   // weight of the walkers before this range
+  double xi_comb = 0.0;
+  if (D.reconfigure) {
+    const U32x4 r = philox4x32_10(step, 0xCu, 0u, 2u, S.seed_lo, S.seed_hi);
+    xi_comb = unit_open(r.v[0]);
+  }
+  // copy counts of this thread's walkers
+  auto copies = [&](int i, double c_before, double c_after) {
+    if (D.reconfigure) {
+      const int a = comb_teeth_below(c_before, wtot, n, xi_comb);
+      const int b = i == n - 1 ? n : comb_teeth_below(c_after, wtot, n, xi_comb);
+      return max(b - a, 0);
+    }
+    const U32x4 r = philox4x32_10(step, 0xBu, Wk.wid[i], 2u, S.seed_lo, S.seed_hi);
+    return dmc_copies(Wk.weight[i], unit_open(r.v[0]), D.cap);
+  };
+  int mloc = 0, xloc = 0;
+  {
+    double c = cum;
+    for (int i = i0; i < i1; ++i) {
+      const double c1 = c + Wk.weight[i];
+      const int M = copies(i, c, c1);
+      c = c1;
+      mloc = min(mloc + M, D.cap);               // sums bounded by cap: no overflow
+      xloc = min(xloc + (M > 0 ? M - 1 : 0), D.cap);
+    }
   }
   // block sums of the weights
 #pragma unroll
@@ -68,9 +118,9 @@ __global__ void __launch_bounds__(1024) k_dmc_branch(SysParams S, WalkParams Wk,
   int xr = scan2[tid] - xloc;
   const uint32_t nid = *D.next_id;
   for (int i = i0; i < i1; ++i) {
-    const double wgt = Wk.weight[i];
-    const U32x4 r = philox4x32_10(step, 0xBu, Wk.wid[i], 2u, S.seed_lo, S.seed_hi);
-    const int M = dmc_copies(wgt, unit_open(r.v[0]), D.cap);
+    const double c1 = cum + Wk.weight[i];
+    const int M = copies(i, cum, c1);
+    cum = c1;
     for (int c = 0; c < M && dest + c < D.cap; ++c) {
       const int d = dest + c;
       D.src_of[d] = i;
@@ -110,13 +160,15 @@ __global__ void __launch_bounds__(256) k_dmc_copy(SysParams S, WalkParams src, W
   if (d >= D.n_live[parity ^ 1]) return;
   const int i = D.src_of[d];
   const int n_e = S.n_e;
-  const size_t nb = (size_t)S.n_up * S.n_up + (size_t)S.n_dn * S.n_dn;
   const size_t nv = (size_t)n_e * 5 * src.ld_v;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int k = tid; k < 3 * n_e; k += nt) dst.pos[(size_t)d * 3 * n_e + k] = src.pos[(size_t)i * 3 * n_e + k];
-  const TW* bs = static_cast<const TW*>(src.binv) + (size_t)i * nb;
-  TW* bd = static_cast<TW*>(dst.binv) + (size_t)d * nb;
-  for (size_t k = tid; k < nb; k += nt) bd[k] = bs[k];
+  for (int spin = 0; spin < 2; ++spin) {
+    const size_t nb = spin ? (size_t)S.n_dn * S.n_dn : (size_t)S.n_up * S.n_up;
+    const TW* bs = binv_block<const TW>(S, src, i, spin);
+    TW* bd = binv_block<TW>(S, dst, d, spin);
+    for (size_t k = tid; k < nb; k += nt) bd[k] = bs[k];
+  }
   const float4* vs = reinterpret_cast<const float4*>(static_cast<const TW*>(src.vgl) + (size_t)i * nv);
   float4* vd = reinterpret_cast<float4*>(static_cast<TW*>(dst.vgl) + (size_t)d * nv);
   const size_t nv4 = nv * sizeof(TW) / 16;

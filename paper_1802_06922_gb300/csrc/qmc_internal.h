@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace qmcgb {
 
 constexpr int kMaxKnots = 32;       // largest Jastrow M
@@ -44,6 +46,7 @@ struct SysParams {
   double v_ion_ion;    // Z^2 sum_{I<J} v(R_IJ), a constant
   int move;            // 0 Metropolis, 1 drift
   double step;
+  double drift_a;      // > 0: nodal drift rescaling parameter (0: the plain drift)
   uint32_t seed_lo, seed_hi;
 };
 
@@ -52,7 +55,9 @@ struct WalkParams {
   int n_w;
   int ld_v;            // row length of per-electron orbital vectors (>= max N_s, multiple of 8)
   double* pos;         // [W][3][n_e]
-  void* binv;          // working precision [W][n_up*n_up + n_dn*n_dn]; Binv[e][j] = (A^-1)[j][e]
+  void* binv[2];       // per spin block, working precision [W][N_s][N_s]; Binv[e][j] = (A^-1)[j][e]
+  void* binv_alt[2];   // second buffer of each spin block: the single-precision re-inversion
+                       // writes the refined inverse there and the two buffers swap roles
   void* vgl;           // working precision [W][n_e][5][ld_v]: value, gx, gy, gz, lap at r_e
   double* logdet;      // [W][2]
   double* sgn;         // [W][2]
@@ -73,10 +78,24 @@ struct WalkParams {
   void* win_cinv;      // [W][kc][kc]   C^-1
   int* win_row;        // [W][kc]       row (electron index within the spin block)
   int* win_m;          // [W]           fill
-  float* refine_max;   // [W]           max |I - A X| of the last refinement
+  float* refine_max;   // [W]           max |I - A X| of the refinement in progress
+  float* refine_last;  // [W][2]        max |I - A X| measured by the last refinement of each
+                       //               spin block (before its Newton step); NaN if none yet
+  float* logdet_shift; // [W][2]        change of ln|det A| made by the last log-det anchor
+                       //               (anchor value minus the accumulated one); NaN if none
   int* rscale;         // [W][2][2][ld_v] power-of-two exponents of the rows of A and X
   const int* n_live;   // optional device count: blocks of walkers >= *n_live return at once
+  double* r2;          // [W][2] sums of the squared proposed and accepted displacements of
+                       //        drift moves since the last reset (effective time step)
 };
+
+// Inverse of walker w's spin block: Binv[e][j] = (A^-1)[j][e], N_s x N_s, row-major.
+template <class T>
+__host__ __device__ inline T* binv_block(const SysParams& S, const WalkParams& W, int w, int spin) {
+  const size_t ns = spin ? S.n_dn : S.n_up;
+  using V = typename std::remove_const<T>::type;
+  return static_cast<V*>(W.binv[spin]) + (size_t)w * ns * ns;
+}
 
 // Device state of the branching DMC of one system.
 struct DmcParams {
@@ -90,6 +109,8 @@ struct DmcParams {
   double* stats;        // [8] sum W, sum W E, weighted mean E, E_T used, population before, after
   int n_target, cap;
   double tau;
+  int tau_eff;          // 1: branching factor with tau_eff = tau * accepted / proposed |dr|^2
+  int reconfigure;      // 1: stochastic reconfiguration at a fixed walker count
 };
 
 }  // namespace qmcgb

@@ -262,8 +262,7 @@ __device__ void reinvert_block(const SysParams& S, const WalkParams& Wk, int w, 
   __syncthreads();
   double ld, sg;
   const bool ok = gj_invert_fp64(M, ns, colk, perm, redv, redi, ld, sg);
-  TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-          (spin ? S.n_up * S.n_up : 0);
+  TW* B = binv_block<TW>(S, Wk, w, spin);
   if (ok)
     for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) B[i] = (TW)M[i];
   if (threadIdx.x == 0) {
@@ -363,8 +362,7 @@ static __device__ float refine_inverse(const SysParams& S, const WalkParams& Wk,
   const int first = spin ? S.n_up : 0;
   const int ld5 = 5 * Wk.ld_v;
   const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
-  float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-             (spin ? S.n_up * S.n_up : 0);
+  float* B = binv_block<float>(S, Wk, w, spin);
   float* Rg = reinterpret_cast<float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
   float* Bn = Rg + (size_t)ns * ns;
   float* As = tile;
@@ -759,8 +757,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   const int ns = spin ? S.n_dn : S.n_up;
   const TW Lw = Cst<TW>::L(S), iLw = Cst<TW>::invL(S);
   const TW* ionw = Cst<TW>::ions(S);
-  TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-          (spin ? S.n_up * S.n_up : 0);
+  TW* B = binv_block<TW>(S, Wk, w, spin);
   TW* VG = static_cast<TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
   double* gpos = Wk.pos + (size_t)w * 3 * n_e;
   // Prefetch of move index e (orbital rows, proposal, inverse row) into buffer b: one
@@ -807,6 +804,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   }
   double logdet = 0.0, sgn = 1.0;        // thread 0
   long long nacc = 0;
+  double r2p = 0.0, r2a = 0.0;           // thread 0: squared proposed / accepted displacements
   if (tid == 0) {
     logdet = Wk.logdet[2 * w + spin];
     sgn = Wk.sgn[2 * w + spin];
@@ -967,13 +965,14 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
           for (int q = 0; q < nw; ++q) v += sm.red[q * 6 + c] + sm.red[q * 6 + 3 + c];
           go[c] = (double)v;
         }
-        double xi[3], u;
+        double xi[3], u, dd[3];
         move_draws(S, t, (uint32_t)e, Wk.wid[w], xi, u);
         const double tau = S.step, sq = sqrt(tau);
+        drift_disp(go, tau, S.drift_a, dd);
         for (int c = 0; c < 3; ++c) {
-          const double rn = wrap_box(sm.posd[c * n_e + e] + tau * go[c] + sq * xi[c], S.L);
+          const double rn = wrap_box(sm.posd[c * n_e + e] + dd[c] + sq * xi[c], S.L);
           sm.propb[4 * cur + c] = rn;
-          sm.outd[10 + c] = go[c];
+          sm.outd[10 + c] = dd[c];               // drift displacement of the forward move
           sm.sc[c] = (TW)rn;
         }
         sm.propb[4 * cur + 3] = u;
@@ -1062,16 +1061,23 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       const double u = sm.propb[4 * cur + 3];
       const bool ok = (R != TW(0)) && isfinite(R);
       TW A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
+      double dr2 = 0.0;                          // |r' - r|^2 of a drift move
       if constexpr (kDrift) {
+        // T(R'->R) / T(R->R') with displacement d = r' - r (minimum image) and the drift
+        // displacements of both ends
+        const double tau = S.step;
+        double d[3], gn[3], db[3];
+        for (int c = 0; c < 3; ++c) {
+          d[c] = min_image<double>(sm.propb[4 * cur + c] - sm.posd[c * n_e + e], S.L);
+          dr2 += d[c] * d[c];
+          gn[c] = (double)(tot[1 + c] / R) + (double)tot[6 + c];
+        }
         if (ok) {
-          // T(R'->R) / T(R->R') with displacement d = r' - r (minimum image)
-          const double tau = S.step;
+          drift_disp(gn, tau, S.drift_a, db);
           double f2 = 0.0, b2 = 0.0;
           for (int c = 0; c < 3; ++c) {
-            const double d = min_image<double>(sm.propb[4 * cur + c] - sm.posd[c * n_e + e], S.L);
-            const double gn = (double)(tot[1 + c] / R) + (double)tot[6 + c];
-            const double fw = d - tau * sm.outd[10 + c];
-            const double bw = -d - tau * gn;
+            const double fw = d[c] - sm.outd[10 + c];
+            const double bw = -d[c] - db[c];
             f2 += fw * fw;
             b2 += bw * bw;
           }
@@ -1082,6 +1088,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       bool accept = u < (double)A;
       if (kFixedNode && R < TW(0)) accept = false;
       if (Wk.forced) accept = Wk.forced[(size_t)w * n_e + e] != 0;
+      if (kDrift) {
+        r2p += dr2;
+        if (accept) r2a += dr2;
+      }
       if (Wk.trace) {
         double* tr = Wk.trace + ((size_t)w * n_e + e) * 8;
         tr[0] = (double)R;
@@ -1236,6 +1246,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
     Wk.sgn[2 * w + spin] = sgn;
     Wk.n_acc[w] += nacc;
     Wk.acc_since[2 * w + spin] = since;
+    if (kDrift) {
+      Wk.r2[2 * w] += r2p;
+      Wk.r2[2 * w + 1] += r2a;
+    }
   }
 }
 
@@ -1279,8 +1293,7 @@ __global__ void __launch_bounds__(256) k_flush(SysParams S, WalkParams Wk, int s
   const TW* gphi = static_cast<const TW*>(Wk.win_phi) + (size_t)w * kc * ld_v;
   const TW* gu = static_cast<const TW*>(Wk.win_u) + (size_t)w * kc * ld_v;
   const TW* gc = static_cast<const TW*>(Wk.win_cinv) + (size_t)w * kc * kc;
-  TW* B = static_cast<TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-          (spin ? S.n_up * S.n_up : 0);
+  TW* B = binv_block<TW>(S, Wk, w, spin);
   for (int i = tid; i < m * ld_v; i += nt) { phi[i] = gphi[i]; U[i] = gu[i]; }
   for (int i = tid; i < kc * kc; i += nt) ci[i] = gc[i];
   for (int i = tid; i < m; i += nt) wrow[i] = Wk.win_row[(size_t)w * kc + i];
@@ -1344,30 +1357,30 @@ static __global__ void k_window_reset(WalkParams Wk) {
 // =============================================================================
 // Batched single-precision re-inversion (the refinement of refine_inverse as separate
 // kernels over all walkers): the error-free residual R = I - A X comes from the tensor
-// cores (k_refine_residual_tc), then X <- X + X R and the commit below.
+// cores (k_refine_residual_tc), then X <- X + X R into the second buffer of the spin block
+// (k_refine_update_tc) and the FP64 fallback below.
 // =============================================================================
-// Copies the refined inverse back (walkers that refined), and re-inverts in FP64 the
-// walkers whose residual was too large.
+// After the Newton update has written the refined inverses into the spin block's second
+// buffer and the host has swapped the two buffers: walkers whose residual was too large
+// (or not finite) are re-inverted in FP64 into the now current buffer, and the measured
+// residual is recorded in refine_last.
 template <class TW>
-__global__ void __launch_bounds__(256) k_refine_commit(SysParams S, WalkParams Wk, int spin) {
+__global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams Wk, int spin) {
   extern __shared__ __align__(16) char smem_c[];
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
-  const int ns = spin ? S.n_dn : S.n_up;
-  float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-             (spin ? S.n_up * S.n_up : 0);
-  if (Wk.refine_max[w] <= kRefineMax) {
-    const float* Bn = reinterpret_cast<const float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v) +
-                      (size_t)ns * ns;
-    for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) B[i] = Bn[i];
-  } else {
+  const float rm = Wk.refine_max[w];
+  if (!(rm <= kRefineMax)) {
     double* colk = reinterpret_cast<double*>(smem_c);
     double* redv = colk + Wk.ld_v;
     int* perm = reinterpret_cast<int*>(redv + 32);
     int* redi = perm + Wk.ld_v;
     reinvert_block<TW>(S, Wk, w, spin, colk, perm, redv, redi);
   }
-  if (threadIdx.x == 0) Wk.refine_max[w] = 0.f;
+  if (threadIdx.x == 0) {
+    Wk.refine_last[2 * w + spin] = rm;
+    Wk.refine_max[w] = 0.f;
+  }
 }
 
 // =============================================================================
@@ -1394,15 +1407,15 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
   const TW hL2 = TW(0.25) * Lw * Lw;
   const TW* ionw = Cst<TW>::ions(S);
   const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
-  const TW* Bw = static_cast<const TW*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn);
+
   double kin = 0.0, pot = 0.0, jas = 0.0;   // lane 0 of each warp
   for (int i = warp; i < n_e; i += nw) {
     const int spin = i >= S.n_up;
     const int ns = spin ? S.n_dn : S.n_up;
     const int row = i - (spin ? S.n_up : 0);
-    const TW* Bi = Bw + (spin ? S.n_up * S.n_up : 0) + (size_t)row * ns;
+    const TW* Bi = binv_block<const TW>(S, Wk, w, spin) + (size_t)row * ns;
     const TW* v = VG + (size_t)i * 5 * ld_v;
-    TW s[10];
+    TW s[9];
     {
       TW g0 = 0, g1 = 0, g2 = 0, l0 = 0;
       for (int j = lane; j < ns; j += 32) {
@@ -1415,8 +1428,10 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
       s[0] = g0; s[1] = g1; s[2] = g2; s[3] = l0;
     }
     const TW ri[3] = {posw[i], posw[n_e + i], posw[2 * n_e + i]};
+    double jsum;   // this electron's share of J, summed without loss (ln|Psi| needs J to
+                   // about 1e-7 relative while its ~10^5 pair terms add up to ~10^4)
     {
-      TW gx = 0, gy = 0, gz = 0, lj = 0, jj = 0, pv = 0;
+      TW gx = 0, gy = 0, gz = 0, lj = 0, jj = 0, jc = 0, pv = 0;
       const int ntot = n_e + S.n_ion;
       for (int j = lane; j < ntot; j += 32) {
         if (j == i) continue;
@@ -1439,7 +1454,10 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
         const bool in_v = S.with_potential && once && r2 < hL2;
         const bool in_j = jt.M[f] != 0 && r2 < jt.rc2[f];
         if (!(in_v || in_j) || !(r2 > TW(0))) continue;
-        const TW rinv = rsqrt_w(r2), r = r2 * rinv;
+        const TW rinv = rsqrt_w(r2), r0 = r2 * rinv;
+        // one Newton correction: r2 * rsqrt(r2) in single precision carries a bias of a few
+        // ulp that the J value (a sum of ~10^5 pair terms) would accumulate
+        const TW r = fma(TW(0.5) * fma(-r0, r0, r2), rinv, r0);
         if (in_v) {
           const TW y = exp_w(-kap * r) * rinv;        // Yukawa e^{-kappa r} / r
           pv += (j < n_e) ? y : -Zw * y;
@@ -1447,21 +1465,30 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
         if (!in_j) continue;
         TW u, du, d2u;
         jastrow_eval<TW>(jt, f, r, u, du, d2u);
-        if (once) jj += u;
+        if (once) {   // TwoSum: jj + jc carries the exact running sum of the 6 u terms
+          TW u6, u6lo;
+          jastrow_value6<TW>(jt, f, r, u6, u6lo);
+          const TW t = jj + u6, z = t - jj;
+          jc += ((jj - (t - z)) + (u6 - z)) + u6lo;
+          jj = t;
+        }
         const TW g = du * rinv;
         gx += g * dd[0]; gy += g * dd[1]; gz += g * dd[2];
         lj += d2u + TW(2) * g;
       }
-      s[4] = gx; s[5] = gy; s[6] = gz; s[7] = lj; s[8] = pv; s[9] = jj;
+      s[4] = gx; s[5] = gy; s[6] = gz; s[7] = lj; s[8] = pv;
+      jsum = ((double)jj + (double)jc) / 6.0;
     }
-    warp_sum<10, TW>(s);
+    warp_sum<9, TW>(s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) jsum += __shfl_xor_sync(0xffffffffu, jsum, o);
     if (lane == 0) {
       const double g0 = s[0], g1 = s[1], g2 = s[2];
       const double lapD = (double)s[3] - (g0 * g0 + g1 * g1 + g2 * g2);
       const double gx = g0 + (double)s[4], gy = g1 + (double)s[5], gz = g2 + (double)s[6];
       kin += -0.5 * (lapD + (double)s[7] + gx * gx + gy * gy + gz * gz);
       pot += (double)s[8];
-      jas += (double)s[9];
+      jas += jsum;
     }
   }
   // sum the warp totals (lane 0 of each warp) in double

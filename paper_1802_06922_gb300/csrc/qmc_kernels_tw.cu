@@ -4,6 +4,7 @@
 #include "qmc_tc_kernels.cuh"
 #include "qmc_dmc.cuh"
 #include "qmc_sweep_win.cuh"
+#include "qmc_logdet.cuh"
 
 namespace qmcgb {
 namespace {
@@ -79,21 +80,23 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
   if (ns == 0) return cudaSuccess;
   if constexpr (sizeof(TW) == 4) {
     if (part == 1) {
-      // X <- X + X R on the tensor cores (3xTF32), then the commit
+      // X <- X + X R on the tensor cores (3xTF32) into the second buffer of the spin block
       const size_t smem = refine_update_tc_smem_bytes();
       cudaError_t e = cudaFuncSetAttribute(k_refine_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       const int nt = (ns + kTcRows - 1) / kTcRows;
       k_refine_update_tc<<<dim3(W.n_w, nt * nt), kThreads, smem, st>>>(S, W, spin);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      k_refine_commit<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
+      return cudaGetLastError();
+    }
+    if (part == 2) {
+      // after the buffer swap: FP64 re-inversion of the walkers whose residual was too large
+      k_refine_fallback<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
       return cudaGetLastError();
     }
     if (ns > kRsMaxK) {
       // beyond the exactness bound of the slice products: every walker of this spin block
       // takes the FP64 re-inversion (refine_max set to NaN makes the update skip them and
-      // the commit re-invert them)
+      // the fallback re-invert them)
       return cudaMemsetAsync(W.refine_max, 0xFF, sizeof(float) * W.n_w, st);
     }
     // error-free residual on the tensor cores (power-of-two row scales first)
@@ -109,6 +112,21 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
   } else {
     // double precision needs no refinement: FP64 Gauss-Jordan of that spin block
     return cudaErrorNotSupported;
+  }
+}
+
+template <class TW>
+cudaError_t logdet_anchor(const SysParams& S, const WalkParams& W, int spin, cudaStream_t st) {
+  if constexpr (sizeof(TW) == 4) {
+    const int ns = spin ? S.n_dn : S.n_up;
+    if (ns == 0 || ns > kLdMaxN) return cudaSuccess;   // larger blocks re-invert in FP64
+    const size_t smem = logdet_smem_bytes(ns);
+    cudaError_t e = cudaFuncSetAttribute(k_logdet_anchor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_logdet_anchor<<<W.n_w, kLdThreads, smem, st>>>(S, W, spin);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorNotSupported;                       // the FP64 form needs no anchor
   }
 }
 
@@ -148,13 +166,13 @@ cudaError_t dmc_copy(const SysParams& S, const WalkParams& src, const WalkParams
 const TwLaunch& tw_launch_f64() {
   static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
                           sweep_smem<double>, invert_batch<double>, flush<double>,
-                          refine<double>, dmc_branch, dmc_copy<double>};
+                          refine<double>, logdet_anchor<double>, dmc_branch, dmc_copy<double>};
   return L;
 }
 const TwLaunch& tw_launch_f32() {
   static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
                           sweep_smem<float>, invert_batch<float>, flush<float>, refine<float>,
-                          dmc_branch, dmc_copy<float>};
+                          logdet_anchor<float>, dmc_branch, dmc_copy<float>};
   return L;
 }
 

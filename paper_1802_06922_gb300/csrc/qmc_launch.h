@@ -18,8 +18,12 @@ struct TwLaunch {
   cudaError_t (*invert_batch)(const void* A, void* Binv, double* logdet, double* sign, int n,
                               int batch, double* work, cudaStream_t);
   cudaError_t (*flush)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
-  // part 0: row scales + error-free residual; part 1: X <- X + X R, commit or FP64 fallback
+  // part 0: row scales + error-free residual; part 1: X <- X + X R into binv_alt[spin];
+  // part 2 (after the caller has swapped binv and binv_alt of the spin block): FP64
+  // fallback of the walkers whose residual was too large
   cudaError_t (*refine)(const SysParams&, const WalkParams&, int spin, int part, cudaStream_t);
+  // ln|det A| of the spin block by the error-free FP32 LU (single precision only)
+  cudaError_t (*logdet_anchor)(const SysParams&, const WalkParams&, int spin, cudaStream_t);
   cudaError_t (*dmc_branch)(const SysParams&, const WalkParams&, const DmcParams&, int parity,
                             uint32_t step, cudaStream_t);
   cudaError_t (*dmc_copy)(const SysParams&, const WalkParams& src, const WalkParams& dst,

@@ -17,8 +17,11 @@ namespace {
 constexpr size_t kWorkDoubles = size_t(1) << 21;
 static __device__ __align__(256) double g_noalloc_work[kWorkDoubles];
 
-// Device addresses of the work area, looked up once per device (host code must not use
-// the symbol itself: on the host it names a stand-in, not device memory).
+// Device address of the work area per device (host code must not use the symbol itself:
+// on the host it names a stand-in, not device memory). It is looked up again on every call
+// whose stream is not being captured, so a context re-created after cudaDeviceReset gets
+// its own address; a call under stream capture uses the address of the last uncaptured
+// call on that device.
 constexpr int kMaxDevices = 256;
 double* g_work_addr[kMaxDevices] = {nullptr};
 std::mutex g_work_mu;
@@ -62,10 +65,16 @@ extern "C" qmc_status qmc_slater_invert_noalloc(qmc_precision prec, const void* 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return bad(QMC_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return bad(QMC_EINVAL, "qmc_slater_invert_noalloc: device index too large");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cap);
+  if (e != cudaSuccess) return bad(QMC_ECUDA, cudaGetErrorString(e));
   double* work = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_work_mu);
-    if (!g_work_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_work_addr[dev]) {
+      if (cap != cudaStreamCaptureStatusNone)
+        return bad(QMC_EINVAL, "qmc_slater_invert_noalloc: the first call on a device must "
+                               "not be under stream capture");
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_work);
       if (e != cudaSuccess) return bad(QMC_ECUDA, cudaGetErrorString(e));

@@ -134,8 +134,7 @@ __global__ void __launch_bounds__(kWinThreads, 2)
   const int ns = spin ? S.n_dn : S.n_up;
   const TW Lw = Cst<TW>::L(S), iLw = Cst<TW>::invL(S);
   const TW* ionw = Cst<TW>::ions(S);
-  const TW* B = static_cast<const TW*>(Wk.binv) +
-                (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  const TW* B = binv_block<const TW>(S, Wk, w, spin);
   const TW* B0 = B + (size_t)(e0 - first) * ns;                        // row of move t: B0 + t ns
   const TW* P0 = Pv + ((size_t)w * p_n + (e0 - p_e0)) * 5 * ld_v;      // rows of move t: P0 + 5 t ld_v
   double* gpos = Wk.pos + (size_t)w * 3 * n_e;

@@ -25,9 +25,12 @@ constexpr int kTcCols = 128;                    // TMEM columns per block: two a
 // Padded window width (a multiple of 16) for a window capacity kc.
 __host__ __device__ inline int flush_tc_mpad(int kc) { return (kc + 15) & ~15; }
 
+constexpr int kTcStageLd = kTcNChunk + 4;       // row stride (floats) of the epilogue tile
+
 // Dynamic shared memory of k_flush_tc for a window capacity kc. The first region holds
 // the Binv0 chunk during the first product and, once that is complete, the Z tile and the
-// two U^T buffers of the second.
+// two U^T buffers of the second; the last region is the epilogue's staging tile (-P of one
+// 64-column chunk, rows padded to kTcStageLd floats).
 __host__ __device__ inline size_t flush_tc_smem_bytes(int kc) {
   const size_t mx = flush_tc_mpad(kc);
   const size_t a1 = 2 * (size_t)kTcRows * kTcKChunk * 4;                       // hi + lo
@@ -35,6 +38,8 @@ __host__ __device__ inline size_t flush_tc_smem_bytes(int kc) {
   size_t b = a1 > zu ? a1 : zu;
   b += 2 * mx * kTcKChunk * 4;                  // Phi chunk, hi + lo
   b += (size_t)kc * kc * 4 + (size_t)kc * 4 + 64;
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)kTcRows * kTcStageLd * 4;        // epilogue staging tile
   return b;
 }
 
@@ -95,12 +100,16 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   float* B1l = B1h + mx * kTcKChunk;
   float* ci = B1l + mx * kTcKChunk;
   int* wrow = reinterpret_cast<int*>(ci + kc * kc);
+  float* stage = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(wrow + kc) + 64 + 15) & ~uintptr_t(15));   // [128][kTcStageLd]
   const float* gphi = static_cast<const float*>(Wk.win_phi) + (size_t)w * kc * ld_v;
   const float* gu = static_cast<const float*>(Wk.win_u) + (size_t)w * kc * ld_v;
   const float* gc = static_cast<const float*>(Wk.win_cinv) + (size_t)w * kc * kc;
-  float* B = static_cast<float*>(Wk.binv) + (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) +
-             (spin ? S.n_up * S.n_up : 0);
+  float* B = binv_block<float>(S, Wk, w, spin);
   const bool vec = (ns & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+  // epilogue by bulk reduce-add: every row segment of a chunk is a whole number of 16-byte
+  // pieces starting on a 16-byte boundary
+  const bool bulk = vec;
   for (int i = tid; i < kc * kc; i += blockDim.x) ci[i] = gc[i];
   for (int i = tid; i < m; i += blockDim.x) wrow[i] = Wk.win_row[(size_t)w * kc + i];
   if (warp == 0) {
@@ -270,7 +279,47 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   const int q4 = warp & 3, h2 = warp >> 2;      // lane quarter, column half of a chunk
   const int n = q4 * 32 + lane;
   float* erow = B + (size_t)(r0 + n) * ns;
-  for (int c = 0; c < n_chunks && ok; ++c) {
+  if (bulk) {
+    // Binv0 += (-P): -P of each 64-column chunk is written to the staging tile (thread = row,
+    // conflict-free with the padded stride) and added to global memory by one bulk
+    // reduce-add per row, so the epilogue reads no Binv0 and the LSU pipe only stores the
+    // tile once. The reduce-add rounds B + (-P) to nearest, exactly as B - P would be.
+    for (int c = 0; c < n_chunks && ok; ++c) {
+      if (tid == 0 && c + 1 < n_chunks) {
+        tc::fence_after();
+        issue2(c + 1);
+      }
+      ok = tc::mbar_wait(&bar[1 + (c & 1)], (uint32_t)((c >> 1) & 1), kTcWaitPolls);
+      // the previous chunk's reduce-adds have read the staging tile
+      if (tid < kTcRows && c > 0) tc::bulk_wait_read<0>();
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      tc::fence_after();
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (c & 1) * kTcNChunk + h2 * 32 + g * 16, v);
+        float* srow = stage + (size_t)n * kTcStageLd + h2 * 32 + g * 16;
+#pragma unroll
+        for (int t = 0; t < 16; t += 4)
+          *reinterpret_cast<float4*>(srow + t) = make_float4(-v[t], -v[t + 1], -v[t + 2], -v[t + 3]);
+      }
+      // U^T buffer c & 1 is free (its MMAs completed): stage chunk c + 2 there
+      if (c + 2 < n_chunks) stage_u(c + 2, tid, blockDim.x);
+      tc::fence_async_smem();
+      tc::fence_before();
+      __syncthreads();
+      if (tid < nr) {                            // one reduce-add per row of the tile
+        const int j0 = c * kTcNChunk;
+        const int cols = min(kTcNChunk, ns - j0);
+        tc::bulk_s2g_add_f32(B + (size_t)(r0 + tid) * ns + j0, stage + (size_t)tid * kTcStageLd,
+                             (uint32_t)cols * 4u);
+        tc::bulk_commit();
+      }
+    }
+    if (tid < kTcRows) tc::bulk_wait_all<0>();   // done before the block's shared memory goes
+  }
+  for (int c = 0; c < n_chunks && ok && !bulk; ++c) {
     // the other accumulator and U^T buffer were released by the previous iteration
     if (tid == 0 && c + 1 < n_chunks) {
       tc::fence_after();
@@ -368,8 +417,7 @@ __global__ void __launch_bounds__(256) k_refine_scales(SysParams S, WalkParams W
   const int first = spin ? S.n_up : 0;
   const int ld5 = 5 * Wk.ld_v;
   const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
-  const float* B = static_cast<const float*>(Wk.binv) +
-                   (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  const float* B = binv_block<const float>(S, Wk, w, spin);
   int* out = Wk.rscale + (size_t)(2 * w + spin) * 2 * Wk.ld_v + op * Wk.ld_v;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int r = warp; r < ns; r += nwarp) {
@@ -442,8 +490,7 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
   const int e0 = (blockIdx.y / nt) * kRsRows, f0 = (blockIdx.y % nt) * kRsRows;
   const int ld5 = 5 * Wk.ld_v;
   const float* VG = static_cast<const float*>(Wk.vgl) + ((size_t)w * S.n_e + first) * ld5;
-  const float* B = static_cast<const float*>(Wk.binv) +
-                   (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  const float* B = binv_block<const float>(S, Wk, w, spin);
   float* Rg = reinterpret_cast<float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
   const int* sc = Wk.rscale + (size_t)(2 * w + spin) * 2 * Wk.ld_v;
   __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(smem_rt);   // [stage][operand][slice]
@@ -594,8 +641,8 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
 // Bn[e][j] = Binv[e][j] + sum_f R^T[e][f] Binv[f][j], a product of two N_s x N_s matrices per
 // walker and spin. |R| <= 10^-2 (walkers above take the FP64 re-inversion), so 3xTF32
 // operands (error ~2^-22 |R| |X|) keep the result at FP32 storage accuracy. Block
-// (w, y) computes the 128 x 128 tile (e0, j0) into the second half of the walker's work
-// area. A operand: rows e of R^T (K = f contiguous, as the residual kernel stores R).
+// (w, y) computes the 128 x 128 tile (e0, j0) into the spin block's second inverse buffer
+// (binv_alt), which the host then makes the current one. A operand: rows e of R^T (K = f contiguous, as the residual kernel stores R).
 // B operand: Binv[f][j0..j0+127], staged transposed into K-major tiles (thread = column j,
 // 16 consecutive f packed into float4 stores). Two shared-memory stages, loads one
 // chunk ahead in registers, MMAs issued by one thread with bounded mbarrier waits.
@@ -615,10 +662,9 @@ __global__ void __launch_bounds__(256, 1) k_refine_update_tc(SysParams S, WalkPa
   const int ns = spin ? S.n_dn : S.n_up;
   const int nt = (ns + kTcRows - 1) / kTcRows;
   const int e0 = (blockIdx.y / nt) * kTcRows, j0 = (blockIdx.y % nt) * kTcRows;
-  const float* B = static_cast<const float*>(Wk.binv) +
-                   (size_t)w * (S.n_up * S.n_up + S.n_dn * S.n_dn) + (spin ? S.n_up * S.n_up : 0);
+  const float* B = binv_block<const float>(S, Wk, w, spin);
   const float* Rt = reinterpret_cast<const float*>(Wk.scratch64 + (size_t)(2 * w + spin) * Wk.ld_v * Wk.ld_v);
-  float* Bn = const_cast<float*>(Rt) + (size_t)ns * ns;
+  float* Bn = static_cast<float*>(Wk.binv_alt[spin]) + (size_t)w * ns * ns;
   float* tiles = reinterpret_cast<float*>(smem_u);  // [stage][Ah, Al, Bh, Bl][128 x 32]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {

@@ -70,6 +70,13 @@ __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t by
                "r"(smem_u32(src)), "r"(bytes)
                : "memory");
 }
+// global[dst .. dst + bytes) += shared[src ..] element-wise in FP32 (round to nearest), by
+// the bulk-copy unit in the thread's current bulk group; same alignment rules as bulk_s2g.
+__device__ __forceinline__ void bulk_s2g_add_f32(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;\n" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void bulk_wait_read() {

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA"
                 -4: "QMC_ESINGULAR", -5: "QMC_ETIMEOUT", -6: "QMC_ESTATE"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 KERNEL_CLASSES = ("propose", "vgl", "sweep", "energy", "reinvert", "vgl_current",
-                  "accumulate", "flush", "refine", "refine_update")
+                  "accumulate", "flush", "refine", "refine_update", "logdet")
 MOVES = {"metropolis": 0, "drift": 1}
 
 # Exported symbols and their ctypes signatures (argtypes, restype), as declared in
@@ -33,7 +33,7 @@ class SystemDesc(C.Structure):
                 ("kappa", C.c_double), ("with_potential", C.c_int), ("prec", C.c_int),
                 ("move", C.c_int), ("step", C.c_double), ("delay_k", C.c_int),
                 ("reinv_period", C.c_int), ("reinv_on_accepted", C.c_int),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("logdet_period", C.c_int), ("drift_a", C.c_double)]
 
 
 _vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
@@ -53,6 +53,8 @@ SIGNATURES = {
     "qmc_get_inverse": ([_vp, _i, _i, _vp], _i),
     "qmc_get_orbitals": ([_vp, _i, _vp], _i),
     "qmc_check_errors": ([_vp, _vp], _i),
+    "qmc_get_logdet": ([_vp, _vp, _vp], _i),
+    "qmc_get_precision_report": ([_vp, _vp, _vp], _i),
     "qmc_launch_count": ([_vp], C.c_int64),
     "qmc_profile_enable": ([_vp, _i], _i),
     "qmc_profile_read": ([_vp, _vp, _vp], _i),
@@ -63,10 +65,12 @@ SIGNATURES = {
     "qmc_slater_invert_noalloc": ([_i, _vp, _vp, _vp, _vp, _i, _i, _vp], _i),
     "qmc_dmc_create": ([_vp, _vp, _vp, _vp, _i, _i, C.POINTER(_vp)], _i),
     "qmc_dmc_step": ([_vp, _i, _vp], _i),
+    "qmc_dmc_set_mode": ([_vp, _i, _i], _i),
     "qmc_dmc_read": ([_vp, _i, _vp], _i),
     "qmc_dmc_walkers": ([_vp, _i, _i, _vp, _vp, _vp, C.POINTER(_i)], _i),
     "qmc_dmc_launch_count": ([_vp], C.c_int64),
     "qmc_dmc_destroy": ([_vp], None),
+    "qmc_measure_rates": ([_vp], _i),
 }
 
 _lib: Optional[C.CDLL] = None
@@ -107,9 +111,11 @@ def _ptr(a) -> int:
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
         return a.ctypes.data
-    assert a.is_contiguous(), "tensors must be contiguous"
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
     return a.data_ptr()
 
 
@@ -124,7 +130,7 @@ class System:
 
     def __init__(self, n_up, n_dn, L, ions, precision="fp64", move="metropolis", step=0.3,
                  delay_k=1, reinv_period=0, reinv_on_accepted=False, seed=0, ion_Z=4.0,
-                 kappa=1.0, with_potential=True):
+                 kappa=1.0, with_potential=True, logdet_period=0, drift_a=0.0):
         lib = load()
         ions = np.ascontiguousarray(np.asarray(ions, dtype=np.float64).reshape(-1, 3))
         self._ions = ions
@@ -132,7 +138,7 @@ class System:
                        ions.ctypes.data_as(C.POINTER(C.c_double)), float(ion_Z), float(kappa),
                        int(bool(with_potential)), PRECISIONS[precision], MOVES[move],
                        float(step), int(delay_k), int(reinv_period), int(bool(reinv_on_accepted)),
-                       int(seed) & 0xFFFFFFFFFFFFFFFF)
+                       int(seed) & 0xFFFFFFFFFFFFFFFF, int(logdet_period), float(drift_a))
         h = C.c_void_p()
         _check(lib.qmc_system_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -237,6 +243,22 @@ class Walkers:
         _check(load().qmc_get_orbitals(self.h, int(walker), o.ctypes.data))
         return o
 
+    def logdet(self):
+        """(ln|det A|, sign) of both spin blocks of every walker: two [n_w][2] arrays."""
+        ld = np.zeros((self.n_w, 2))
+        sg = np.zeros((self.n_w, 2))
+        _check(load().qmc_get_logdet(self.h, ld.ctypes.data, sg.ctypes.data))
+        return ld, sg
+
+    def precision_report(self):
+        """(residual, logdet_shift), each [n_w][2]: max |I - A X| measured by the last
+        batched re-inversion of each walker and spin block, and the change the last
+        log-determinant anchor made to ln|det A| (NaN before the first of each)."""
+        r = np.zeros((self.n_w, 2))
+        d = np.zeros((self.n_w, 2))
+        _check(load().qmc_get_precision_report(self.h, r.ctypes.data, d.ctypes.data))
+        return r, d
+
     def check(self, stream=None):
         _check(load().qmc_check_errors(self.h, _stream_ptr(stream)))
 
@@ -285,6 +307,11 @@ class DMC:
     def step(self, n=1, stream=None):
         _check(load().qmc_dmc_step(self.h, int(n), _stream_ptr(stream)))
 
+    def set_mode(self, effective_tau=False, reconfigure=False):
+        """Effective time step in the branching factor; stochastic reconfiguration at a
+        fixed walker count instead of branching."""
+        _check(load().qmc_dmc_set_mode(self.h, int(bool(effective_tau)), int(bool(reconfigure))))
+
     def read(self, system):
         """dict: population, sum_w, sum_we, e_mean, e_trial_used, e_trial_next, next_id,
         population_before."""
@@ -321,11 +348,45 @@ class DMC:
             pass
 
 
+def _invert_args(A, Binv, logdet, sign):
+    """(precision, batch, n) of a batched re-inversion after checking every array: the
+    library trusts these sizes, so a short or mistyped buffer must be refused here."""
+    for name, t in (("A", A), ("Binv", Binv)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+    if A.dim() != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError(f"A must be [batch][n][n], got {tuple(A.shape)}")
+    if tuple(Binv.shape) != tuple(A.shape) or Binv.dtype != A.dtype:
+        raise ValueError("Binv must have the shape and dtype of A")
+    if A.element_size() not in (4, 8) or not A.is_floating_point():
+        raise ValueError("A must be float32 or float64")
+    batch = int(A.shape[0])
+    for name, t in (("logdet", logdet), ("sign", sign)):
+        if t is None:
+            continue
+        if not (hasattr(t, "is_cuda") and t.is_cuda) or t.element_size() != 8 or not t.is_floating_point():
+            raise ValueError(f"{name} must be a CUDA float64 tensor")
+        if t.numel() < batch:
+            raise ValueError(f"{name} holds {t.numel()} values for a batch of {batch}")
+    devs = {t.device for t in (A, Binv, logdet, sign) if t is not None}
+    if len(devs) != 1:
+        raise ValueError("all arrays must be on the same device")
+    prec = PRECISIONS["fp64"] if A.element_size() == 8 else PRECISIONS["fp32"]
+    return prec, batch, int(A.shape[1])
+
+
+def measure_rates() -> dict:
+    """FP32 and FP64 FMA throughput (TFLOP/s) and L2 read bandwidth (GB/s) of the current
+    device, measured by the library's own kernels."""
+    o = np.zeros(3)
+    _check(load().qmc_measure_rates(o.ctypes.data))
+    return {"fp32_tflops": float(o[0]), "fp64_tflops": float(o[1]), "l2_read_gbs": float(o[2])}
+
+
 def slater_invert(A, Binv, logdet=None, sign=None, stream=None):
     """FP64 re-inversion of a batch of Slater matrices: A and Binv are CUDA tensors
     [batch][n][n] (float64 or float32), logdet/sign CUDA float64 [batch] or None."""
-    prec = PRECISIONS["fp64"] if A.element_size() == 8 else PRECISIONS["fp32"]
-    batch, n, _ = A.shape
+    prec, batch, n = _invert_args(A, Binv, logdet, sign)
     _check(load().qmc_slater_invert(prec, _ptr(A), _ptr(Binv), _ptr(logdet), _ptr(sign), n,
                                     batch, _stream_ptr(stream)))
 
@@ -333,14 +394,14 @@ def slater_invert(A, Binv, logdet=None, sign=None, stream=None):
 def slater_invert_noalloc(A, Binv, logdet=None, sign=None, stream=None):
     """As slater_invert, for callers that cannot allocate device memory: uses the
     library's fixed 16 MiB work area (batch * n * n <= 2**21); concurrent calls race."""
-    prec = PRECISIONS["fp64"] if A.element_size() == 8 else PRECISIONS["fp32"]
-    batch, n, _ = A.shape
+    prec, batch, n = _invert_args(A, Binv, logdet, sign)
     _check(load().qmc_slater_invert_noalloc(prec, _ptr(A), _ptr(Binv), _ptr(logdet), _ptr(sign),
                                             n, batch, _stream_ptr(stream)))
 
 
 def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0,
-                       reinv_on_accepted=False, step=None, move=None) -> System:
+                       reinv_on_accepted=False, step=None, move=None,
+                       logdet_period=0, drift_a=0.0) -> System:
     """System (with spline table and Jastrow functors) from a ``synthetic.build_inputs``
     dictionary, or any dictionary with the same keys."""
     spec = inputs["spec"]
@@ -348,7 +409,8 @@ def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0
                move=move or spec.move, step=spec.step if step is None else step,
                delay_k=delay_k, reinv_period=reinv_period,
                reinv_on_accepted=reinv_on_accepted, seed=inputs["seed"], ion_Z=spec.ion_Z,
-               kappa=spec.kappa, with_potential=spec.with_potential)
+               kappa=spec.kappa, with_potential=spec.with_potential,
+               logdet_period=logdet_period, drift_a=drift_a)
     s.set_spline(inputs["coef"])
     j = inputs["jastrow"]
     for which, key in enumerate(("eI", "same", "opp")):

@@ -55,3 +55,13 @@ def test_python_binding_raises_instead_of_falling_back():
     from paper_1802_06922_gb300 import qmcgb
     with pytest.raises(qmcgb.QMCError):
         qmcgb.System(4, 4, -1.0, [])
+
+
+def test_invert_wrappers_refuse_host_tensors():
+    """The re-inversion wrappers check their arrays before calling the library."""
+    torch = pytest.importorskip("torch")
+    from paper_1802_06922_gb300 import qmcgb as q
+    A = torch.zeros(2, 4, 4, dtype=torch.float64)
+    for fn in (q.slater_invert, q.slater_invert_noalloc):
+        with pytest.raises(ValueError):
+            fn(A, torch.zeros_like(A))

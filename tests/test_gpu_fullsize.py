@@ -2,13 +2,11 @@
 (all walkers, mixed precision, delayed rank-k, re-inversion cadence), on sampled outputs
 the FP64 oracle can compute one by one:
 
-* the first moves of sampled walkers: relative ratio errors (floor 1e-3) with the 90th
-  percentile below 1e-4 and the maximum below 1e-3, and the same accept decisions up to the
-  first decision that sits at u ~ A (after a legitimate flip the chains differ, so the
-  comparison stops there). The tail is reported, not gated: at N_s = 256 these random
-  plane-wave Slater matrices have condition numbers of 1e3 to 4.5e4, and single-precision
-  storage of the inverse alone bounds a ratio's accuracy by about cond * 2^-24, so 1 to 5 %
-  of moves exceed 1e-4 (the FP64 form agrees to 1e-10 on every move);
+* the first moves of sampled walkers: every move's relative ratio error (floor 1e-3) within
+  the per-move gate max(1e-4, cond 2^-24) of parity_util, with cond the oracle's condition
+  number of the moved spin block, and the same accept decisions up to the first decision
+  that sits at u ~ A within twice that gate (after a legitimate flip the chains differ, so
+  the comparison stops there);
 * the local energy of sampled walkers at the GPU's final configuration within
   1e-5 Ha per electron of the oracle's value at the same positions;
 * the inverse of sampled walkers against the orbital matrix at the final positions.
@@ -25,11 +23,13 @@ if not torch.cuda.is_available():
 
 import paper_1802_06922_gb300 as q   # noqa: E402
 from oracle.vmc import OracleSystem   # noqa: E402
+from parity_util import logpsi_tol, ratio_gate   # noqa: E402
 
 CASES = [
     # preset, precision, delay k, re-inversion period, counted on accepted moves,
     # sampled walkers, sampled moves
-    ("sj512", "fp32", 16, 128, False, (0, 129), 40),
+    ("sj512", "fp32", 32, 128, False, (0, 129), 40),    # the benched configuration
+    ("sj512", "fp32", 16, 128, False, (3,), 40),
     ("sj512", "bf16", 16, 128, False, (7,), 24),
     ("sj128", "fp32", 16, 64, True, (0, 300), 64),
     ("sj1024", "fp32", 32, 256, False, (5,), 20),
@@ -41,13 +41,13 @@ def test_full_size_sampled_parity(preset, precision, k, period, on_acc, sample, 
     spec = spec_for(preset)
     inputs = build_inputs(spec)
     s = q.system_from_inputs(inputs, precision=precision, delay_k=k, reinv_period=period,
-                             reinv_on_accepted=on_acc)
+                             reinv_on_accepted=on_acc, logdet_period=0 if on_acc else period)
     w = q.Walkers(s, inputs["pos"])
     ne, nw = spec.n_elec, spec.n_walkers
     buf = torch.zeros((nw, ne, 8), dtype=torch.float64, device="cuda")
     w.trace_enable(buf)
     w.sweep(1)
-    e_gpu, _ = w.measure()
+    e_gpu, lp_gpu = w.measure()
     tr = buf.cpu().numpy()
     final = w.positions()
     acc = tr[..., 7].mean()
@@ -57,23 +57,29 @@ def test_full_size_sampled_parity(preset, precision, k, period, on_acc, sample, 
         from parity_util import bf16_round
         coef = bf16_round(coef)
     osys = OracleSystem(inputs, coef=coef)
-    errs = []
+    errs, worst = [], 0.0
     for wid in sample:
         ow = osys.walker(inputs["pos"][wid], wid)
-        rows = []
-        osys.sweep(ow, 0, trace=rows, electrons=range(n_moves))
+        rows, conds = [], []
+        osys.sweep(ow, 0, trace=rows, electrons=range(n_moves), conds=conds)
         ref = np.array(rows)
         got = tr[wid, :n_moves]
         for mv in range(n_moves):
-            errs.append(abs(got[mv, 0] - ref[mv, 0]) / max(abs(ref[mv, 0]), 1e-3))
+            err, bound = ratio_gate(got[mv, 0], ref[mv, 0], conds[mv])
+            errs.append(float(err))
+            worst = max(worst, float(err / bound))
+            assert err <= bound, (wid, mv, float(err), float(bound), conds[mv])
             assert got[mv, 5] == ref[mv, 5]
             if got[mv, 7] != ref[mv, 7]:
-                assert abs(ref[mv, 5] - ref[mv, 6]) <= 1e-3 * ref[mv, 6] + 1e-12, (wid, mv)
+                assert abs(ref[mv, 5] - ref[mv, 6]) <= 2 * bound * ref[mv, 6] + 1e-12, (wid, mv)
                 break
         # local energy at the GPU's final configuration
         fw = osys.walker(final[wid], wid)
-        e_ref = osys.measure(fw)[0]
+        e_ref, _, lp_ref = osys.measure(fw)
         assert abs(e_gpu[wid] - e_ref) / ne < 1e-5, (wid, e_gpu[wid], e_ref)
+        print(f"{preset} {precision} k={k} walker {wid}: ln|Psi| error {lp_gpu[wid] - lp_ref:.2e}")
+        if not on_acc:       # anchored at every re-inversion (the batched form)
+            assert abs(lp_gpu[wid] - lp_ref) <= logpsi_tol(ne), (wid, lp_gpu[wid] - lp_ref)
         # the inverse of each spin block against the orbital values at the final positions
         orb = w.orbitals(wid)
         for spin, (first, ns) in enumerate(((0, spec.n_up), (spec.n_up, spec.n_dn))):
@@ -82,8 +88,42 @@ def test_full_size_sampled_parity(preset, precision, k, period, on_acc, sample, 
             assert res < 1e-3, (wid, spin, res)
     errs = np.array(errs)
     print(f"{preset} {precision} k={k}: ratio rel err median {np.median(errs):.2e} "
-          f"p90 {np.quantile(errs, 0.9):.2e} p99 {np.quantile(errs, 0.99):.2e} max {errs.max():.2e}")
-    assert np.quantile(errs, 0.9) < 1e-4
-    assert errs.max() < 1e-3
+          f"p90 {np.quantile(errs, 0.9):.2e} p99 {np.quantile(errs, 0.99):.2e} "
+          f"max {errs.max():.2e}; worst err/bound {worst:.3f}")
+    w.close()
+    s.close()
+
+
+@pytest.mark.parametrize("precision,anchor", [("fp32", 128), ("bf16", 128), ("fp32", 1024)])
+def test_logpsi_over_many_sweeps(precision, anchor):
+    """ln|Psi| of the single-precision forms stays tied to the FP64 oracle over 56 sweeps of
+    the 512-electron workload (k = 32, re-inversion every 128 moves, log-determinant anchor
+    every `anchor` moves; 1024 is the bench's cadence): the oracle recomputes ln|Psi| from
+    scratch at the GPU's final positions of sampled walkers. 56 sweeps (14336 moves per spin
+    block) end right after an anchor for both cadences, so the gate is the single-precision
+    floor; the drift the anchors removed along the way (their shifts) is reported."""
+    spec = spec_for("sj512")
+    inputs = build_inputs(spec)
+    coef = inputs["coef"]
+    if precision == "bf16":
+        from parity_util import bf16_round
+        coef = bf16_round(coef)
+    s = q.system_from_inputs(inputs, precision=precision, delay_k=32, reinv_period=128,
+                             logdet_period=anchor)
+    w = q.Walkers(s, inputs["pos"])
+    shifts = []
+    for _ in range(56):
+        w.sweep(1)
+        shifts.append(w.precision_report()[1].ravel())
+    _, lp = w.measure()
+    final = w.positions()
+    osys = OracleSystem(inputs, coef=coef)
+    errs = [lp[wid] - osys.wf.log_psi(final[wid])[0] for wid in (0, 101, 255)]
+    sh = np.abs(np.concatenate(shifts))
+    sh = sh[np.isfinite(sh)]                      # NaN before a walker's first anchor
+    print(f"{precision} anchor {anchor}: ln|Psi| error after 56 sweeps {np.round(errs, 7)}; anchor "
+          f"shifts median {np.median(sh):.2e} p99 {np.quantile(sh, 0.99):.2e} max {sh.max():.2e}")
+    assert sh.size > 0
+    assert np.max(np.abs(errs)) <= logpsi_tol(spec.n_elec), errs
     w.close()
     s.close()

@@ -50,8 +50,28 @@ def test_singular_matrix_is_reported():
 
 def test_invert_rejects_bad_arguments():
     A = torch.zeros((1, 4, 4), dtype=torch.float64, device="cuda")
-    with pytest.raises(q.QMCError):
-        q.slater_invert(A.cpu(), A)                      # host memory
+    with pytest.raises(ValueError):
+        q.slater_invert(A.cpu(), A)                      # host memory, caught by the binding
+    h = A.cpu()
+    lib = q.load()                                       # and by the library itself
+    assert lib.qmc_slater_invert(0, h.data_ptr(), A.data_ptr(), None, None, 4, 1, None) == q.QMC_EINVAL
     big = torch.zeros((1, 1025, 1025), dtype=torch.float64, device="cuda")
     with pytest.raises(q.QMCError):
         q.slater_invert(big, big)
+
+
+def test_invert_refuses_mismatched_buffers():
+    """Shapes, dtypes and lengths are checked before the library is called (a short or
+    mistyped buffer would otherwise be written past its end)."""
+    A = torch.eye(8, dtype=torch.float64, device="cuda").expand(3, 8, 8).contiguous()
+    bad = [
+        (A, torch.empty(3, 8, 8, dtype=torch.float32, device="cuda"), None, None),   # dtype
+        (A, torch.empty(2, 8, 8, dtype=torch.float64, device="cuda"), None, None),   # shape
+        (A, torch.empty_like(A), torch.empty(2, dtype=torch.float64, device="cuda"), None),
+        (A, torch.empty_like(A), None, torch.empty(3, dtype=torch.float32, device="cuda")),
+        (A[:, :, :7].contiguous(), torch.empty(3, 8, 7, dtype=torch.float64, device="cuda"), None, None),
+    ]
+    for args in bad:
+        for fn in (q.slater_invert, q.slater_invert_noalloc):
+            with pytest.raises(ValueError):
+                fn(*args)

@@ -48,3 +48,21 @@ def test_noalloc_refuses_a_batch_beyond_its_work_area():
         q.slater_invert_noalloc(A, A)
     assert err.value.status == q.QMC_EINVAL
     assert "work area" in str(err.value)
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After a first call (which may make the runtime load the work area), further calls
+    leave the device's free memory unchanged: nothing is allocated on their behalf."""
+    batch, n = 4, 128
+    A = _inputs(7, batch, n, torch.float64)
+    B = torch.empty_like(A)
+    ld = torch.empty(batch, dtype=torch.float64, device="cuda")
+    sg = torch.empty_like(ld)
+    q.slater_invert_noalloc(A, B, ld, sg)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        q.slater_invert_noalloc(A, B, ld, sg)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
