@@ -134,6 +134,22 @@ qmc_status qmc_system_set_spline(qmc_system_t sys, int nx, int ny, int nz, int n
 qmc_status qmc_system_set_jastrow(qmc_system_t sys, int which, int M, double rcut,
                                   const double* p, int cusp_set, double cusp);
 
+/* Semi-local (non-local) pseudopotential channels of every ion (Sec. "Hamiltonian": the
+ * electron-ion term gains sum_lm |Y_lm> [v_l(r) - v_loc(r)] <Y_lm| within a cutoff, evaluated
+ * following Mitas et al. with a 12-point angular integration). Channels l = 0 .. n_channels-1
+ * with v_l - v_loc = amp[l] exp(-(r / width[l])^2) for r < rcut (host arrays, copied; a smooth
+ * synthetic form, as no tabulated pseudopotential is used). Every measurement then adds, for
+ * each electron within rcut of an ion (nearest image), the 12-point quadrature
+ *   sum_l (2l+1) dv_l(r) (1/12) sum_q P_l(u . O n_q) Psi(r_i -> R_I + r O n_q) / Psi
+ * to E_L: n_q the vertices of an icosahedron (exact to degree 5), O a uniform random rotation
+ * from Philox block (t, 0xD, walker ID, 3) with t the walker set's count of completed sweeps,
+ * and each ratio a virtual move (determinant ratio times exp(dJ)) with no update. At most
+ * 2 N_e pairs per walker (else the next synchronising call fails with QMC_ECUDA).
+ * n_channels = 0 removes the channels. QMC_EINVAL for n_channels outside [0, 4], a width
+ * <= 0 or rcut outside (0, L/2]. Takes effect at the next measurement. */
+qmc_status qmc_system_set_nonlocal(qmc_system_t sys, int n_channels, const double* amp,
+                                   const double* width, double rcut);
+
 /* Creates n_walkers walkers (the ensemble of independent Markov chains of Sec.
  * "Variational Monte Carlo", each a configuration R of all electrons) with IDs
  * 0..n_walkers-1 at positions pos (host or device [n_walkers][n_up+n_dn][3], wrapped into
@@ -196,6 +212,10 @@ qmc_status qmc_set_state(qmc_walkers_t w, const void* buf, size_t len);
  * QMC_EINVAL for a walker index outside [0, n_walkers) or spin outside {0, 1}. */
 qmc_status qmc_get_inverse(qmc_walkers_t w, int walker, int spin, double* out);
 qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out);
+
+/* The non-local pseudopotential part of the last measurement's E_L, [n_walkers] doubles
+ * (host or device); zeros without channels. Synchronous. */
+qmc_status qmc_get_nonlocal(qmc_walkers_t w, double* out);
 
 /* ln|det A| and the sign of det A of every walker's two Slater matrices (Sec.
  * "Multi-Determinant Slater-Jastrow Form"), as the walker set carries them: logdet and sign
@@ -323,7 +343,8 @@ typedef enum {
   QMC_K_REFINE = 8,       /* single-precision re-inversion: error-free residual R = I - A X */
   QMC_K_REFINE_UPDATE = 9,/* single-precision re-inversion: X <- X + X R, FP64 fallback */
   QMC_K_LOGDET = 10,      /* log-determinant anchor (error-free FP32 LU) */
-  QMC_NKERNELS = 11
+  QMC_K_NLPP = 11,        /* non-local pseudopotential quadrature (pairs and virtual moves) */
+  QMC_NKERNELS = 12
 } qmc_kernel;
 
 /* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA

@@ -295,6 +295,29 @@ extern "C" qmc_status qmc_system_set_jastrow(qmc_system_t s, int which, int M, d
   return QMC_OK;
 }
 
+extern "C" qmc_status qmc_system_set_nonlocal(qmc_system_t s, int n_channels, const double* amp,
+                                               const double* width, double rcut) {
+  if (!s) return fail(QMC_EINVAL, "qmc_system_set_nonlocal: NULL system");
+  if (n_channels < 0 || n_channels > kMaxNlChannels)
+    return fail(QMC_EINVAL, "n_channels must be in [0, %d]", kMaxNlChannels);
+  SysParams& P = s->P;
+  if (n_channels == 0) {
+    P.nl_nch = 0;
+    return QMC_OK;
+  }
+  if (!amp || !width) return fail(QMC_EINVAL, "qmc_system_set_nonlocal: NULL channel arrays");
+  if (!(rcut > 0.0) || rcut > 0.5 * s->d.L * (1 + 1e-12)) return fail(QMC_EINVAL, "rcut must be in (0, L/2]");
+  for (int l = 0; l < n_channels; ++l)
+    if (!(width[l] > 0.0) || !std::isfinite(amp[l])) return fail(QMC_EINVAL, "bad channel %d", l);
+  for (int l = 0; l < kMaxNlChannels; ++l) {
+    P.nl_amp[l] = l < n_channels ? amp[l] : 0.0;
+    P.nl_width[l] = l < n_channels ? width[l] : 1.0;
+  }
+  P.nl_rcut = rcut;
+  P.nl_nch = n_channels;
+  return QMC_OK;
+}
+
 extern "C" void qmc_system_destroy(qmc_system_t s) {
   if (!s) return;
   cudaFree(s->d_table);
@@ -314,7 +337,23 @@ qmc_status check_err(qmc_walkers_s* w, cudaStream_t st) {
     QMC_CUDA(cudaMemset(w->W.err, 0, sizeof(int)));
     if (err & kErrSingular) return fail(QMC_ESINGULAR, "a Slater matrix was singular at (re-)inversion");
     if (err & kErrTimeout) return fail(QMC_ETIMEOUT, "a bounded device wait timed out");
+    if (err & kErrOverflow)
+      return fail(QMC_ECUDA, "more electron-ion pairs inside the pseudopotential cutoff than the "
+                             "per-walker list holds (2 per electron)");
     return fail(QMC_ECUDA, "device error flag 0x%x", err);
+  }
+  return QMC_OK;
+}
+
+// Local energy (and ln|Psi|) of every walker: kinetic + local potential, then the non-local
+// pseudopotential part when the system has one; t seeds the quadrature's rotation.
+qmc_status measure_energy(qmc_walkers_s* w, const WalkParams& W, uint32_t t, cudaStream_t st) {
+  qmc_system_s* s = w->sys;
+  { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, W, st)); }
+  if (s->P.nl_nch > 0 && s->P.n_ion > 0) {
+    Bracket b(w, st, QMC_K_NLPP);
+    QMC_CUDA(s->tt->nlpp(s->P, W, t, st));
+    w->launches += 1;
   }
   return QMC_OK;
 }
@@ -323,7 +362,7 @@ qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   qmc_system_s* s = w->sys;
   { Bracket b(w, st, QMC_K_VGL_CURRENT); QMC_CUDA(s->tt->vgl_current(s->P, w->W, st)); }
   { Bracket b(w, st, QMC_K_REINVERT); QMC_CUDA(s->tw->reinvert(s->P, w->W, st)); }
-  { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, w->W, st)); }
+  { qmc_status r = measure_energy(w, w->W, w->sweep, st); if (r != QMC_OK) return r; }
   QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
   w->since_moves[0] = w->since_moves[1] = 0;
   w->since_anchor[0] = w->since_anchor[1] = 0;
@@ -337,7 +376,7 @@ void free_walkers(qmc_walkers_s* w) {
                   W.sgn, W.wid, W.weight, W.e_loc, W.log_psi, W.n_acc, W.acc_since, W.scratch64,
                   W.err, w->d_P, w->d_prop, w->d_out, w->d_nacc, w->d_forced, W.win_phi,
                   W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
-                  W.logdet_shift, W.rscale, W.r2};
+                  W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -414,6 +453,9 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.refine_last, nw * 2 * sizeof(float)},
       {(void**)&W.logdet_shift, nw * 2 * sizeof(float)},
       {(void**)&W.r2, nw * 2 * sizeof(double)},
+      {(void**)&W.vnl, nw * sizeof(double)},
+      {(void**)&W.nl_pairs, nw * (size_t)std::max(64, 2 * (int)ne) * sizeof(int)},
+      {(void**)&W.nl_count, nw * sizeof(int)},
       {(void**)&W.rscale, nw * 4 * (size_t)W.ld_v * sizeof(int)},
   };
   for (auto& a : allocs) {
@@ -437,6 +479,8 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   cudaMemset(W.refine_last, 0xFF, nw * 2 * sizeof(float));   // NaN: no refinement yet
   cudaMemset(W.logdet_shift, 0xFF, nw * 2 * sizeof(float));  // NaN: no anchor yet
   cudaMemset(W.r2, 0, nw * 2 * sizeof(double));
+  cudaMemset(W.vnl, 0, nw * sizeof(double));
+  W.nl_cap = std::max(64, 2 * (int)ne);
   W.kc = s->d.delay_k;
   *out = w;
   return QMC_OK;
@@ -568,7 +612,8 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
       W.forced = w->d_forced + (size_t)sw * W.n_w * P.n_e;
     qmc_status r = sweep_once(w, W, false, st);
     if (r != QMC_OK) return r;
-    { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(P, W, st)); }
+    r = measure_energy(w, W, w->sweep + 1, st);
+    if (r != QMC_OK) return r;
     if (W.trace) ++w->traced;
     ++w->sweep;
     w->proposed += (long long)W.n_w * P.n_e;
@@ -587,7 +632,8 @@ extern "C" qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_
   if (!w) return fail(QMC_EINVAL, "qmc_measure: NULL walkers");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!w->energy_valid) {
-    { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(w->sys->tw->local_energy(w->sys->P, w->W, st)); }
+    qmc_status r = measure_energy(w, w->W, w->sweep, st);
+    if (r != QMC_OK) return r;
     w->energy_valid = true;
   }
   const size_t b = sizeof(double) * w->W.n_w;
@@ -765,6 +811,19 @@ extern "C" qmc_status qmc_get_orbitals(qmc_walkers_t w, int walker, double* out)
     for (int c = 0; c < 5; ++c)
       for (int j = 0; j < nsm; ++j) o[((size_t)e * 5 + c) * nsm + j] = h[((size_t)e * 5 + c) * ld + j];
   QMC_CUDA(cudaMemcpy(out, o.data(), o.size() * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_get_nonlocal(qmc_walkers_t w, double* out) {
+  if (!w || !out) return fail(QMC_EINVAL, "qmc_get_nonlocal: NULL argument");
+  qmc_status r = check_err(w, 0);
+  if (r != QMC_OK) return r;
+  if (w->sys->P.nl_nch == 0 || w->sys->P.n_ion == 0) {
+    std::vector<double> z(w->W.n_w, 0.0);
+    QMC_CUDA(cudaMemcpy(out, z.data(), z.size() * sizeof(double), cudaMemcpyDefault));
+    return QMC_OK;
+  }
+  QMC_CUDA(cudaMemcpy(out, w->W.vnl, sizeof(double) * w->W.n_w, cudaMemcpyDefault));
   return QMC_OK;
 }
 
@@ -966,7 +1025,8 @@ extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
       QMC_CUDA(cudaMemsetAsync(W.r2, 0, sizeof(double) * 2 * (size_t)W.n_w, y.st));
       qmc_status r = sweep_once(w, W, true, y.st);
       if (r != QMC_OK) return r;
-      { Bracket b(w, y.st, QMC_K_ENERGY); QMC_CUDA(y.sys->tw->local_energy(y.sys->P, W, y.st)); }
+      r = measure_energy(w, W, d->step + 1, y.st);
+      if (r != QMC_OK) return r;
       DmcParams D = y.D;
       D.e_old = y.e_old[y.parity];
       D.e_old_next = y.e_old[y.parity ^ 1];

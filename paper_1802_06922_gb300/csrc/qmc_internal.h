@@ -8,6 +8,7 @@
 namespace qmcgb {
 
 constexpr int kMaxKnots = 32;       // largest Jastrow M
+constexpr int kMaxNlChannels = 4;   // non-local pseudopotential channels l = 0..3
 constexpr size_t kMaxDynSmem = 227 * 1024;   // largest dynamic shared memory of one block (sm_103a)
 constexpr int kMaxDelay = 64;       // largest delay rank k
 constexpr int kThreads = 256;
@@ -19,7 +20,7 @@ struct alignas(32) Prop {
 };
 
 // Device error flags (bitwise OR into WalkParams::err).
-enum : int { kErrSingular = 1, kErrNonFinite = 2, kErrTimeout = 4 };
+enum : int { kErrSingular = 1, kErrNonFinite = 2, kErrTimeout = 4, kErrOverflow = 8 };
 
 // Read-only description of a system, passed to kernels by value.
 struct SysParams {
@@ -47,6 +48,9 @@ struct SysParams {
   int move;            // 0 Metropolis, 1 drift
   double step;
   double drift_a;      // > 0: nodal drift rescaling parameter (0: the plain drift)
+  // non-local pseudopotential: channels dv_l(r) = nl_amp[l] exp(-(r / nl_width[l])^2), r < nl_rcut
+  int nl_nch;          // 0: none
+  double nl_amp[kMaxNlChannels], nl_width[kMaxNlChannels], nl_rcut;
   uint32_t seed_lo, seed_hi;
 };
 
@@ -87,6 +91,10 @@ struct WalkParams {
   const int* n_live;   // optional device count: blocks of walkers >= *n_live return at once
   double* r2;          // [W][2] sums of the squared proposed and accepted displacements of
                        //        drift moves since the last reset (effective time step)
+  double* vnl;         // [W]    non-local pseudopotential energy of the last measurement
+  int* nl_pairs;       // [W][nl_cap] electron * n_ion + ion of the pairs inside the cutoff
+  int* nl_count;       // [W]
+  int nl_cap;
 };
 
 // Inverse of walker w's spin block: Binv[e][j] = (A^-1)[j][e], N_s x N_s, row-major.

@@ -1,6 +1,7 @@
 // Instantiations of the orbital-evaluation kernels per coefficient-table type.
 #include "qmc_kernels.cuh"
 #include "qmc_launch.h"
+#include "qmc_nlpp.cuh"
 
 namespace qmcgb {
 namespace {
@@ -41,21 +42,39 @@ cudaError_t sweep_drift(const SysParams& S, const WalkParams& W, uint32_t t, int
   return cudaGetLastError();
 }
 
+template <class TT, class TW>
+cudaError_t nlpp(const SysParams& S, const WalkParams& W, uint32_t t, cudaStream_t st) {
+  if (S.nl_nch == 0 || S.n_ion == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(W.nl_count, 0, sizeof(int) * W.n_w, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(W.vnl, 0, sizeof(double) * W.n_w, st);
+  if (e != cudaSuccess) return e;
+  const long long n1 = (long long)W.n_w * S.n_e;
+  k_nlpp_pairs<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(S, W, W.nl_pairs, W.nl_count, W.nl_cap);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long warps = (long long)W.n_w * W.nl_cap;
+  k_nlpp_eval<TT, TW><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+      S, W, W.nl_pairs, W.nl_count, W.nl_cap, t, W.vnl);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const TtLaunch& tt_launch_f64() {
   static const TtLaunch L{TabVec<double>::V, vgl_current<double, double>,
-                          vgl_proposals<double, double>, sweep_drift<double, double>};
+                          vgl_proposals<double, double>, sweep_drift<double, double>,
+                          nlpp<double, double>};
   return L;
 }
 const TtLaunch& tt_launch_f32() {
   static const TtLaunch L{TabVec<float>::V, vgl_current<float, float>, vgl_proposals<float, float>,
-                          sweep_drift<float, float>};
+                          sweep_drift<float, float>, nlpp<float, float>};
   return L;
 }
 const TtLaunch& tt_launch_bf16() {
   static const TtLaunch L{TabVec<__nv_bfloat16>::V, vgl_current<__nv_bfloat16, float>,
-                          vgl_proposals<__nv_bfloat16, float>, sweep_drift<__nv_bfloat16, float>};
+                          vgl_proposals<__nv_bfloat16, float>, sweep_drift<__nv_bfloat16, float>,
+                          nlpp<__nv_bfloat16, float>};
   return L;
 }
 

@@ -42,6 +42,8 @@ struct TtLaunch {
   cudaError_t (*sweep_drift)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
                              int k, int reinv_period, int reinv_on_acc, int ext_flush,
                              bool fixed_node, cudaStream_t);
+  // non-local pseudopotential energy of every walker (added to E_L), quadrature rotation t
+  cudaError_t (*nlpp)(const SysParams&, const WalkParams&, uint32_t t, cudaStream_t);
 };
 const TtLaunch& tt_launch_f64();
 const TtLaunch& tt_launch_f32();

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA"
                 -4: "QMC_ESINGULAR", -5: "QMC_ETIMEOUT", -6: "QMC_ESTATE"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 KERNEL_CLASSES = ("propose", "vgl", "sweep", "energy", "reinvert", "vgl_current",
-                  "accumulate", "flush", "refine", "refine_update", "logdet")
+                  "accumulate", "flush", "refine", "refine_update", "logdet", "nlpp")
 MOVES = {"metropolis": 0, "drift": 1}
 
 # Exported symbols and their ctypes signatures (argtypes, restype), as declared in
@@ -41,6 +41,8 @@ SIGNATURES = {
     "qmc_system_create": ([C.POINTER(SystemDesc), C.POINTER(_vp)], _i),
     "qmc_system_set_spline": ([_vp, _i, _i, _i, _i, _vp], _i),
     "qmc_system_set_jastrow": ([_vp, _i, _i, _d, _vp, _i, _d], _i),
+    "qmc_system_set_nonlocal": ([_vp, _i, _vp, _vp, _d], _i),
+    "qmc_get_nonlocal": ([_vp, _vp], _i),
     "qmc_walkers_create": ([_vp, _i, _vp, C.POINTER(_vp)], _i),
     "qmc_sweep": ([_vp, _i, _vp], _i),
     "qmc_measure": ([_vp, _vp, _vp, _vp], _i),
@@ -155,6 +157,14 @@ class System:
                                              p.ctypes.data, int(cusp is not None),
                                              float(cusp or 0.0)))
 
+    def set_nonlocal(self, amp, width, rcut: float):
+        """Non-local pseudopotential channels dv_l(r) = amp[l] exp(-(r/width[l])^2), r < rcut
+        (empty amp removes them)."""
+        a = np.ascontiguousarray(amp, dtype=np.float64)
+        b = np.ascontiguousarray(width, dtype=np.float64)
+        _check(load().qmc_system_set_nonlocal(self.h, int(a.size), a.ctypes.data if a.size else None,
+                                              b.ctypes.data if b.size else None, float(rcut)))
+
     def close(self):
         if getattr(self, "h", None):
             load().qmc_system_destroy(self.h)
@@ -241,6 +251,12 @@ class Walkers:
     def orbitals(self, walker: int) -> np.ndarray:
         o = np.zeros((self.n_e, 5, max(self.system.n_up, self.system.n_dn)))
         _check(load().qmc_get_orbitals(self.h, int(walker), o.ctypes.data))
+        return o
+
+    def nonlocal_energy(self) -> np.ndarray:
+        """V_NL of every walker at the last measurement."""
+        o = np.zeros(self.n_w)
+        _check(load().qmc_get_nonlocal(self.h, o.ctypes.data))
         return o
 
     def logdet(self):
