@@ -486,6 +486,23 @@ def run_ours(args, spec, rank, world, local_rank):
                 "value": whole_job_rate(world, moves_per_step * 10, msa / 1e3), "unit": UNIT,
                 "ms_per_step": msa / 10, "steps": 10, "logdet_period": args.reinv_period,
                 "prof": profa}
+        if args.precision != "fp64" and spec.n_ion > 0:
+            # the same workload with non-local pseudopotential channels on every ion: the
+            # 12-point quadrature's virtual moves are measured after every sweep
+            sn = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+                                      reinv_period=args.reinv_period, logdet_period=logdet_period)
+            sn.set_nonlocal(NL_AMP, NL_WIDTH, NL_RCUT)
+            msn, profn, _, _, _ = timed(sn, 10, args.warmup, profile=True)
+            wn = q.Walkers(sn, pos)
+            wn.sweep(1)
+            pairs = nl_pairs(wn.positions(), inputs["ions"], spec.L, NL_RCUT)
+            wn.close()
+            sn.close()
+            extras["nonlocal_pp"] = {
+                "value": whole_job_rate(world, moves_per_step * 10, msn / 1e3), "unit": UNIT,
+                "ms_per_step": msn / 10, "steps": 10, "channels": {"amp": NL_AMP, "width": NL_WIDTH,
+                                                                    "rcut": NL_RCUT},
+                "pairs_per_walker": pairs / spec.n_walkers, "prof": profn}
         extras["dmc"] = dmc_measure(args, rank, world, 10, dist)
 
     if rank != 0:
@@ -503,6 +520,22 @@ def run_ours(args, spec, rank, world, local_rank):
     kernels = {n: {"ms_per_step": float(prof_ms[i]) / args.steps, "launches": int(prof_n[i]),
                    "roofline": per_class.get(n)}
                for i, n in enumerate(qb.KERNEL_CLASSES) if prof_n[i]}
+    if extras is not None and "nonlocal_pp" in extras:
+        pm, pn = extras["nonlocal_pp"].pop("prof")
+        ix = qb.KERNEL_CLASSES.index("nlpp")
+        nl = extras["nonlocal_pp"]
+        ld = (spec.n_orb + 7) // 8 * 8
+        tab = {"fp32": 4, "bf16": 2, "fp64": 8}[args.precision]
+        per_launch = nl["pairs_per_walker"] * spec.n_walkers * 12 * 64 * ld * tab
+        sec = float(pm[ix]) / 1e3 / max(int(pn[ix]), 1)
+        nl["kernels"] = {n: float(pm[i]) / 10 for i, n in enumerate(qb.KERNEL_CLASSES) if pn[i]}
+        nl["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": peaks.get("hbm_gbs", 6800.0),
+                          "achieved": per_launch / sec / 1e9 if sec > 0 else None,
+                          "kernel": "k_nlpp_pairs + k_nlpp_eval",
+                          "per_unit": f"12 quadrature points x 64 coefficient rows x N_orb x {tab} B "
+                                      f"per electron-ion pair inside the cutoff"}
+        if nl["roofline"]["achieved"]:
+            nl["roofline"]["frac"] = nl["roofline"]["achieved"] / nl["roofline"]["peak"]
     for key, prec in (("bf16_table", "bf16"), ("anchor_every_reinversion", args.precision)):
         if extras is None or key not in extras:
             continue
@@ -538,6 +571,20 @@ def run_ours(args, spec, rank, world, local_rank):
 
 
 DMC_SYSTEMS = ("dmc64", "dmc192", "dmc384")
+
+# synthetic non-local channels of the pseudopotential extra: s and p, Gaussian, cutoff 1.6 bohr
+NL_AMP, NL_WIDTH, NL_RCUT = [1.5, -1.0], [1.0, 0.9], 1.6
+
+
+def nl_pairs(pos, ions, L, rcut):
+    """Electron-ion pairs inside the cutoff (nearest image), summed over walkers."""
+    import numpy as np
+    n = 0
+    for R in pos:
+        d = R[:, None, :] - ions[None, :, :]
+        d -= L * np.rint(d / L)
+        n += int(((d * d).sum(-1) < rcut * rcut).sum())
+    return n
 
 
 def dmc_measure(args, rank, world, n_steps, dist=None):

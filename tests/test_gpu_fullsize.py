@@ -111,10 +111,12 @@ def test_logpsi_over_many_sweeps(precision, anchor):
     s = q.system_from_inputs(inputs, precision=precision, delay_k=32, reinv_period=128,
                              logdet_period=anchor)
     w = q.Walkers(s, inputs["pos"])
-    shifts = []
+    shifts, resid = [], []
     for _ in range(56):
         w.sweep(1)
-        shifts.append(w.precision_report()[1].ravel())
+        res, shift = w.precision_report()
+        shifts.append(shift.ravel())
+        resid.append(res.ravel())
     _, lp = w.measure()
     final = w.positions()
     osys = OracleSystem(inputs, coef=coef)
@@ -125,5 +127,16 @@ def test_logpsi_over_many_sweeps(precision, anchor):
           f"shifts median {np.median(sh):.2e} p99 {np.quantile(sh, 0.99):.2e} max {sh.max():.2e}")
     assert sh.size > 0
     assert np.max(np.abs(errs)) <= logpsi_tol(spec.n_elec), errs
+    # max |I - A X| before the Newton step of each re-inversion (the last one of each spin
+    # block per sweep): one step leaves about its square, so values up to 2^-12 end at
+    # single-precision storage accuracy
+    r = np.concatenate(resid)
+    r = r[np.isfinite(r)]
+    edges = [0, 1e-6, 3e-6, 1e-5, 3e-5, 1e-4, 2.0 ** -12, 5e-4, 1e-3, 1e-2, np.inf]
+    print(f"{precision} anchor {anchor}: residual before the Newton step: n {r.size} median "
+          f"{np.median(r):.2e} p90 {np.quantile(r, 0.9):.2e} p99 {np.quantile(r, 0.99):.2e} "
+          f"max {r.max():.2e}; histogram over {[f'{e:.3g}' for e in edges]}: "
+          f"{np.histogram(r, bins=edges)[0].tolist()}")
+    assert np.mean(r <= 2.0 ** -12) > 0.98
     w.close()
     s.close()
