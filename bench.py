@@ -503,6 +503,19 @@ def run_ours(args, spec, rank, world, local_rank):
                 "ms_per_step": msn / 10, "steps": 10, "channels": {"amp": NL_AMP, "width": NL_WIDTH,
                                                                     "rcut": NL_RCUT},
                 "pairs_per_walker": pairs / spec.n_walkers, "prof": profn}
+        if args.precision != "fp64":
+            # the same workload with Coulomb interactions by Ewald summation in place of the
+            # Yukawa form: erfc(alpha L / 2) = erfc(4) and exp(-kcut^2 / (4 alpha^2)) = e^-16
+            se = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+                                      reinv_period=args.reinv_period, logdet_period=logdet_period)
+            alpha = 8.0 / spec.L
+            se.set_ewald(alpha, 8.0 * alpha)
+            mse, profe, _, _, _ = timed(se, 10, args.warmup, profile=True)
+            extras["ewald"] = {
+                "value": whole_job_rate(world, moves_per_step * 10, mse / 1e3), "unit": UNIT,
+                "ms_per_step": mse / 10, "steps": 10, "alpha": alpha, "kcut": 8.0 * alpha,
+                "k_vectors": se.ewald_count, "prof": profe}
+            se.close()
         extras["dmc"] = dmc_measure(args, rank, world, 10, dist)
 
     if rank != 0:
@@ -536,6 +549,15 @@ def run_ours(args, spec, rank, world, local_rank):
                                       f"per electron-ion pair inside the cutoff"}
         if nl["roofline"]["achieved"]:
             nl["roofline"]["frac"] = nl["roofline"]["achieved"] / nl["roofline"]["peak"]
+    if extras is not None and "ewald" in extras:
+        pm, pn = extras["ewald"].pop("prof")
+        ix = qb.KERNEL_CLASSES.index("ewald")
+        ew = extras["ewald"]
+        sec = float(pm[ix]) / 1e3 / max(int(pn[ix]), 1)
+        ew["kernels"] = {n: float(pm[i]) / 10 for i, n in enumerate(qb.KERNEL_CLASSES) if pn[i]}
+        # one phase term e^{i k.r_i} per electron, k vector and walker at every measurement
+        ew["phase_terms_per_s"] = (spec.n_elec * ew["k_vectors"] * spec.n_walkers / sec
+                                   if sec > 0 else None)
     for key, prec in (("bf16_table", "bf16"), ("anchor_every_reinversion", args.precision)):
         if extras is None or key not in extras:
             continue

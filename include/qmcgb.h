@@ -150,6 +150,29 @@ qmc_status qmc_system_set_jastrow(qmc_system_t sys, int which, int M, double rcu
 qmc_status qmc_system_set_nonlocal(qmc_system_t sys, int n_channels, const double* amp,
                                    const double* width, double rcut);
 
+/* Coulomb interactions by Ewald summation in place of the Yukawa form (Sec. "Hamiltonian":
+ * v_ee = 1/r, v_eI = -Z/r and v_II = Z^2/r summed over every periodic image of the cell,
+ * evaluated with the Ewald technique; Sec. "Long-Range Interactions": short-ranged terms
+ * summed in real space, long-ranged ones in reciprocal space). With splitting parameter
+ * alpha (1/bohr) and reciprocal cutoff kcut, electrons of charge -1, ions of charge +Z,
+ * Q = N_ion Z - N_e and Omega = L^3, every measurement's potential becomes
+ *   V = sum_{a<b} q_a q_b erfc(alpha r_ab) / r_ab          (nearest image of every pair)
+ *     + (4 pi / Omega) sum_{k in H} exp(-k^2 / (4 alpha^2)) / k^2 |rho_k|^2
+ *     - alpha / sqrt(pi) (N_e + N_ion Z^2) - pi Q^2 / (2 Omega alpha^2),
+ * rho_k = Z sum_I e^{i k.R_I} - sum_i e^{i k.r_i}, H the vectors k = 2 pi n / L (n integer)
+ * with 0 < |k| <= kcut, one of each +-k pair. The nearest-image real-space sum equals the
+ * periodic one only when erfc(alpha L / 2) is negligible (alpha L / 2 >= 4: below 2e-8).
+ * rho_k of every walker is evaluated from its positions at each measurement, O(N_e |H|).
+ * alpha = 0 restores the Yukawa form. Synchronous (builds the ions' rho_k and the constant
+ * terms on the device); no other call may use the system meanwhile. QMC_EINVAL for a system
+ * without a potential, alpha < 0 or not finite, kcut not finite or <= 0 with alpha > 0,
+ * kcut L / (2 pi) > 64, or more than 65536 vectors in H. */
+qmc_status qmc_system_set_ewald(qmc_system_t sys, double alpha, double kcut);
+
+/* Number of k vectors in the Ewald half set H of the system, or -1 when the Yukawa form is
+ * in use. */
+int qmc_system_ewald_count(qmc_system_t sys);
+
 /* Creates n_walkers walkers (the ensemble of independent Markov chains of Sec.
  * "Variational Monte Carlo", each a configuration R of all electrons) with IDs
  * 0..n_walkers-1 at positions pos (host or device [n_walkers][n_up+n_dn][3], wrapped into
@@ -344,7 +367,8 @@ typedef enum {
   QMC_K_REFINE_UPDATE = 9,/* single-precision re-inversion: X <- X + X R, FP64 fallback */
   QMC_K_LOGDET = 10,      /* log-determinant anchor (error-free FP32 LU) */
   QMC_K_NLPP = 11,        /* non-local pseudopotential quadrature (pairs and virtual moves) */
-  QMC_NKERNELS = 12
+  QMC_K_EWALD = 12,       /* Ewald reciprocal-space energy (structure factors) */
+  QMC_NKERNELS = 13
 } qmc_kernel;
 
 /* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA

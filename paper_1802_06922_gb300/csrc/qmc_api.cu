@@ -74,6 +74,8 @@ struct qmc_system_s {
   void* d_table = nullptr;
   double* d_ions = nullptr;
   float* d_ionsf = nullptr;
+  int4* d_ew_n = nullptr;      // Ewald half set of integer k vectors
+  double* d_ew = nullptr;      // c_k [n_k], the ions' rho_k [2][n_k], constant [1]
   bool has_spline = false;
   const TwLaunch* tw = nullptr;
   const TtLaunch* tt = nullptr;
@@ -318,8 +320,61 @@ extern "C" qmc_status qmc_system_set_nonlocal(qmc_system_t s, int n_channels, co
   return QMC_OK;
 }
 
+extern "C" qmc_status qmc_system_set_ewald(qmc_system_t s, double alpha, double kcut) {
+  if (!s) return fail(QMC_EINVAL, "qmc_system_set_ewald: NULL system");
+  if (!std::isfinite(alpha) || alpha < 0.0) return fail(QMC_EINVAL, "alpha must be finite and >= 0");
+  SysParams& P = s->P;
+  if (alpha == 0.0) {
+    P.ew_on = 0;
+    return QMC_OK;
+  }
+  if (!s->d.with_potential) return fail(QMC_EINVAL, "qmc_system_set_ewald: the system has no potential");
+  if (!(kcut > 0.0) || !std::isfinite(kcut)) return fail(QMC_EINVAL, "kcut must be finite and > 0");
+  const double L = s->d.L, tl = 2.0 * M_PI / L;
+  const double nm = std::floor(kcut / tl);
+  if (nm > 64.0) return fail(QMC_EINVAL, "kcut L / (2 pi) must not exceed 64");
+  const int nmax = (int)nm;
+  // the half set: one of each +-n pair (the first nonzero component of n positive)
+  std::vector<int4> ns;
+  for (int x = 0; x <= nmax; ++x)
+    for (int y = -nmax; y <= nmax; ++y)
+      for (int z = -nmax; z <= nmax; ++z) {
+        if (!(x > 0 || (x == 0 && (y > 0 || (y == 0 && z > 0))))) continue;
+        const double k2 = tl * tl * (double)(x * x + y * y + z * z);
+        if (k2 > kcut * kcut) continue;
+        if ((int)ns.size() == kEwMaxK)
+          return fail(QMC_EINVAL, "more than %d k vectors in the half set", kEwMaxK);
+        ns.push_back(make_int4(x, y, z, 0));
+      }
+  const int nk = (int)ns.size();
+  QMC_CUDA(cudaDeviceSynchronize());     // no kernel may still read the previous tables
+  cudaFree(s->d_ew_n);
+  cudaFree(s->d_ew);
+  s->d_ew_n = nullptr;
+  s->d_ew = nullptr;
+  P.ew_on = 0;
+  QMC_CUDA(cudaMalloc(&s->d_ew_n, sizeof(int4) * (nk > 0 ? nk : 1)));
+  QMC_CUDA(cudaMalloc(&s->d_ew, sizeof(double) * (3 * (size_t)nk + 1)));
+  if (nk > 0) QMC_CUDA(cudaMemcpy(s->d_ew_n, ns.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice));
+  P.ew_nk = nk;
+  P.ew_alpha = alpha;
+  P.ew_alphaf = (float)alpha;
+  P.ew_n = s->d_ew_n;
+  P.ew_ck = s->d_ew;
+  P.ew_rho_ion = s->d_ew + nk;
+  P.ew_const = s->d_ew + 3 * (size_t)nk;
+  QMC_CUDA(launch_ewald_setup(P, s->d_ew, s->d_ew + nk, s->d_ew + 3 * (size_t)nk, 0));
+  QMC_CUDA(cudaDeviceSynchronize());
+  P.ew_on = 1;
+  return QMC_OK;
+}
+
+extern "C" int qmc_system_ewald_count(qmc_system_t s) { return (s && s->P.ew_on) ? s->P.ew_nk : -1; }
+
 extern "C" void qmc_system_destroy(qmc_system_t s) {
   if (!s) return;
+  cudaFree(s->d_ew_n);
+  cudaFree(s->d_ew);
   cudaFree(s->d_table);
   cudaFree(s->d_ions);
   cudaFree(s->d_ionsf);
@@ -350,6 +405,10 @@ qmc_status check_err(qmc_walkers_s* w, cudaStream_t st) {
 qmc_status measure_energy(qmc_walkers_s* w, const WalkParams& W, uint32_t t, cudaStream_t st) {
   qmc_system_s* s = w->sys;
   { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, W, st)); }
+  if (s->P.ew_on && s->P.ew_nk > 0) {
+    Bracket b(w, st, QMC_K_EWALD);
+    QMC_CUDA(s->tw->ewald_recip(s->P, W, st));
+  }
   if (s->P.nl_nch > 0 && s->P.n_ion > 0) {
     Bracket b(w, st, QMC_K_NLPP);
     QMC_CUDA(s->tt->nlpp(s->P, W, t, st));

@@ -115,6 +115,7 @@ template <> struct Cst<double> {
   __device__ static __forceinline__ double invd(const SysParams& S, int d) { return S.inv_delta[d]; }
   __device__ static __forceinline__ double Z(const SysParams& S) { return S.ion_Z; }
   __device__ static __forceinline__ double kappa(const SysParams& S) { return S.kappa; }
+  __device__ static __forceinline__ double alpha(const SysParams& S) { return S.ew_alpha; }
 };
 template <> struct Cst<float> {
   __device__ static __forceinline__ float knot(const SysParams& S, int f, int m) { return S.jpf[f][m]; }
@@ -125,6 +126,7 @@ template <> struct Cst<float> {
   __device__ static __forceinline__ float invd(const SysParams& S, int d) { return S.inv_deltaf[d]; }
   __device__ static __forceinline__ float Z(const SysParams& S) { return S.ion_Zf; }
   __device__ static __forceinline__ float kappa(const SysParams& S) { return S.kappaf; }
+  __device__ static __forceinline__ float alpha(const SysParams& S) { return S.ew_alphaf; }
 };
 
 template <class T>
@@ -281,6 +283,8 @@ __device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_w(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float exp_w(float x) { return __expf(x); }
 __device__ __forceinline__ double exp_w(double x) { return exp(x); }
+__device__ __forceinline__ float erfc_w(float x) { return erfcf(x); }
+__device__ __forceinline__ double erfc_w(double x) { return erfc(x); }
 
 // Yukawa pair potential exp(-kappa r)/r for r < L/2 (stand-in for v_ee, v_eI).
 template <class T>

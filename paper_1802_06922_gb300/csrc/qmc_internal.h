@@ -9,6 +9,7 @@ namespace qmcgb {
 
 constexpr int kMaxKnots = 32;       // largest Jastrow M
 constexpr int kMaxNlChannels = 4;   // non-local pseudopotential channels l = 0..3
+constexpr int kEwMaxK = 65536;      // largest half set of Ewald k vectors
 constexpr size_t kMaxDynSmem = 227 * 1024;   // largest dynamic shared memory of one block (sm_103a)
 constexpr int kMaxDelay = 64;       // largest delay rank k
 constexpr int kThreads = 256;
@@ -51,6 +52,15 @@ struct SysParams {
   // non-local pseudopotential: channels dv_l(r) = nl_amp[l] exp(-(r / nl_width[l])^2), r < nl_rcut
   int nl_nch;          // 0: none
   double nl_amp[kMaxNlChannels], nl_width[kMaxNlChannels], nl_rcut;
+  // Coulomb interactions by Ewald summation in place of the Yukawa form (ew_on = 1)
+  int ew_on;
+  int ew_nk;               // k vectors in the half set
+  double ew_alpha;         // splitting parameter (1/bohr)
+  float ew_alphaf;
+  const int4* ew_n;        // device [ew_nk] integer vectors n, k = 2 pi n / L (w unused)
+  const double* ew_ck;     // device [ew_nk] (4 pi / Omega) exp(-k^2 / (4 alpha^2)) / k^2
+  const double* ew_rho_ion;// device [2][ew_nk] Z sum_I cos(k.R_I), Z sum_I sin(k.R_I)
+  const double* ew_const;  // device [1] ion-ion real-space, self and background terms
   uint32_t seed_lo, seed_hi;
 };
 

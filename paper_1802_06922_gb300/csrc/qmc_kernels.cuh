@@ -1387,7 +1387,9 @@ __global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams
 // Local energy (Sec. "Hamiltonian", E_L = Psi^-1 H Psi) and ln|Psi| of every walker.
 // Per electron i, with g_D = grad phi(r_i) . Binv[i] and l_D = lap phi(r_i) . Binv[i]:
 //   T_i = -1/2 [ l_D - |g_D|^2 + lap_i J + |g_D + grad_i J|^2 ],
-//   V = sum_{i<j} v(r_ij) - Z sum_{i,I} v(r_iI) + Z^2 sum_{I<J} v(R_IJ).
+//   V = sum_{i<j} v(r_ij) - Z sum_{i,I} v(r_iI) + Z^2 sum_{I<J} v(R_IJ),
+// v the Yukawa form, or with Ewald summation the real-space part erfc(alpha r) / r over the
+// nearest image of every pair (the reciprocal-space part is a kernel of its own).
 // One block per walker, one warp per electron; per-electron terms summed in FP64.
 // =============================================================================
 template <class TW>
@@ -1404,6 +1406,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
   for (int i = threadIdx.x; i < 3 * n_e; i += blockDim.x) posw[i] = (TW)P[i];
   __syncthreads();
   const TW Lw = Cst<TW>::L(S), iLw = Cst<TW>::invL(S), kap = Cst<TW>::kappa(S), Zw = Cst<TW>::Z(S);
+  const TW alw = Cst<TW>::alpha(S);
+  const bool ewald = S.ew_on != 0;
   const TW hL2 = TW(0.25) * Lw * Lw;
   const TW* ionw = Cst<TW>::ions(S);
   const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
@@ -1450,8 +1454,9 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
         for (int c = 0; c < 3; ++c) dd[c] = min_image<TW>(ri[c] - q[c], Lw, iLw);
         const TW r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
         const bool once = (j >= n_e) || (j > i);
-        // pairs beyond both cutoffs (Jastrow r_c, potential L/2) contribute nothing
-        const bool in_v = S.with_potential && once && r2 < hL2;
+        // pairs beyond both cutoffs (Jastrow r_c, Yukawa L/2) contribute nothing; the Ewald
+        // real-space part takes every pair
+        const bool in_v = S.with_potential && once && (ewald || r2 < hL2);
         const bool in_j = jt.M[f] != 0 && r2 < jt.rc2[f];
         if (!(in_v || in_j) || !(r2 > TW(0))) continue;
         const TW rinv = rsqrt_w(r2), r0 = r2 * rinv;
@@ -1459,7 +1464,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
         // ulp that the J value (a sum of ~10^5 pair terms) would accumulate
         const TW r = fma(TW(0.5) * fma(-r0, r0, r2), rinv, r0);
         if (in_v) {
-          const TW y = exp_w(-kap * r) * rinv;        // Yukawa e^{-kappa r} / r
+          // Yukawa e^{-kappa r} / r, or the Ewald real-space term erfc(alpha r) / r
+          const TW y = (ewald ? erfc_w(alw * r) : exp_w(-kap * r)) * rinv;
           pv += (j < n_e) ? y : -Zw * y;
         }
         if (!in_j) continue;
@@ -1499,7 +1505,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
   if (threadIdx.x == 0) {
     double k = 0, p = 0, j = 0;
     for (int q = 0; q < nw; ++q) { k += part[3 * q]; p += part[3 * q + 1]; j += part[3 * q + 2]; }
-    const double vii = S.with_potential ? S.v_ion_ion : 0.0;
+    const double vii = !S.with_potential ? 0.0 : ewald ? *S.ew_const : S.v_ion_ion;
     Wk.e_loc[w] = k + p + vii;
     Wk.log_psi[w] = Wk.logdet[2 * w] + Wk.logdet[2 * w + 1] + j;
   }

@@ -5,6 +5,7 @@
 #include "qmc_dmc.cuh"
 #include "qmc_sweep_win.cuh"
 #include "qmc_logdet.cuh"
+#include "qmc_ewald.cuh"
 
 namespace qmcgb {
 namespace {
@@ -161,18 +162,29 @@ cudaError_t dmc_copy(const SysParams& S, const WalkParams& src, const WalkParams
   return cudaGetLastError();
 }
 
+template <class TW>
+cudaError_t ewald_recip(const SysParams& S, const WalkParams& W, cudaStream_t st) {
+  if (!S.ew_on || S.ew_nk == 0) return cudaSuccess;
+  const size_t smem = ewald_smem_bytes(S.n_e, sizeof(TW));
+  cudaError_t e = cudaFuncSetAttribute(k_ewald_recip<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_ewald_recip<TW><<<W.n_w, kEwThreads, smem, st>>>(S, W);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const TwLaunch& tw_launch_f64() {
   static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
                           sweep_smem<double>, invert_batch<double>, flush<double>,
-                          refine<double>, logdet_anchor<double>, dmc_branch, dmc_copy<double>};
+                          refine<double>, logdet_anchor<double>, dmc_branch, dmc_copy<double>,
+                          ewald_recip<double>};
   return L;
 }
 const TwLaunch& tw_launch_f32() {
   static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
                           sweep_smem<float>, invert_batch<float>, flush<float>, refine<float>,
-                          logdet_anchor<float>, dmc_branch, dmc_copy<float>};
+                          logdet_anchor<float>, dmc_branch, dmc_copy<float>, ewald_recip<float>};
   return L;
 }
 
@@ -186,6 +198,16 @@ cudaError_t launch_proposals(const SysParams& S, const WalkParams& W, uint32_t t
 
 cudaError_t launch_accumulate(const WalkParams& W, double* out, long long* nacc, cudaStream_t st) {
   k_accumulate<<<1, 256, 0, st>>>(W, out, nacc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ewald_setup(const SysParams& S, double* ck, double* rho, double* cst, cudaStream_t st) {
+  if (S.ew_nk > 0) {
+    k_ewald_kspace_setup<<<(S.ew_nk + 255) / 256, 256, 0, st>>>(S, ck, rho);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_ewald_constant<<<1, 256, 0, st>>>(S, cst);
   return cudaGetLastError();
 }
 

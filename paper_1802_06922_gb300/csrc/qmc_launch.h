@@ -28,6 +28,8 @@ struct TwLaunch {
                             uint32_t step, cudaStream_t);
   cudaError_t (*dmc_copy)(const SysParams&, const WalkParams& src, const WalkParams& dst,
                           const DmcParams&, int parity, cudaStream_t);
+  // Ewald reciprocal-space energy of every walker, added to E_L
+  cudaError_t (*ewald_recip)(const SysParams&, const WalkParams&, cudaStream_t);
 };
 const TwLaunch& tw_launch_f64();
 const TwLaunch& tw_launch_f32();
@@ -53,6 +55,8 @@ const TtLaunch& tt_launch_bf16();
 cudaError_t launch_proposals(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
                              void* prop, cudaStream_t);
 cudaError_t launch_accumulate(const WalkParams&, double* out, long long* nacc, cudaStream_t);
+// Ewald setup from the ions: c_k, the ions' rho_k and the constant terms (FP64).
+cudaError_t launch_ewald_setup(const SysParams&, double* ck, double* rho, double* cst, cudaStream_t);
 
 // Records the message returned by qmc_last_error on this thread; returns s.
 int set_last_error(int s, const char* msg);

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA"
                 -4: "QMC_ESINGULAR", -5: "QMC_ETIMEOUT", -6: "QMC_ESTATE"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 KERNEL_CLASSES = ("propose", "vgl", "sweep", "energy", "reinvert", "vgl_current",
-                  "accumulate", "flush", "refine", "refine_update", "logdet", "nlpp")
+                  "accumulate", "flush", "refine", "refine_update", "logdet", "nlpp", "ewald")
 MOVES = {"metropolis": 0, "drift": 1}
 
 # Exported symbols and their ctypes signatures (argtypes, restype), as declared in
@@ -42,6 +42,8 @@ SIGNATURES = {
     "qmc_system_set_spline": ([_vp, _i, _i, _i, _i, _vp], _i),
     "qmc_system_set_jastrow": ([_vp, _i, _i, _d, _vp, _i, _d], _i),
     "qmc_system_set_nonlocal": ([_vp, _i, _vp, _vp, _d], _i),
+    "qmc_system_set_ewald": ([_vp, _d, _d], _i),
+    "qmc_system_ewald_count": ([_vp], _i),
     "qmc_get_nonlocal": ([_vp, _vp], _i),
     "qmc_walkers_create": ([_vp, _i, _vp, C.POINTER(_vp)], _i),
     "qmc_sweep": ([_vp, _i, _vp], _i),
@@ -164,6 +166,16 @@ class System:
         b = np.ascontiguousarray(width, dtype=np.float64)
         _check(load().qmc_system_set_nonlocal(self.h, int(a.size), a.ctypes.data if a.size else None,
                                               b.ctypes.data if b.size else None, float(rcut)))
+
+    def set_ewald(self, alpha: float, kcut: float = 0.0):
+        """Coulomb interactions by Ewald summation with splitting parameter alpha and
+        reciprocal cutoff kcut (alpha = 0 restores the Yukawa form)."""
+        _check(load().qmc_system_set_ewald(self.h, float(alpha), float(kcut)))
+
+    @property
+    def ewald_count(self) -> int:
+        """k vectors in the Ewald half set, -1 with the Yukawa form."""
+        return int(load().qmc_system_ewald_count(self.h))
 
     def close(self):
         if getattr(self, "h", None):
