@@ -17,7 +17,9 @@
  *       use drift-diffusion proposals (Eq. pmc:driftdiffusion_step), the fixed-node
  *       rule, weights (Eq. pmc:walker_weight) and branching (Sec. "Diffusion Monte Carlo");
  *     - the local energy E_L = Psi^-1 H Psi (Sec. "Hamiltonian") is kinetic plus a
- *       short-range Yukawa potential standing in for the Coulomb terms.
+ *       short-range Yukawa potential standing in for the Coulomb terms, or the Coulomb
+ *       terms themselves by Ewald summation, plus optionally the non-local
+ *       pseudopotential's quadrature of virtual moves.
  *
  * Conventions for every call:
  *   - Units are Hartree atomic units; the cell is the cube [0, L)^3, periodic.
@@ -192,8 +194,10 @@ qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream);
 
 /* Local energy and ln|Psi| of every walker's current configuration
  * (E_L = Psi^-1 H Psi, Sec. "Hamiltonian"). e_local and log_psi: [n_walkers] doubles,
- * host or device (either may be NULL). Synchronises `stream` when an output is host
- * memory; reports deferred device errors. */
+ * host or device (either may be NULL). The values measured at the end of the last sweep are
+ * returned unless a qmc_system_set_jastrow, qmc_system_set_nonlocal or qmc_system_set_ewald
+ * call changed the system since, in which case the walkers are measured again. Synchronises
+ * `stream` when an output is host memory; reports deferred device errors. */
 qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_psi, void* stream);
 
 /* FP64 sums over walkers of the last measurement (Sec. "Variational Monte Carlo" and

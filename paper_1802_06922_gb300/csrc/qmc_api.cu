@@ -74,6 +74,7 @@ struct qmc_system_s {
   void* d_table = nullptr;
   double* d_ions = nullptr;
   float* d_ionsf = nullptr;
+  uint64_t ham_version = 0;    // bumped by every change of the Hamiltonian's terms
   int4* d_ew_n = nullptr;      // Ewald half set of integer k vectors
   double* d_ew = nullptr;      // c_k [n_k], the ions' rho_k [2][n_k], constant [1]
   bool has_spline = false;
@@ -97,7 +98,8 @@ struct qmc_walkers_s {
   uint8_t* d_forced = nullptr;
   int forced_sweeps = 0;
   int64_t launches = 0;
-  bool energy_valid = false;
+  bool energy_valid = false;   // e_loc / log_psi hold the current configuration's values
+  uint64_t energy_version = 0; // the system's Hamiltonian version they were measured with
   int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
   int since_anchor[2] = {0, 0};// proposed moves per spin since the last log-det anchor
   bool profiling = false;
@@ -288,6 +290,7 @@ extern "C" qmc_status qmc_system_set_jastrow(qmc_system_t s, int which, int M, d
     return fail(QMC_EINVAL, "rcut must be in (0, L/2]");
   if (cusp_set && M < 2) return fail(QMC_EINVAL, "a cusp needs M >= 2");
   SysParams& P = s->P;
+  ++s->ham_version;
   P.jM[which] = M;
   P.jrc[which] = rcut;
   P.jrcf[which] = (float)rcut;
@@ -303,6 +306,7 @@ extern "C" qmc_status qmc_system_set_nonlocal(qmc_system_t s, int n_channels, co
   if (n_channels < 0 || n_channels > kMaxNlChannels)
     return fail(QMC_EINVAL, "n_channels must be in [0, %d]", kMaxNlChannels);
   SysParams& P = s->P;
+  ++s->ham_version;
   if (n_channels == 0) {
     P.nl_nch = 0;
     return QMC_OK;
@@ -324,6 +328,7 @@ extern "C" qmc_status qmc_system_set_ewald(qmc_system_t s, double alpha, double 
   if (!s) return fail(QMC_EINVAL, "qmc_system_set_ewald: NULL system");
   if (!std::isfinite(alpha) || alpha < 0.0) return fail(QMC_EINVAL, "alpha must be finite and >= 0");
   SysParams& P = s->P;
+  ++s->ham_version;
   if (alpha == 0.0) {
     P.ew_on = 0;
     return QMC_OK;
@@ -426,6 +431,7 @@ qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   w->since_moves[0] = w->since_moves[1] = 0;
   w->since_anchor[0] = w->since_anchor[1] = 0;
   w->energy_valid = true;
+  w->energy_version = s->ham_version;
   return check_err(w, st);
 }
 
@@ -684,16 +690,18 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
     w->forced_sweeps = 0;
   }
   w->energy_valid = true;
+  w->energy_version = w->sys->ham_version;
   return QMC_OK;
 }
 
 extern "C" qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_psi, void* stream) {
   if (!w) return fail(QMC_EINVAL, "qmc_measure: NULL walkers");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!w->energy_valid) {
+  if (!w->energy_valid || w->energy_version != w->sys->ham_version) {
     qmc_status r = measure_energy(w, w->W, w->sweep, st);
     if (r != QMC_OK) return r;
     w->energy_valid = true;
+    w->energy_version = w->sys->ham_version;
   }
   const size_t b = sizeof(double) * w->W.n_w;
   if (e_local) QMC_CUDA(cudaMemcpyAsync(e_local, w->W.e_loc, b, cudaMemcpyDefault, st));

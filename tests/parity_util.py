@@ -110,3 +110,31 @@ def assert_logpsi(gpu_lp, ref_lp, n_e, label="", extra=0.0):
     tol = logpsi_tol(n_e) + extra
     print(f"{label}: ln|Psi| error max {err.max():.2e} (gate {tol:.2e})")
     assert err.max() <= tol, (label, float(err.max()), tol)
+
+
+# Single-precision local energy, per walker: max(1e-5 Ha per electron, 2^-24 cond K), where
+# K = sum_i [ sum_j |lap phi_j(r_i) Ainv[j][i]| + 2 |grad_i ln D| sum_j |grad phi_j(r_i)| |Ainv[j][i]| ]
+# is the sum of the magnitudes of the kinetic energy's determinant terms and cond the larger
+# 2-norm condition number of the two Slater matrices: to first order the dot products add
+# about 2^-24 of K, and an inverse carried to a relative error of about cond 2^-24 adds
+# cond 2^-24 of K.
+EL_PER_E = 1e-5
+
+
+def el_gate(wf, R) -> float:
+    R = np.asarray(R, dtype=np.float64)
+    kmag, cond = 0.0, 1.0
+    inv = {}
+    for sp in (0, 1):
+        ns = wf.n_up if sp == 0 else wf.n_dn
+        if ns:
+            A = wf.slater_matrix(R, sp)
+            inv[sp] = np.linalg.inv(A)
+            cond = max(cond, float(np.linalg.cond(A)))
+    for i in range(R.shape[0]):
+        spin, first, ns = wf.block(i)
+        _, grad, lap = wf.orb.vgl(R[i])
+        col = inv[spin][:, i - first]
+        g = grad[:, :ns] @ col
+        kmag += float(np.abs(lap[:ns] * col).sum() + 2.0 * np.linalg.norm(g) * np.abs(grad[:, :ns] * col).sum())
+    return max(EL_PER_E * R.shape[0], 2.0 ** -24 * cond * kmag)
