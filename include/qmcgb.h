@@ -12,7 +12,8 @@
  *       accepted move updates A^-1 by Sherman-Morrison or by the delayed rank-k scheme
  *       (Sec. "Multi-Determinant Slater-Jastrow Form");
  *     - J holds one- and two-body terms built from 1D cubic B-spline radial functors
- *       with minimum-image distances (Sec. "Jastrow factor");
+ *       with minimum-image distances, and optionally the three-body e-e-I polynomial
+ *       term (Sec. "Jastrow factor");
  *     - a move is accepted with min(1, |Psi'/Psi|^2 T'/T) (Eq. accept_reject); DMC steps
  *       use drift-diffusion proposals (Eq. pmc:driftdiffusion_step), the fixed-node
  *       rule, weights (Eq. pmc:walker_weight) and branching (Sec. "Diffusion Monte Carlo");
@@ -152,6 +153,22 @@ qmc_status qmc_system_set_jastrow(qmc_system_t sys, int which, int M, double rcu
 qmc_status qmc_system_set_nonlocal(qmc_system_t sys, int n_channels, const double* amp,
                                    const double* width, double rcut);
 
+/* Three-body electron-electron-ion Jastrow factor added to J (Sec. "Jastrow factor": the
+ * correlation function of Drummond et al.). For electrons i < j and every ion I, with
+ * a = r_iI, b = r_jI, c = r_ij (minimum image) and h = rcut / 2:
+ *   u(a, b, c) = sum_{l,m=0}^{m_ei} sum_{n=0}^{m_ee} gamma_lmn a^l b^m c^n (a - h)^3 (b - h)^3
+ * when a < h and b < h, else 0; J3 = sum_I sum_{i<j} u. gamma_same applies to same-spin
+ * pairs, gamma_opp to opposite-spin pairs; each is host [m_ei+1][m_ei+1][m_ee+1] (index
+ * (l (m_ei+1) + m) (m_ee+1) + n), copied, and must satisfy gamma_lmn = gamma_mln. Moves
+ * (Metropolis, drift, the windowed delayed update), E_L, ln|Psi| and the pseudopotential's
+ * virtual moves all include the term. At most 8 ions may lie within h of the two positions
+ * of one move of the windowed delayed update (else the next synchronising call fails with
+ * QMC_ECUDA). m_ei < 0 removes the term. Synchronous; no other call may use the system
+ * meanwhile. QMC_EINVAL for orders above 4, rcut outside (0, L/2], a coefficient that is
+ * not finite or a set that is not symmetric in l and m. */
+qmc_status qmc_system_set_jastrow3(qmc_system_t sys, int m_ei, int m_ee, double rcut,
+                                   const double* gamma_same, const double* gamma_opp);
+
 /* Coulomb interactions by Ewald summation in place of the Yukawa form (Sec. "Hamiltonian":
  * v_ee = 1/r, v_eI = -Z/r and v_II = Z^2/r summed over every periodic image of the cell,
  * evaluated with the Ewald technique; Sec. "Long-Range Interactions": short-ranged terms
@@ -195,8 +212,9 @@ qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream);
 /* Local energy and ln|Psi| of every walker's current configuration
  * (E_L = Psi^-1 H Psi, Sec. "Hamiltonian"). e_local and log_psi: [n_walkers] doubles,
  * host or device (either may be NULL). The values measured at the end of the last sweep are
- * returned unless a qmc_system_set_jastrow, qmc_system_set_nonlocal or qmc_system_set_ewald
- * call changed the system since, in which case the walkers are measured again. Synchronises
+ * returned unless a qmc_system_set_jastrow, qmc_system_set_jastrow3, qmc_system_set_nonlocal
+ * or qmc_system_set_ewald call changed the system since, in which case the walkers are
+ * measured again. Synchronises
  * `stream` when an output is host memory; reports deferred device errors. */
 qmc_status qmc_measure(qmc_walkers_t w, double* e_local, double* log_psi, void* stream);
 
@@ -372,7 +390,8 @@ typedef enum {
   QMC_K_LOGDET = 10,      /* log-determinant anchor (error-free FP32 LU) */
   QMC_K_NLPP = 11,        /* non-local pseudopotential quadrature (pairs and virtual moves) */
   QMC_K_EWALD = 12,       /* Ewald reciprocal-space energy (structure factors) */
-  QMC_NKERNELS = 13
+  QMC_K_JASTROW3 = 13,    /* three-body Jastrow gradient, Laplacian and value per electron */
+  QMC_NKERNELS = 14
 } qmc_kernel;
 
 /* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA

@@ -106,15 +106,13 @@ class ThreeBodyJastrow:
 
     def value(self, R):
         R = np.asarray(R, dtype=np.float64)
-        n = R.shape[0]
         J = 0.0
         for I in range(self.ions.shape[0]):
             dI = _min_image(R - self.ions[I], self.L)
             rI = np.sqrt((dI * dI).sum(-1))
-            for i in range(n):
-                for j in range(i + 1, n):
-                    if rI[i] >= self.h or rI[j] >= self.h:
-                        continue
+            inside = np.flatnonzero(rI < self.h)       # only these electrons have u != 0
+            for x, i in enumerate(inside):
+                for j in inside[x + 1:]:
                     d = _min_image(R[i] - R[j], self.L)
                     c = np.sqrt(d @ d)
                     J += float(u3_derivs(rI[i], rI[j], c, self._set(i, j), self.h)[0])
@@ -123,7 +121,6 @@ class ThreeBodyJastrow:
     def grad_lap(self, R, i):
         """grad_i J3 (3,) and lap_i J3 for electron i."""
         R = np.asarray(R, dtype=np.float64)
-        n = R.shape[0]
         g = np.zeros(3)
         lap = 0.0
         for I in range(self.ions.shape[0]):
@@ -131,13 +128,12 @@ class ThreeBodyJastrow:
             a = np.sqrt(da @ da)
             if a >= self.h:
                 continue
-            for j in range(n):
+            dI = _min_image(R - self.ions[I], self.L)
+            rI = np.sqrt((dI * dI).sum(-1))
+            for j in np.flatnonzero(rI < self.h):     # only these electrons have u != 0
                 if j == i:
                     continue
-                db = _min_image(R[j] - self.ions[I], self.L)
-                b = np.sqrt(db @ db)
-                if b >= self.h:
-                    continue
+                b = rI[j]
                 dc = _min_image(R[i] - R[j], self.L)
                 c = np.sqrt(dc @ dc)
                 u, ua, uc, uaa, ucc, uac = (float(x) for x in

@@ -75,6 +75,7 @@ struct qmc_system_s {
   double* d_ions = nullptr;
   float* d_ionsf = nullptr;
   uint64_t ham_version = 0;    // bumped by every change of the Hamiltonian's terms
+  double* d_j3 = nullptr;      // three-body Jastrow coefficients [2][n_coef]
   int4* d_ew_n = nullptr;      // Ewald half set of integer k vectors
   double* d_ew = nullptr;      // c_k [n_k], the ions' rho_k [2][n_k], constant [1]
   bool has_spline = false;
@@ -100,6 +101,7 @@ struct qmc_walkers_s {
   int64_t launches = 0;
   bool energy_valid = false;   // e_loc / log_psi hold the current configuration's values
   uint64_t energy_version = 0; // the system's Hamiltonian version they were measured with
+  void* d_j3vgl = nullptr;     // three-body Jastrow terms per electron [W][n_e][5] (working precision)
   int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
   int since_anchor[2] = {0, 0};// proposed moves per spin since the last log-det anchor
   bool profiling = false;
@@ -324,6 +326,47 @@ extern "C" qmc_status qmc_system_set_nonlocal(qmc_system_t s, int n_channels, co
   return QMC_OK;
 }
 
+extern "C" qmc_status qmc_system_set_jastrow3(qmc_system_t s, int m_ei, int m_ee, double rcut,
+                                              const double* gamma_same, const double* gamma_opp) {
+  if (!s) return fail(QMC_EINVAL, "qmc_system_set_jastrow3: NULL system");
+  SysParams& P = s->P;
+  if (m_ei < 0) {
+    ++s->ham_version;
+    P.j3_on = 0;
+    return QMC_OK;
+  }
+  if (m_ei > kJ3MaxOrder || m_ee < 0 || m_ee > kJ3MaxOrder)
+    return fail(QMC_EINVAL, "the orders must lie in [0, %d]", kJ3MaxOrder);
+  if (!gamma_same || !gamma_opp) return fail(QMC_EINVAL, "qmc_system_set_jastrow3: NULL coefficients");
+  if (!(rcut > 0.0) || rcut > 0.5 * s->d.L * (1 + 1e-12)) return fail(QMC_EINVAL, "rcut must be in (0, L/2]");
+  const int n1 = m_ei + 1, n3 = m_ee + 1, nc = n1 * n1 * n3;
+  const double* g[2] = {gamma_same, gamma_opp};
+  for (int f = 0; f < 2; ++f)
+    for (int l = 0; l < n1; ++l)
+      for (int m = 0; m < n1; ++m)
+        for (int n = 0; n < n3; ++n) {
+          const double a = g[f][(l * n1 + m) * n3 + n], b = g[f][(m * n1 + l) * n3 + n];
+          if (!std::isfinite(a)) return fail(QMC_EINVAL, "a coefficient is not finite");
+          if (a != b) return fail(QMC_EINVAL, "gamma_lmn must equal gamma_mln");
+        }
+  std::vector<double> h(2 * (size_t)nc);
+  std::copy(gamma_same, gamma_same + nc, h.begin());
+  std::copy(gamma_opp, gamma_opp + nc, h.begin() + nc);
+  QMC_CUDA(cudaDeviceSynchronize());     // no kernel may still read the previous coefficients
+  ++s->ham_version;
+  P.j3_on = 0;
+  cudaFree(s->d_j3);
+  s->d_j3 = nullptr;
+  QMC_CUDA(cudaMalloc(&s->d_j3, sizeof(double) * h.size()));
+  QMC_CUDA(cudaMemcpy(s->d_j3, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+  P.j3_g = s->d_j3;
+  P.j3_meI = m_ei;
+  P.j3_mee = m_ee;
+  P.j3_h = 0.5 * rcut;
+  P.j3_on = 1;
+  return QMC_OK;
+}
+
 extern "C" qmc_status qmc_system_set_ewald(qmc_system_t s, double alpha, double kcut) {
   if (!s) return fail(QMC_EINVAL, "qmc_system_set_ewald: NULL system");
   if (!std::isfinite(alpha) || alpha < 0.0) return fail(QMC_EINVAL, "alpha must be finite and >= 0");
@@ -378,6 +421,7 @@ extern "C" int qmc_system_ewald_count(qmc_system_t s) { return (s && s->P.ew_on)
 
 extern "C" void qmc_system_destroy(qmc_system_t s) {
   if (!s) return;
+  cudaFree(s->d_j3);
   cudaFree(s->d_ew_n);
   cudaFree(s->d_ew);
   cudaFree(s->d_table);
@@ -397,6 +441,9 @@ qmc_status check_err(qmc_walkers_s* w, cudaStream_t st) {
     QMC_CUDA(cudaMemset(w->W.err, 0, sizeof(int)));
     if (err & kErrSingular) return fail(QMC_ESINGULAR, "a Slater matrix was singular at (re-)inversion");
     if (err & kErrTimeout) return fail(QMC_ETIMEOUT, "a bounded device wait timed out");
+    if (err & kErrJ3Near)
+      return fail(QMC_ECUDA, "more than %d ions within r_c / 2 of a move of the three-body Jastrow "
+                             "factor", kJ3MaxNear);
     if (err & kErrOverflow)
       return fail(QMC_ECUDA, "more electron-ion pairs inside the pseudopotential cutoff than the "
                              "per-walker list holds (2 per electron)");
@@ -407,8 +454,15 @@ qmc_status check_err(qmc_walkers_s* w, cudaStream_t st) {
 
 // Local energy (and ln|Psi|) of every walker: kinetic + local potential, then the non-local
 // pseudopotential part when the system has one; t seeds the quadrature's rotation.
-qmc_status measure_energy(qmc_walkers_s* w, const WalkParams& W, uint32_t t, cudaStream_t st) {
+qmc_status measure_energy(qmc_walkers_s* w, const WalkParams& W0, uint32_t t, cudaStream_t st) {
   qmc_system_s* s = w->sys;
+  WalkParams W = W0;
+  W.j3vgl = nullptr;
+  if (s->P.j3_on && s->P.n_ion > 0) {
+    W.j3vgl = w->d_j3vgl;
+    Bracket b(w, st, QMC_K_JASTROW3);
+    QMC_CUDA(s->tw->j3_vgl(s->P, W, st));
+  }
   { Bracket b(w, st, QMC_K_ENERGY); QMC_CUDA(s->tw->local_energy(s->P, W, st)); }
   if (s->P.ew_on && s->P.ew_nk > 0) {
     Bracket b(w, st, QMC_K_EWALD);
@@ -441,7 +495,7 @@ void free_walkers(qmc_walkers_s* w) {
                   W.sgn, W.wid, W.weight, W.e_loc, W.log_psi, W.n_acc, W.acc_since, W.scratch64,
                   W.err, w->d_P, w->d_prop, w->d_out, w->d_nacc, w->d_forced, W.win_phi,
                   W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
-                  W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count};
+                  W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count, w->d_j3vgl};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -522,6 +576,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.nl_pairs, nw * (size_t)std::max(64, 2 * (int)ne) * sizeof(int)},
       {(void**)&W.nl_count, nw * sizeof(int)},
       {(void**)&W.rscale, nw * 4 * (size_t)W.ld_v * sizeof(int)},
+      {(void**)&w->d_j3vgl, nw * (size_t)ne * 5 * tw},
   };
   for (auto& a : allocs) {
     *a.p = nullptr;

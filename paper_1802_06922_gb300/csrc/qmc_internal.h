@@ -10,6 +10,9 @@ namespace qmcgb {
 constexpr int kMaxKnots = 32;       // largest Jastrow M
 constexpr int kMaxNlChannels = 4;   // non-local pseudopotential channels l = 0..3
 constexpr int kEwMaxK = 65536;      // largest half set of Ewald k vectors
+constexpr int kJ3MaxOrder = 4;      // largest polynomial order of the three-body Jastrow
+constexpr int kJ3MaxCoef = (kJ3MaxOrder + 1) * (kJ3MaxOrder + 1) * (kJ3MaxOrder + 1);
+constexpr int kJ3MaxNear = 8;       // ions within r_c / 2 of a move's two positions
 constexpr size_t kMaxDynSmem = 227 * 1024;   // largest dynamic shared memory of one block (sm_103a)
 constexpr int kMaxDelay = 64;       // largest delay rank k
 constexpr int kThreads = 256;
@@ -21,7 +24,7 @@ struct alignas(32) Prop {
 };
 
 // Device error flags (bitwise OR into WalkParams::err).
-enum : int { kErrSingular = 1, kErrNonFinite = 2, kErrTimeout = 4, kErrOverflow = 8 };
+enum : int { kErrSingular = 1, kErrNonFinite = 2, kErrTimeout = 4, kErrOverflow = 8, kErrJ3Near = 16 };
 
 // Read-only description of a system, passed to kernels by value.
 struct SysParams {
@@ -52,6 +55,11 @@ struct SysParams {
   // non-local pseudopotential: channels dv_l(r) = nl_amp[l] exp(-(r / nl_width[l])^2), r < nl_rcut
   int nl_nch;          // 0: none
   double nl_amp[kMaxNlChannels], nl_width[kMaxNlChannels], nl_rcut;
+  // three-body e-e-I Jastrow (j3_on = 1): orders M_eI, M_ee, h = r_c / 2, coefficients
+  // [2][M_eI + 1][M_eI + 1][M_ee + 1] (same-spin set, opposite-spin set)
+  int j3_on, j3_meI, j3_mee;
+  double j3_h;
+  const double* j3_g;      // device
   // Coulomb interactions by Ewald summation in place of the Yukawa form (ew_on = 1)
   int ew_on;
   int ew_nk;               // k vectors in the half set
@@ -105,6 +113,8 @@ struct WalkParams {
   int* nl_pairs;       // [W][nl_cap] electron * n_ion + ion of the pairs inside the cutoff
   int* nl_count;       // [W]
   int nl_cap;
+  void* j3vgl;         // working precision [W][n_e][5]: grad_i J3, lap_i J3 and electron i's
+                       // share of J3 for the next local energy; nullptr without that term
 };
 
 // Inverse of walker w's spin block: Binv[e][j] = (A^-1)[j][e], N_s x N_s, row-major.

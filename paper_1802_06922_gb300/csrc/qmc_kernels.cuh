@@ -8,6 +8,7 @@
 // re-inversion.
 #pragma once
 #include "qmc_device.cuh"
+#include "qmc_jastrow3.cuh"
 #include "tc_sm100.cuh"
 
 namespace qmcgb {
@@ -752,6 +753,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   const int n_e = S.n_e, ld_v = Wk.ld_v, kcp = kc + 1;
   SweepSmem<TW> sm = carve<TW>(smem_s, n_e, ld_v, kc, nw, !ext_flush);
   jastrow_tab_fill<TW>(S, jt);
+  __shared__ J3Tab<TW> j3t;
+  j3_tab_fill<TW>(S, j3t);
   const int spin = e0 >= S.n_up ? 1 : 0;
   const int first = spin ? S.n_up : 0;
   const int ns = spin ? S.n_dn : S.n_up;
@@ -1016,11 +1019,24 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
                         (TW)sm.propb[4 * cur + 2]};
       acc[5] = jastrow_delta_value<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, jtid, jnt);
       acc[6] = 0; acc[7] = 0; acc[8] = 0;
+      if (j3t.on) {
+        const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+        TW g3[3];
+        acc[5] += j3_delta<TW, false>(S, j3t, sm.posw, ionw, e, ro, rn, Lw, iLw,
+                                      j3_group_warps(jtid, jnt), g3);
+      }
     } else {
       const TW rn[3] = {(TW)sm.propb[4 * cur], (TW)sm.propb[4 * cur + 1],
                         (TW)sm.propb[4 * cur + 2]};
       TW g[3];
       acc[5] = jastrow_delta_grad<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, jtid, jnt, g);
+      if (j3t.on) {
+        const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+        TW g3[3];
+        acc[5] += j3_delta<TW, true>(S, j3t, sm.posw, ionw, e, ro, rn, Lw, iLw,
+                                     j3_group_warps(jtid, jnt), g3);
+        g[0] += g3[0]; g[1] += g3[1]; g[2] += g3[2];
+      }
       acc[6] = g[0]; acc[7] = g[1]; acc[8] = g[2];
     }
     // block sums; warp partials added by thread 0 in working precision, R and a compensated
@@ -1489,10 +1505,18 @@ __global__ void __launch_bounds__(kEnergyThreads) k_local_energy(SysParams S, Wa
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) jsum += __shfl_xor_sync(0xffffffffu, jsum, o);
     if (lane == 0) {
+      double j3[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // three-body Jastrow terms of electron i
+      if (Wk.j3vgl) {
+        const TW* q3 = static_cast<const TW*>(Wk.j3vgl) + ((size_t)w * n_e + i) * 5;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) j3[k] = (double)q3[k];
+      }
       const double g0 = s[0], g1 = s[1], g2 = s[2];
       const double lapD = (double)s[3] - (g0 * g0 + g1 * g1 + g2 * g2);
-      const double gx = g0 + (double)s[4], gy = g1 + (double)s[5], gz = g2 + (double)s[6];
-      kin += -0.5 * (lapD + (double)s[7] + gx * gx + gy * gy + gz * gz);
+      const double gx = g0 + (double)s[4] + j3[0], gy = g1 + (double)s[5] + j3[1],
+                   gz = g2 + (double)s[6] + j3[2];
+      kin += -0.5 * (lapD + (double)s[7] + j3[3] + gx * gx + gy * gy + gz * gz);
+      jsum += j3[4];
       pot += (double)s[8];
       jas += jsum;
     }

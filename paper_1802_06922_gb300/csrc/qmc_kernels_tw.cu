@@ -172,19 +172,29 @@ cudaError_t ewald_recip(const SysParams& S, const WalkParams& W, cudaStream_t st
   return cudaGetLastError();
 }
 
+template <class TW>
+cudaError_t j3_vgl(const SysParams& S, const WalkParams& W, cudaStream_t st) {
+  const size_t smem = j3_smem_bytes(S.n_e, sizeof(TW));
+  cudaError_t e = cudaFuncSetAttribute(k_j3_vgl<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_j3_vgl<TW><<<W.n_w, kJ3Threads, smem, st>>>(S, W);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 const TwLaunch& tw_launch_f64() {
   static const TwLaunch L{sizeof(double), reinvert<double>, sweep<double>, local_energy<double>,
                           sweep_smem<double>, invert_batch<double>, flush<double>,
                           refine<double>, logdet_anchor<double>, dmc_branch, dmc_copy<double>,
-                          ewald_recip<double>};
+                          ewald_recip<double>, j3_vgl<double>};
   return L;
 }
 const TwLaunch& tw_launch_f32() {
   static const TwLaunch L{sizeof(float), reinvert<float>, sweep<float>, local_energy<float>,
                           sweep_smem<float>, invert_batch<float>, flush<float>, refine<float>,
-                          logdet_anchor<float>, dmc_branch, dmc_copy<float>, ewald_recip<float>};
+                          logdet_anchor<float>, dmc_branch, dmc_copy<float>, ewald_recip<float>,
+                          j3_vgl<float>};
   return L;
 }
 

@@ -30,6 +30,8 @@ struct TwLaunch {
                           const DmcParams&, int parity, cudaStream_t);
   // Ewald reciprocal-space energy of every walker, added to E_L
   cudaError_t (*ewald_recip)(const SysParams&, const WalkParams&, cudaStream_t);
+  // three-body Jastrow gradient, Laplacian and value of every electron into W.j3vgl
+  cudaError_t (*j3_vgl)(const SysParams&, const WalkParams&, cudaStream_t);
 };
 const TwLaunch& tw_launch_f64();
 const TwLaunch& tw_launch_f32();

@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(256, 2) k_nlpp_eval(SysParams S, WalkParams Wk
   using A = typename AccOf<TT>::type;
   constexpr int V = TabVec<TT>::V;
   __shared__ JastrowTab<TW> jt;
+  __shared__ J3Tab<TW> j3t;
   jastrow_tab_fill<TW>(S, jt);
+  j3_tab_fill<TW>(S, j3t);
   __syncthreads();
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -221,6 +223,10 @@ __global__ void __launch_bounds__(256, 2) k_nlpp_eval(SysParams S, WalkParams Wk
         do2 += ao * ao;
       }
       dj += jastrow_value_r2<TW>(jt, f, dn2) - jastrow_value_r2<TW>(jt, f, do2);
+    }
+    if (j3t.on) {
+      TW g3[3];
+      dj += j3_delta<TW, false>(S, j3t, P, ionw, e, xo, xn, Lw, iLw, j3_group_warps(lane, 32), g3);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dj += __shfl_xor_sync(0xffffffffu, dj, o);

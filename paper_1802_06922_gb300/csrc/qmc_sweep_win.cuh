@@ -119,6 +119,9 @@ __global__ void __launch_bounds__(kWinThreads, 2)
                 const Prop* __restrict__ prop, int p_e0, int p_n) {
   extern __shared__ __align__(16) char smem_w[];
   __shared__ JastrowTab<TW> jt;
+  __shared__ J3Tab<TW> j3t;
+  __shared__ int j3_near[kWinMaxK][kJ3MaxNear];   // three-body Jastrow: ions near each move
+  __shared__ int j3_nn[kWinMaxK];
   __shared__ __align__(8) uint64_t cp_bar[2];
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;            // empty DMC slot
@@ -146,6 +149,7 @@ __global__ void __launch_bounds__(kWinThreads, 2)
   }
   cp_async_commit();
   jastrow_tab_fill<TW>(S, jt);
+  j3_tab_fill<TW>(S, j3t);
   if (tid == kCopier) {
     tc::mbar_init(&cp_bar[0], 1);
     tc::mbar_init(&cp_bar[1], 1);
@@ -218,10 +222,24 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     if (t < kk) {
       const TW rn[3] = {sm.propw[4 * t], sm.propw[4 * t + 1], sm.propw[4 * t + 2]};
       v = jastrow_delta_value<TW>(S, jt, sm.posw, ionw, e0 + t, rn, Lw, iLw, gl, 8);
+      if (j3t.on) {
+        // the three-body term, with the list of ions near the move for the pair corrections
+        const int e = e0 + t;
+        const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+        TW g3[3];
+        int nn = 0;
+        v += j3_delta<TW, false>(S, j3t, sm.posw, ionw, e, ro, rn, Lw, iLw,
+                                 j3_group_sub(8, gl, 8), g3, j3_near[t], kJ3MaxNear, &nn);
+        if (gl == 0) {
+          j3_nn[t] = min(nn, kJ3MaxNear);
+          if (nn > kJ3MaxNear) atomicOr(Wk.err, kErrJ3Near);
+        }
+      }
     }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (t < kk && gl == 0) sm.jb[t] = v;
+    if (j3t.on) __syncthreads();                // the near-ion lists are complete
     for (int i = tid; i < kk * kk; i += nt) {
       const int ta = i / kk, tb = i - ta * kk;
       TW q = TW(0);
@@ -237,6 +255,13 @@ __global__ void __launch_bounds__(kWinThreads, 2)
         }
         q = (jastrow_value_r2<TW>(jt, 1, d2[0]) - jastrow_value_r2<TW>(jt, 1, d2[1])) -
             (jastrow_value_r2<TW>(jt, 1, d2[2]) - jastrow_value_r2<TW>(jt, 1, d2[3]));
+        if (j3t.on) {
+          const TW pa[3] = {sm.propw[4 * ta], sm.propw[4 * ta + 1], sm.propw[4 * ta + 2]};
+          const TW pb[3] = {sm.propw[4 * tb], sm.propw[4 * tb + 1], sm.propw[4 * tb + 2]};
+          const TW oa[3] = {sm.posw[e0 + ta], sm.posw[n_e + e0 + ta], sm.posw[2 * n_e + e0 + ta]};
+          const TW ob[3] = {sm.posw[e0 + tb], sm.posw[n_e + e0 + tb], sm.posw[2 * n_e + e0 + tb]};
+          q += j3_pair_correction<TW>(S, j3t, ionw, j3_near[ta], j3_nn[ta], pa, oa, pb, ob, Lw, iLw);
+        }
       }
       sm.Q[ta * kWinP + tb] = q;
     }
@@ -302,6 +327,13 @@ __global__ void __launch_bounds__(kWinThreads, 2)
         const TW rn[3] = {sm.propw[4 * t], sm.propw[4 * t + 1], sm.propw[4 * t + 2]};
         TW g[3];
         (void)jastrow_delta_grad<TW>(S, jt, sm.posw, ionw, e, rn, Lw, iLw, tid, jn, g);
+        if (j3t.on) {
+          const TW ro[3] = {sm.posw[e], sm.posw[n_e + e], sm.posw[2 * n_e + e]};
+          TW g3[3];
+          (void)j3_delta<TW, true>(S, j3t, sm.posw, ionw, e, ro, rn, Lw, iLw,
+                                   j3_group_warps(tid, jn), g3);
+          g[0] += g3[0]; g[1] += g3[1]; g[2] += g3[2];
+        }
         v[1] = g[0]; v[2] = g[1]; v[3] = g[2];
       }
     } else {

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA"
                 -4: "QMC_ESINGULAR", -5: "QMC_ETIMEOUT", -6: "QMC_ESTATE"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 KERNEL_CLASSES = ("propose", "vgl", "sweep", "energy", "reinvert", "vgl_current",
-                  "accumulate", "flush", "refine", "refine_update", "logdet", "nlpp", "ewald")
+                  "accumulate", "flush", "refine", "refine_update", "logdet", "nlpp", "ewald",
+                  "jastrow3")
 MOVES = {"metropolis": 0, "drift": 1}
 
 # Exported symbols and their ctypes signatures (argtypes, restype), as declared in
@@ -43,6 +44,7 @@ SIGNATURES = {
     "qmc_system_set_jastrow": ([_vp, _i, _i, _d, _vp, _i, _d], _i),
     "qmc_system_set_nonlocal": ([_vp, _i, _vp, _vp, _d], _i),
     "qmc_system_set_ewald": ([_vp, _d, _d], _i),
+    "qmc_system_set_jastrow3": ([_vp, _i, _i, _d, _vp, _vp], _i),
     "qmc_system_ewald_count": ([_vp], _i),
     "qmc_get_nonlocal": ([_vp, _vp], _i),
     "qmc_walkers_create": ([_vp, _i, _vp, C.POINTER(_vp)], _i),
@@ -166,6 +168,19 @@ class System:
         b = np.ascontiguousarray(width, dtype=np.float64)
         _check(load().qmc_system_set_nonlocal(self.h, int(a.size), a.ctypes.data if a.size else None,
                                               b.ctypes.data if b.size else None, float(rcut)))
+
+    def set_jastrow3(self, gamma_same, gamma_opp=None, rcut: float = 0.0):
+        """Three-body e-e-I Jastrow term with coefficient arrays [M_eI+1][M_eI+1][M_ee+1]
+        (gamma_opp defaults to gamma_same); None removes the term."""
+        if gamma_same is None:
+            _check(load().qmc_system_set_jastrow3(self.h, -1, 0, 0.0, None, None))
+            return
+        a = np.ascontiguousarray(gamma_same, dtype=np.float64)
+        b = np.ascontiguousarray(a if gamma_opp is None else gamma_opp, dtype=np.float64)
+        if a.ndim != 3 or a.shape[0] != a.shape[1] or b.shape != a.shape:
+            raise ValueError("gamma arrays must have shape (M_eI + 1, M_eI + 1, M_ee + 1)")
+        _check(load().qmc_system_set_jastrow3(self.h, a.shape[0] - 1, a.shape[2] - 1,
+                                              float(rcut), a.ctypes.data, b.ctypes.data))
 
     def set_ewald(self, alpha: float, kcut: float = 0.0):
         """Coulomb interactions by Ewald summation with splitting parameter alpha and

@@ -233,3 +233,21 @@ def build_inputs(spec: SystemSpec, seed: int = 0, n_walkers: Optional[int] = Non
 
 def _name_key(name: str) -> int:
     return int.from_bytes(name.encode()[:8].ljust(8, b"\0"), "little")
+
+
+def jastrow3_coefficients(m_ei: int, m_ee: int, rc: float, seed: int = 0):
+    """Coefficient sets (same spin, opposite spin) of the three-body e-e-I polynomial, each
+    [m_ei+1][m_ei+1][m_ee+1] and symmetric in its first two indices: gamma_lmn =
+    x_lmn * 0.05 / h^(6 + l + m + n) with h = rc / 2 and x ~ N(0, 1) symmetrised, so that every
+    term of the polynomial times the cutoff factors is of order 0.05 inside the sphere."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x4A33]))
+    h = 0.5 * rc
+    l = np.arange(m_ei + 1)[:, None, None]
+    m = np.arange(m_ei + 1)[None, :, None]
+    n = np.arange(m_ee + 1)[None, None, :]
+    scale = 0.05 / h ** (6 + l + m + n)
+    out = []
+    for _ in range(2):
+        x = rng.normal(0.0, 1.0, size=(m_ei + 1, m_ei + 1, m_ee + 1))
+        out.append(0.5 * (x + x.transpose(1, 0, 2)) * scale)
+    return out[0], out[1]

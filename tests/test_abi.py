@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     text = open(os.path.join(ROOT, "include", "qmcgb.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return set(re.findall(r"\b(qmc_[a-z_]+)\s*\(", text))
+    return set(re.findall(r"\b(qmc_[a-z0-9_]+)\s*\(", text))
 
 
 def test_every_declared_symbol_is_exported_and_bound():
