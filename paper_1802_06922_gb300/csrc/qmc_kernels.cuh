@@ -955,6 +955,12 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
           g[3] += gg * dq[0]; g[4] += gg * dq[1]; g[5] += gg * dq[2];
         }
       }
+      if (j3t.on) {   // the three-body term's gradient at r_e (its difference is zero here)
+        TW g3[3];
+        (void)j3_delta<TW, true>(S, j3t, sm.posw, ionw, e, ro, ro, Lw, iLw,
+                                 j3_group_warps(tid, nt), g3);
+        g[3] += g3[0]; g[4] += g3[1]; g[5] += g3[2];
+      }
       warp_sum<6, TW>(g);
       if (lane == 0)
 #pragma unroll
