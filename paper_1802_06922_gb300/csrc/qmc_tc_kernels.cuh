@@ -212,6 +212,23 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
       ul[off] = lo;
     }
   };
+  // U^T element i of chunk c (tile row jj = i mod 64, window row l = i / 64): its global value,
+  // and its hi/lo store into buffer c & 1. Loads are issued as a batch into registers one
+  // phase ahead of the stores, so their latency overlaps the MMA waits.
+  auto u_elem = [&](int c, int i) -> float {
+    const int l = i / kTcNChunk, j = c * kTcNChunk + i % kTcNChunk;
+    return (i < kTcNChunk * mx && l < m && j < ns) ? gu[(size_t)l * ld_v + j] : 0.f;
+  };
+  auto u_store = [&](int c, int i, float x) {
+    if (i >= kTcNChunk * mx) return;
+    float* uh = Ub + (size_t)(c & 1) * 2 * kTcNChunk * mx;
+    float hi, lo;
+    split_tf32(x, hi, lo);
+    const uint32_t off = tc::tile_offset(i % kTcNChunk, i / kTcNChunk, kz, 4) >> 2;
+    uh[off] = hi;
+    uh[kTcNChunk * mx + off] = lo;
+  };
+  constexpr int kUPer = KP * kTcNChunk / 256;   // U^T elements per thread when 256 threads stage
   if (ok) {
     if (warp < 4) {
       const int n = warp * 32 + lane;           // TMEM lane = row in the tile
@@ -246,8 +263,19 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
         Zl[off] = lo;
       }
     } else {
-      stage_u(0, tid - 128, 128);
-      if (n_chunks > 1) stage_u(1, tid - 128, 128);
+      // chunks 0 and 1 by the upper four warps: all loads first, then the stores
+      const int t0 = tid - 128;
+      float ux0[2 * kUPer], ux1[2 * kUPer];
+#pragma unroll
+      for (int q = 0; q < 2 * kUPer; ++q) {
+        ux0[q] = u_elem(0, t0 + 128 * q);
+        ux1[q] = n_chunks > 1 ? u_elem(1, t0 + 128 * q) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 2 * kUPer; ++q) {
+        u_store(0, t0 + 128 * q, ux0[q]);
+        if (n_chunks > 1) u_store(1, t0 + 128 * q, ux1[q]);
+      }
     }
   }
   tc::fence_async_smem();
@@ -285,6 +313,11 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
     // reduce-add per row, so the epilogue reads no Binv0 and the LSU pipe only stores the
     // tile once. The reduce-add rounds B + (-P) to nearest, exactly as B - P would be.
     for (int c = 0; c < n_chunks && ok; ++c) {
+      // the U^T values of chunk c + 2, in flight while chunk c's MMAs finish
+      const bool su = c + 2 < n_chunks;
+      float ux[kUPer];
+#pragma unroll
+      for (int q = 0; q < kUPer; ++q) ux[q] = su ? u_elem(c + 2, tid + 256 * q) : 0.f;
       if (tid == 0 && c + 1 < n_chunks) {
         tc::fence_after();
         issue2(c + 1);
@@ -304,8 +337,10 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
         for (int t = 0; t < 16; t += 4)
           *reinterpret_cast<float4*>(srow + t) = make_float4(-v[t], -v[t + 1], -v[t + 2], -v[t + 3]);
       }
-      // U^T buffer c & 1 is free (its MMAs completed): stage chunk c + 2 there
-      if (c + 2 < n_chunks) stage_u(c + 2, tid, blockDim.x);
+      // U^T buffer c & 1 is free (its MMAs completed): chunk c + 2 goes there
+      if (su)
+#pragma unroll
+        for (int q = 0; q < kUPer; ++q) u_store(c + 2, tid + 256 * q, ux[q]);
       tc::fence_async_smem();
       tc::fence_before();
       __syncthreads();
