@@ -114,11 +114,16 @@ typedef struct {
                               tau v 2 / (1 + sqrt(1 + 2 a |v|^2 tau)), below sqrt(2 tau / a)
                               for any v, in the proposal and in the Green's-function ratio of
                               the acceptance; 0 = the plain drift. */
+  int prop_chunk;          /* Metropolis moves whose proposals and orbital rows are formed by
+                              one launch pair, per spin block (0 = the whole block); smaller
+                              batches keep the rows in L2 until the sweep reads them. A
+                              launch parameter only: the chain does not depend on it. */
 } qmc_system_desc;
 
 /* Creates a system. Fails with QMC_EINVAL for n_up or n_dn outside [0, 1024], n_up+n_dn
- * = 0, L <= 0, step < 0, delay_k outside [1, 64], an unknown precision/move, or a
- * logdet_period that is negative or not a multiple of a positive reinv_period. */
+ * = 0, L <= 0, step < 0, delay_k outside [1, 64], an unknown precision/move, a
+ * logdet_period that is negative or not a multiple of a positive reinv_period, or a negative
+ * prop_chunk. */
 qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out);
 
 /* Sets the B-spline orbital table (Sec. "B-spline basis sets"). coef is host memory

@@ -165,6 +165,7 @@ extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_
   if (d.n_ion < 0 || (d.n_ion > 0 && !d.ion_pos)) return fail(QMC_EINVAL, "bad ion list");
   if (!(d.step >= 0.0)) return fail(QMC_EINVAL, "step must be >= 0");
   if (!(d.drift_a >= 0.0) || !std::isfinite(d.drift_a)) return fail(QMC_EINVAL, "drift_a must be >= 0");
+  if (d.prop_chunk < 0) return fail(QMC_EINVAL, "prop_chunk must be >= 0");
   if (d.delay_k < 1 || d.delay_k > kMaxDelay) return fail(QMC_EINVAL, "delay_k must be in [1, %d]", kMaxDelay);
   if (d.prec < QMC_FP64 || d.prec > QMC_FP32_BF16TAB) return fail(QMC_EINVAL, "unknown precision");
   if (d.move != QMC_MOVE_METROPOLIS && d.move != QMC_MOVE_DRIFT) return fail(QMC_EINVAL, "unknown move");
@@ -534,7 +535,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   W.ld_v = round_up(std::max(ns_max, 1), 8);
   const size_t tw = s->tw->tw_size;
   const size_t nw = cap, ne = P.n_e;
-  w->chunk = ns_max;
+  w->chunk = s->d.prop_chunk > 0 ? std::min(ns_max, s->d.prop_chunk) : ns_max;
   // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
   while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
   const size_t np = proposals ? nw * (size_t)w->chunk : 1;

@@ -27,48 +27,20 @@ __host__ __device__ inline int flush_tc_mpad(int kc) { return (kc + 15) & ~15; }
 
 constexpr int kTcStageLd = kTcNChunk + 4;       // row stride (floats) of the epilogue tile
 
-// Dynamic shared memory of k_flush_tc for a window capacity kc. The first region serves the
-// first product as a ring of three Binv0 chunks and three Phi chunks (each rounded to TF32 in
-// place once it lands) with one lo tile of each, and the second product as the Z tile, the
-// two U^T buffers and the epilogue's staging tile (-P of one 64-column chunk, rows padded to
-// kTcStageLd floats); C^-1 and the window rows follow.
-constexpr int kTcRing = 3;                       // Binv0 / Phi chunks in flight or in use
-__host__ __device__ inline size_t flush_tc_ring_floats(int mx) {
-  return (size_t)(kTcRing + 1) * (kTcRows + mx) * kTcKChunk;
-}
-__host__ __device__ inline size_t flush_tc_region_floats(int mx) {
-  const size_t zu = 2 * (size_t)kTcRows * mx + 4 * (size_t)kTcNChunk * mx;
-  const size_t p3 = zu + (size_t)kTcRows * kTcStageLd;
-  const size_t p1 = flush_tc_ring_floats(mx);
-  return p1 > p3 ? p1 : p3;
-}
+// Dynamic shared memory of k_flush_tc for a window capacity kc. The first region holds
+// the Binv0 chunk during the first product and, once that is complete, the Z tile and the
+// two U^T buffers of the second; the last region is the epilogue's staging tile (-P of one
+// 64-column chunk, rows padded to kTcStageLd floats).
 __host__ __device__ inline size_t flush_tc_smem_bytes(int kc) {
-  const int mx = flush_tc_mpad(kc);
-  size_t b = flush_tc_region_floats(mx) * 4;
+  const size_t mx = flush_tc_mpad(kc);
+  const size_t a1 = 2 * (size_t)kTcRows * kTcKChunk * 4;                       // hi + lo
+  const size_t zu = 2 * (size_t)kTcRows * mx * 4 + 2 * 2 * (size_t)kTcNChunk * mx * 4;
+  size_t b = a1 > zu ? a1 : zu;
+  b += 2 * mx * kTcKChunk * 4;                  // Phi chunk, hi + lo
   b += (size_t)kc * kc * 4 + (size_t)kc * 4 + 64;
-  return (b + 15) & ~(size_t)15;
-}
-
-// 16-byte asynchronous copy that writes zeros when `valid` is false (no bytes are read then).
-__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// Rounds a landed 16-byte group of FP32 values to TF32 in place and writes the remainders.
-__device__ __forceinline__ void split_tf32_inplace4(float* hi, float* lo) {
-  float4 x = *reinterpret_cast<const float4*>(hi), h, l;
-  split_tf32(x.x, h.x, l.x);
-  split_tf32(x.y, h.y, l.y);
-  split_tf32(x.z, h.z, l.z);
-  split_tf32(x.w, h.w, l.w);
-  *reinterpret_cast<float4*>(hi) = h;
-  *reinterpret_cast<float4*>(lo) = l;
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)kTcRows * kTcStageLd * 4;        // epilogue staging tile
+  return b;
 }
 
 // Stages one 16-float slice of a Binv0 row into the hi/lo TF32 tiles.
@@ -116,22 +88,20 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   const int mp = (m + 15) & ~15;                // N of the first product, K of the second
   const int mx = flush_tc_mpad(kc);             // staged width of the Z and U^T tiles (<= KP)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // shared memory: the region (first product: ring of Binv0 and Phi chunks and their lo
-  // tiles; second product: Z, U^T and the staging tile), then C^-1 and the window rows
-  float* R = reinterpret_cast<float*>(smem_t);
-  // Binv0 chunk slot i (TF32 hi after the split) and Phi chunk slot i
-  const auto Ah = [&](int i) { return R + (size_t)i * kTcRows * kTcKChunk; };
-  const auto Bh = [&](int i) {
-    return R + (size_t)(kTcRing + 1) * kTcRows * kTcKChunk + (size_t)i * mx * kTcKChunk;
-  };
-  float* Al = R + (size_t)kTcRing * kTcRows * kTcKChunk;
-  float* Bl = R + (size_t)(kTcRing + 1) * kTcRows * kTcKChunk + (size_t)kTcRing * mx * kTcKChunk;
-  float* Zh = R;
+  // shared memory: region 1 (A1 during the first product; Z and U^T after it), Phi, C^-1
+  const size_t a1 = 2 * (size_t)kTcRows * kTcKChunk;
+  const size_t zu = 2 * (size_t)kTcRows * mx + 4 * (size_t)kTcNChunk * mx;
+  float* A1h = reinterpret_cast<float*>(smem_t);
+  float* A1l = A1h + kTcRows * kTcKChunk;
+  float* Zh = A1h;
   float* Zl = Zh + kTcRows * mx;
   float* Ub = Zl + kTcRows * mx;                // [buffer][hi, lo][64 x mx]
-  float* stage = Ub + 4 * (size_t)kTcNChunk * mx;   // [128][kTcStageLd]
-  float* ci = R + flush_tc_region_floats(mx);
+  float* B1h = A1h + (a1 > zu ? a1 : zu);
+  float* B1l = B1h + mx * kTcKChunk;
+  float* ci = B1l + mx * kTcKChunk;
   int* wrow = reinterpret_cast<int*>(ci + kc * kc);
+  float* stage = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(wrow + kc) + 64 + 15) & ~uintptr_t(15));   // [128][kTcStageLd]
   const float* gphi = static_cast<const float*>(Wk.win_phi) + (size_t)w * kc * ld_v;
   const float* gu = static_cast<const float*>(Wk.win_u) + (size_t)w * kc * ld_v;
   const float* gc = static_cast<const float*>(Wk.win_cinv) + (size_t)w * kc * kc;
@@ -160,110 +130,66 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
   const int lr = tid >> 1, lc = (tid & 1) * 16;
   const int kc1 = kTcKChunk * 4 / 16;           // 16-byte K columns per chunk
   const float* brow = B + (size_t)(r0 + lr) * ns;
-  const int nch = (ns + kTcKChunk - 1) / kTcKChunk;
-  const uint32_t id1 = tc::instr_desc(tc::kFmtTF32, kTcRows, mp);
-  auto mma1 = [&](const float* ah0, const float* al0, const float* bh0, const float* bl0, int ch) {
-    tc::fence_after();
-#pragma unroll
-    for (int s = 0; s < kTcKChunk / 8; ++s) {
-      const uint64_t ah = tc::smem_desc(ah0 + s * 64, 128, kc1 * 128);
-      const uint64_t al = tc::smem_desc(al0 + s * 64, 128, kc1 * 128);
-      const uint64_t bh = tc::smem_desc(bh0 + s * 64, 128, kc1 * 128);
-      const uint64_t bl = tc::smem_desc(bl0 + s * 64, 128, kc1 * 128);
-      const uint32_t first = (ch == 0 && s == 0) ? 0u : 1u;
-      tc::mma_tf32(tmem, ah, bh, id1, first);
-      tc::mma_tf32(tmem, ah, bl, id1, 1u);
-      tc::mma_tf32(tmem, al, bh, id1, 1u);
-    }
-    tc::mma_commit(&bar[0]);
-  };
-  uint32_t ph1 = 0;
-  if (vec) {
-    // Binv0 and Phi chunks arrive by cp.async two chunks ahead of their MMAs; each thread
-    // rounds the 16-byte groups it copied itself, so only the MMA needs the barrier.
-    auto issue = [&](int ch) {
-      const int k0 = ch * kTcKChunk, sl = ch % kTcRing;
-      char* at = reinterpret_cast<char*>(Ah(sl));
+  float xa[16];
+  constexpr int kPhiPer = KP * kTcKChunk / 256;  // Phi elements per thread and chunk
+  float xp[kPhiPer];
+  auto load_chunk = [&](int k0) {
+    const int j = k0 + lc;
+    if (vec) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int j = k0 + lc + 4 * t;
-        const bool v = lr < nr && j < ns;
-        cp_async16_zfill(at + tc::tile_offset(lr, lc + 4 * t, kc1, 4), v ? brow + j : B, v);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lr < nr && j + 4 * t < ns) v = *reinterpret_cast<const float4*>(brow + j + 4 * t);
+        xa[4 * t] = v.x; xa[4 * t + 1] = v.y; xa[4 * t + 2] = v.z; xa[4 * t + 3] = v.w;
       }
-      char* bt = reinterpret_cast<char*>(Bh(sl));
-      for (int g = tid; g < mx * 8; g += 256) {
-        const int l = g >> 3, kk = (g & 7) * 4, j = k0 + kk;
-        const bool v = l < m && j < ns;
-        cp_async16_zfill(bt + tc::tile_offset(l, kk, kc1, 4), v ? gphi + (size_t)l * ld_v + j : gphi, v);
-      }
-      cp_async_commit();
-    };
-    for (int ch = 0; ch < kTcRing; ++ch) {
-      if (ch < nch) issue(ch);
-      else cp_async_commit();                   // one group per chunk, empty past the end
-    }
-    for (int ch = 0; ch < nch; ++ch) {
-      const int sl = ch % kTcRing;
-      if (ch > 0) {                             // MMA ch - 1 done: the lo tiles and its slot free
-        ok = tc::mbar_wait(&bar[0], ph1, kTcWaitPolls) && ok;
-        ph1 ^= 1u;
-        if (ch + kTcRing - 1 < nch) issue(ch + kTcRing - 1);
-        else cp_async_commit();
-      }
-      cp_async_wait_group<kTcRing - 1>();       // this thread's copies of chunk ch have landed
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint32_t off = tc::tile_offset(lr, lc + 4 * t, kc1, 4) >> 2;
-        split_tf32_inplace4(Ah(sl) + off, Al + off);
-      }
-      for (int g = tid; g < mx * 8; g += 256) {
-        const uint32_t off = tc::tile_offset(g >> 3, (g & 7) * 4, kc1, 4) >> 2;
-        split_tf32_inplace4(Bh(sl) + off, Bl + off);
-      }
-      tc::fence_async_smem();
-      ok = __syncthreads_and(ok);
-      if (!ok) break;
-      if (tid == 0) mma1(Ah(sl), Al, Bh(sl), Bl, ch);
-    }
-    cp_async_wait_group<0>();
-  } else {
-    // rows that are not whole 16-byte groups: plain loads one chunk ahead, slot 0 only
-    float xa[16];
-    constexpr int kPhiPer = KP * kTcKChunk / 256;  // Phi elements per thread and chunk
-    float xp[kPhiPer];
-    auto load_chunk = [&](int k0) {
-      const int j = k0 + lc;
+    } else {
 #pragma unroll
       for (int t = 0; t < 16; ++t) xa[t] = (lr < nr && j + t < ns) ? brow[j + t] : 0.f;
+    }
 #pragma unroll
-      for (int q = 0; q < kPhiPer; ++q) {
-        const int i = tid + 256 * q, l = i / kTcKChunk, jj = k0 + i % kTcKChunk;
-        xp[q] = (l < m && jj < ns) ? gphi[(size_t)l * ld_v + jj] : 0.f;
-      }
-    };
-    load_chunk(0);
-    for (int ch = 0; ch < nch; ++ch) {
-      if (ch > 0) {                             // the previous chunk's MMAs read the tiles
-        ok = tc::mbar_wait(&bar[0], ph1, kTcWaitPolls) && ok;
-        ph1 ^= 1u;
-      }
-      stage_split16(xa, Ah(0), Al, lr, lc, kc1);
+    for (int q = 0; q < kPhiPer; ++q) {
+      const int i = tid + 256 * q, l = i / kTcKChunk, jj = k0 + i % kTcKChunk;
+      xp[q] = (l < m && jj < ns) ? gphi[(size_t)l * ld_v + jj] : 0.f;
+    }
+  };
+  const uint32_t id1 = tc::instr_desc(tc::kFmtTF32, kTcRows, mp);
+  load_chunk(0);
+  uint32_t ph1 = 0;
+  for (int k0 = 0; k0 < ns; k0 += kTcKChunk) {
+    if (k0 > 0) {                               // the previous chunk's MMAs read A1 and B1
+      ok = tc::mbar_wait(&bar[0], ph1, kTcWaitPolls) && ok;
+      ph1 ^= 1u;
+    }
+    stage_split16(xa, A1h, A1l, lr, lc, kc1);
 #pragma unroll
-      for (int q = 0; q < kPhiPer; ++q) {
-        const int i = tid + 256 * q, l = i / kTcKChunk, k = i % kTcKChunk;
-        if (l < mx) {
-          float hi, lo;
-          split_tf32(xp[q], hi, lo);
-          const uint32_t off = tc::tile_offset(l, k, kc1, 4) >> 2;
-          Bh(0)[off] = hi;
-          Bl[off] = lo;
-        }
+    for (int q = 0; q < kPhiPer; ++q) {
+      const int i = tid + 256 * q, l = i / kTcKChunk, k = i % kTcKChunk;
+      if (l < mx) {
+        float hi, lo;
+        split_tf32(xp[q], hi, lo);
+        const uint32_t off = tc::tile_offset(l, k, kc1, 4) >> 2;
+        B1h[off] = hi;
+        B1l[off] = lo;
       }
-      tc::fence_async_smem();
-      ok = __syncthreads_and(ok);
-      if (!ok) break;
-      if (ch + 1 < nch) load_chunk((ch + 1) * kTcKChunk);
-      if (tid == 0) mma1(Ah(0), Al, Bh(0), Bl, ch);
+    }
+    tc::fence_async_smem();
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    if (k0 + kTcKChunk < ns) load_chunk(k0 + kTcKChunk);
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int s = 0; s < kTcKChunk / 8; ++s) {
+        const uint64_t ah = tc::smem_desc(A1h + s * 64, 128, kc1 * 128);
+        const uint64_t al = tc::smem_desc(A1l + s * 64, 128, kc1 * 128);
+        const uint64_t bh = tc::smem_desc(B1h + s * 64, 128, kc1 * 128);
+        const uint64_t bl = tc::smem_desc(B1l + s * 64, 128, kc1 * 128);
+        const uint32_t first = (k0 == 0 && s == 0) ? 0u : 1u;
+        tc::mma_tf32(tmem, ah, bh, id1, first);
+        tc::mma_tf32(tmem, ah, bl, id1, 1u);
+        tc::mma_tf32(tmem, al, bh, id1, 1u);
+      }
+      tc::mma_commit(&bar[0]);
     }
   }
   if (ok) ok = tc::mbar_wait(&bar[0], ph1, kTcWaitPolls);
