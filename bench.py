@@ -65,6 +65,8 @@ def parse_args():
                         "(64/192/384 electrons with 768/512/256 target walkers)")
     p.add_argument("--walkers", type=int, default=0,
                    help="walker count (default: the preset's); smaller counts serve profiling")
+    p.add_argument("--dmc-delay-k", type=int, default=16,
+                   help="delay rank of the batched DMC workload (drift moves)")
     p.add_argument("--dmc-vmc-sweeps", type=int, default=4,
                    help="drift-diffusion VMC sweeps that equilibrate the walkers before DMC")
     return p.parse_args()
@@ -637,7 +639,9 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
     import paper_1802_06922_gb300 as q
     from synthetic import build_inputs, spec_for
     stream = torch.cuda.current_stream()
-    dmc_k = 16 if args.delay_k == "auto" else int(args.delay_k)
+    # drift moves run the per-move window form, whose work grows with k: the DMC workload has
+    # its own delay rank (k = 16 measured best among 8, 16 and 32 for these systems)
+    dmc_k = args.dmc_delay_k
     precision = "fp32" if args.precision == "fp64" and args.workload == "vmc" else args.precision
     systems, pos, et, specs = [], [], [], []
     for name in DMC_SYSTEMS:

@@ -7,7 +7,7 @@ kernels of ``libqmcgb.so`` built from ``csrc/`` for sm_103a.
 """
 from .qmcgb import (DMC, QMCError, System, Walkers, load, measure_rates,  # noqa: F401
                     slater_invert, slater_invert_noalloc, system_from_inputs)
-from .autotune import tune_delay  # noqa: F401
+from .autotune import tune_delay, tune_launch  # noqa: F401
 
 __all__ = ["DMC", "QMCError", "System", "Walkers", "load", "measure_rates", "slater_invert",
-           "slater_invert_noalloc", "system_from_inputs", "tune_delay"]
+           "slater_invert_noalloc", "system_from_inputs", "tune_delay", "tune_launch"]

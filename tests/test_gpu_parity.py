@@ -223,3 +223,24 @@ def test_refinement_beyond_the_exact_slice_bound_falls_back_to_fp64():
         assert err < 1e-4 * max(1.0, np.linalg.cond(A) * 2.0 ** -24 / 1e-4), err
     w.close()
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_proposal_batch_does_not_change_the_chain(precision):
+    """The proposal batch (moves whose proposals and orbital rows one launch pair forms) is a
+    launch parameter: batches of 8 and 24 moves and the whole block give identical chains."""
+    inputs = build_inputs(small_spec(40, 37, grid=12), n_walkers=3)
+    out = []
+    for chunk in (0, 8, 24):
+        s = q.system_from_inputs(inputs, precision=precision, delay_k=8, prop_chunk=chunk,
+                                 reinv_period=16 if precision == "fp32" else 0,
+                                 logdet_period=16 if precision == "fp32" else 0)
+        w = q.Walkers(s, inputs["pos"])
+        w.sweep(2)
+        e, l = w.measure()
+        out.append((w.positions(), e, l))
+        w.close()
+        s.close()
+    for pos, e, l in out[1:]:
+        assert np.array_equal(pos, out[0][0])
+        assert np.array_equal(e, out[0][1]) and np.array_equal(l, out[0][2])
