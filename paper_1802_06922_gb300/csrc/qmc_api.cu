@@ -102,6 +102,8 @@ struct qmc_walkers_s {
   bool energy_valid = false;   // e_loc / log_psi hold the current configuration's values
   uint64_t energy_version = 0; // the system's Hamiltonian version they were measured with
   void* d_j3vgl = nullptr;     // three-body Jastrow terms per electron [W][n_e][5] (working precision)
+  cudaStream_t side = nullptr; // the up block's last refinement of a sweep runs here, beside
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // the down block's moves
   int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
   int since_anchor[2] = {0, 0};// proposed moves per spin since the last log-det anchor
   bool profiling = false;
@@ -498,6 +500,9 @@ void free_walkers(qmc_walkers_s* w) {
                   W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
                   W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count, w->d_j3vgl};
   for (void* p : ptrs) cudaFree(p);
+  if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+  if (w->ev_join) cudaEventDestroy(w->ev_join);
+  if (w->side) cudaStreamDestroy(w->side);
 }
 
 qmc_status upload_positions(qmc_walkers_s* w, const double* pos, bool pos_on_device) {
@@ -569,7 +574,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.win_cinv, nw * (size_t)s->d.delay_k * s->d.delay_k * tw},
       {(void**)&W.win_row, nw * (size_t)s->d.delay_k * sizeof(int)},
       {(void**)&W.win_m, nw * sizeof(int)},
-      {(void**)&W.refine_max, nw * sizeof(float)},
+      {(void**)&W.refine_max, nw * 2 * sizeof(float)},
       {(void**)&W.refine_last, nw * 2 * sizeof(float)},
       {(void**)&W.logdet_shift, nw * 2 * sizeof(float)},
       {(void**)&W.r2, nw * 2 * sizeof(double)},
@@ -590,13 +595,20 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
                   cudaGetErrorString(e));
     }
   }
+  if (cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    free_walkers(w);
+    delete w;
+    return fail(QMC_ECUDA, "cannot create the walker set's side stream");
+  }
   // zero the orbital rows so padded columns never hold garbage
   cudaMemset(W.vgl, 0, nw * ne * 5 * W.ld_v * tw);
   cudaMemset(W.err, 0, sizeof(int));
   cudaMemset(W.n_acc, 0, nw * sizeof(long long));
   cudaMemset(W.acc_since, 0, nw * 2 * sizeof(int));
   cudaMemset(W.win_m, 0, nw * sizeof(int));
-  cudaMemset(W.refine_max, 0, nw * sizeof(float));
+  cudaMemset(W.refine_max, 0, nw * 2 * sizeof(float));
   cudaMemset(W.refine_last, 0xFF, nw * 2 * sizeof(float));   // NaN: no refinement yet
   cudaMemset(W.logdet_shift, 0xFF, nw * 2 * sizeof(float));  // NaN: no anchor yet
   cudaMemset(W.r2, 0, nw * 2 * sizeof(double));
@@ -655,6 +667,7 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStre
   const bool drift = s->d.move == QMC_MOVE_DRIFT;
   const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
                    !(period > 0 && s->d.prec == QMC_FP64);
+  bool joined = true;             // the side stream's work has been joined back into st
   for (int spin = 0; spin < 2; ++spin) {
     const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
     const int pchunk = drift ? std::max(b1 - b0, 1) : w->chunk;
@@ -690,22 +703,36 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStre
         if (period > 0) {
           w->since_moves[spin] += e1 - e0;
           if (w->since_moves[spin] >= period) {
-            { Bracket b(w, st, QMC_K_REFINE); QMC_CUDA(s->tw->refine(P, W, spin, 0, st)); }
+            // The up block's last refinement of the sweep (and its log-det anchor) runs on the
+            // side stream beside the down block's moves, which read the positions and the
+            // down block's own arrays only; the sweep joins it back before it returns.
+            const bool fork = spin == 0 && e1 == b1 && P.n_dn > 0;
+            cudaStream_t rs = st;
+            if (fork) {
+              QMC_CUDA(cudaEventRecord(w->ev_fork, st));
+              QMC_CUDA(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
+              rs = w->side;
+            }
+            { Bracket b(w, rs, QMC_K_REFINE); QMC_CUDA(s->tw->refine(P, W, spin, 0, rs)); }
             {
-              Bracket b(w, st, QMC_K_REFINE_UPDATE);
-              QMC_CUDA(s->tw->refine(P, W, spin, 1, st));
+              Bracket b(w, rs, QMC_K_REFINE_UPDATE);
+              QMC_CUDA(s->tw->refine(P, W, spin, 1, rs));
               // the refined inverse is in the second buffer: it becomes the current one
               std::swap(W.binv[spin], W.binv_alt[spin]);
               std::swap(w->W.binv[spin], w->W.binv_alt[spin]);
-              QMC_CUDA(s->tw->refine(P, W, spin, 2, st));
+              QMC_CUDA(s->tw->refine(P, W, spin, 2, rs));
             }
             w->launches += 2;   // row scales + residual, update + fallback
             w->since_anchor[spin] += w->since_moves[spin];
             w->since_moves[spin] = 0;
             if (s->d.logdet_period > 0 && w->since_anchor[spin] >= s->d.logdet_period) {
-              Bracket b(w, st, QMC_K_LOGDET);
-              QMC_CUDA(s->tw->logdet_anchor(P, W, spin, st));
+              Bracket b(w, rs, QMC_K_LOGDET);
+              QMC_CUDA(s->tw->logdet_anchor(P, W, spin, rs));
               w->since_anchor[spin] = 0;
+            }
+            if (fork) {
+              QMC_CUDA(cudaEventRecord(w->ev_join, w->side));
+              joined = false;
             }
           }
         }
@@ -713,6 +740,7 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStre
       }
     }
   }
+  if (!joined) QMC_CUDA(cudaStreamWaitEvent(st, w->ev_join, 0));
   return QMC_OK;
 }
 }  // namespace

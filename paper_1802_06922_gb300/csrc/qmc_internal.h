@@ -100,7 +100,8 @@ struct WalkParams {
   void* win_cinv;      // [W][kc][kc]   C^-1
   int* win_row;        // [W][kc]       row (electron index within the spin block)
   int* win_m;          // [W]           fill
-  float* refine_max;   // [W]           max |I - A X| of the refinement in progress
+  float* refine_max;   // [W][2]        max |I - A X| of the refinement in progress of each
+                       //               spin block (the two blocks' refinements may overlap)
   float* refine_last;  // [W][2]        max |I - A X| measured by the last refinement of each
                        //               spin block (before its Newton step); NaN if none yet
   float* logdet_shift; // [W][2]        change of ln|det A| made by the last log-det anchor

@@ -163,7 +163,16 @@ __global__ void __launch_bounds__(256, sizeof(TT) == 8 ? 1 : 2) k_vgl_proposals(
   const long long mv = gw / chunks;
   const Prop p = prop[mv];
   const double r[3] = {p.x, p.y, p.z};
-  vgl_warp<TT, TW>(S, r, ch * 32 * V, ns, out + (size_t)mv * 5 * Wk.ld_v, Wk.ld_v);
+  TW* o = out + (size_t)mv * 5 * Wk.ld_v;
+  vgl_warp<TT, TW>(S, r, ch * 32 * V, ns, o, Wk.ld_v);
+  // the padding columns N_s..ld_v-1 of the five rows are zero, as in the current rows that an
+  // accepted move's rows replace whole (the buffer also serves the other spin block's moves)
+  if (ch == chunks - 1) {
+    const int lane = threadIdx.x & 31;
+    for (int j = ns + lane; j < Wk.ld_v; j += 32)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) o[(size_t)q * Wk.ld_v + j] = TW(0);
+  }
 }
 
 // =============================================================================
@@ -1391,7 +1400,7 @@ __global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams
   extern __shared__ __align__(16) char smem_c[];
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
-  const float rm = Wk.refine_max[w];
+  const float rm = Wk.refine_max[2 * w + spin];
   if (!(rm <= kRefineMax)) {
     double* colk = reinterpret_cast<double*>(smem_c);
     double* redv = colk + Wk.ld_v;
@@ -1401,7 +1410,7 @@ __global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams
   }
   if (threadIdx.x == 0) {
     Wk.refine_last[2 * w + spin] = rm;
-    Wk.refine_max[w] = 0.f;
+    Wk.refine_max[2 * w + spin] = 0.f;
   }
 }
 

@@ -98,7 +98,7 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
       // beyond the exactness bound of the slice products: every walker of this spin block
       // takes the FP64 re-inversion (refine_max set to NaN makes the update skip them and
       // the fallback re-invert them)
-      return cudaMemsetAsync(W.refine_max, 0xFF, sizeof(float) * W.n_w, st);
+      return cudaMemset2DAsync(W.refine_max + spin, 2 * sizeof(float), 0xFF, sizeof(float), W.n_w, st);
     }
     // error-free residual on the tensor cores (power-of-two row scales first)
     k_refine_scales<TW><<<dim3(W.n_w, 2), kThreads, 0, st>>>(S, W, spin);

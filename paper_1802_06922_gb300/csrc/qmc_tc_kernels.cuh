@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-  if (lane == 0) atomicMax(reinterpret_cast<int*>(Wk.refine_max + w), __float_as_int(rmax));
+  if (lane == 0) atomicMax(reinterpret_cast<int*>(Wk.refine_max + 2 * w + spin), __float_as_int(rmax));
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 512);
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(256, 1) k_refine_update_tc(SysParams S, WalkPa
   __shared__ uint32_t tbase;
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;
-  if (!(Wk.refine_max[w] <= kRefineMax)) return;   // FP64 re-inversion in the commit
+  if (!(Wk.refine_max[2 * w + spin] <= kRefineMax)) return;   // FP64 re-inversion in the commit
   const int ns = spin ? S.n_dn : S.n_up;
   const int nt = (ns + kTcRows - 1) / kTcRows;
   const int e0 = (blockIdx.y / nt) * kTcRows, j0 = (blockIdx.y % nt) * kTcRows;
