@@ -65,6 +65,9 @@ def parse_args():
                         "(64/192/384 electrons with 768/512/256 target walkers)")
     p.add_argument("--walkers", type=int, default=0,
                    help="walker count (default: the preset's); smaller counts serve profiling")
+    p.add_argument("--dmc-profile", action="store_true",
+                   help="per-kernel device time of every DMC system (times the steps with "
+                        "profiling events, so the step time reads slightly higher)")
     p.add_argument("--dmc-delay-k", type=int, default=16,
                    help="delay rank of the batched DMC workload (drift moves)")
     p.add_argument("--dmc-vmc-sweeps", type=int, default=4,
@@ -668,6 +671,8 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
     torch.cuda.synchronize()
     l0 = d.launch_count()
     total_ms, moves = 0.0, 0
+    if args.dmc_profile:
+        d.profile(True)
     pops = []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -681,6 +686,14 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
         pops.append([int(x["population_before"]) for x in st])
         moves += sum(sp.n_elec * int(x["population_before"]) for sp, x in zip(specs, st))
     launches = d.launch_count() - l0
+    prof = None
+    if args.dmc_profile:
+        import paper_1802_06922_gb300.qmcgb as qb
+        prof = {}
+        for i, sp in enumerate(specs):
+            pm, pn = d.profile_read(i)
+            prof[sp.name] = {n: round(float(pm[j]) / n_steps, 3)
+                             for j, n in enumerate(qb.KERNEL_CLASSES) if pn[j]}
     final = [d.read(i) for i in range(len(systems))]
     total_ms = max_over_ranks(total_ms, dist)
     d.close()
@@ -699,6 +712,7 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
               f"{args.dmc_vmc_sweeps} VMC sweeps, E_T from their median E_L; systems on "
               f"concurrent streams",
             "populations_first_last": [pops[0], pops[-1]],
+            "kernels_ms_per_step": prof,
             "e_mean_last": [float(x["e_mean"]) for x in final],
             "e_trial_last": [float(x["e_trial_next"]) for x in final],
             "gpu_launches": launches}

@@ -370,6 +370,13 @@ qmc_status qmc_dmc_read(qmc_dmc_t d, int system, double* out);
 qmc_status qmc_dmc_walkers(qmc_dmc_t d, int system, int max_walkers, double* pos, uint32_t* ids,
                            double* e_local, int* n_out);
 int64_t qmc_dmc_launch_count(qmc_dmc_t d);
+/* Per-kernel device time of the driver's steps, as qmc_profile_enable / qmc_profile_read of a
+ * walker set (kernel classes of qmc_kernel), for one system (both of its slot buffers). The
+ * systems run on concurrent streams, so the classes of different systems overlap in time.
+ * Read synchronises with the recorded events and resets the sums. QMC_EINVAL for a NULL
+ * driver or a bad system index. */
+qmc_status qmc_dmc_profile_enable(qmc_dmc_t d, int enable);
+qmc_status qmc_dmc_profile_read(qmc_dmc_t d, int system, double* ms, int64_t* launches);
 void qmc_dmc_destroy(qmc_dmc_t d);
 
 /* Rates of the current device that bound the kernels neither the tensor cores nor HBM
@@ -396,7 +403,8 @@ typedef enum {
   QMC_K_NLPP = 11,        /* non-local pseudopotential quadrature (pairs and virtual moves) */
   QMC_K_EWALD = 12,       /* Ewald reciprocal-space energy (structure factors) */
   QMC_K_JASTROW3 = 13,    /* three-body Jastrow gradient, Laplacian and value per electron */
-  QMC_NKERNELS = 14
+  QMC_K_BRANCH = 14,      /* DMC branching or reconfiguration, and the walker copies */
+  QMC_NKERNELS = 15
 } qmc_kernel;
 
 /* Per-kernel timing: when enabled, every launch of the walker set is bracketed by CUDA

@@ -1181,9 +1181,12 @@ extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
       DmcParams D = y.D;
       D.e_old = y.e_old[y.parity];
       D.e_old_next = y.e_old[y.parity ^ 1];
-      QMC_CUDA(y.sys->tw->dmc_branch(y.sys->P, W, D, y.parity, d->step, y.st));
-      QMC_CUDA(y.sys->tw->dmc_copy(y.sys->P, W, w2->W, D, y.parity, y.st));
-      w->launches += 2;
+      {
+        Bracket b(w, y.st, QMC_K_BRANCH);
+        QMC_CUDA(y.sys->tw->dmc_branch(y.sys->P, W, D, y.parity, d->step, y.st));
+        QMC_CUDA(y.sys->tw->dmc_copy(y.sys->P, W, w2->W, D, y.parity, y.st));
+      }
+      w->launches += 1;   // the copy kernel after the branching kernel
       y.parity ^= 1;
     }
     ++d->step;
@@ -1191,6 +1194,34 @@ extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
   for (size_t i = 0; i < d->sys.size(); ++i) {
     QMC_CUDA(cudaEventRecord(d->ev_out[i], d->sys[i].st));
     QMC_CUDA(cudaStreamWaitEvent(cs, d->ev_out[i], 0));
+  }
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_profile_enable(qmc_dmc_t d, int enable) {
+  if (!d) return fail(QMC_EINVAL, "qmc_dmc_profile_enable: NULL driver");
+  for (auto& y : d->sys)
+    for (auto* w : y.w) w->profiling = enable != 0;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_profile_read(qmc_dmc_t d, int system, double* ms, int64_t* launches) {
+  if (!d) return fail(QMC_EINVAL, "qmc_dmc_profile_read: NULL driver");
+  if (system < 0 || system >= (int)d->sys.size()) return fail(QMC_EINVAL, "qmc_dmc_profile_read: bad system");
+  double acc_ms[QMC_NKERNELS] = {0};
+  int64_t acc_n[QMC_NKERNELS] = {0};
+  for (auto* w : d->sys[system].w) {
+    drain_events(w);
+    for (int k = 0; k < QMC_NKERNELS; ++k) {
+      acc_ms[k] += w->prof_ms[k];
+      acc_n[k] += w->prof_n[k];
+      w->prof_ms[k] = 0.0;
+      w->prof_n[k] = 0;
+    }
+  }
+  for (int k = 0; k < QMC_NKERNELS; ++k) {
+    if (ms) ms[k] = acc_ms[k];
+    if (launches) launches[k] = acc_n[k];
   }
   return QMC_OK;
 }

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "QMC_OK", -1: "QMC_EINVAL", -2: "QMC_ENOMEM", -3: "QMC_ECUDA"
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2}
 KERNEL_CLASSES = ("propose", "vgl", "sweep", "energy", "reinvert", "vgl_current",
                   "accumulate", "flush", "refine", "refine_update", "logdet", "nlpp", "ewald",
-                  "jastrow3")
+                  "jastrow3", "branch")
 MOVES = {"metropolis": 0, "drift": 1}
 
 # Exported symbols and their ctypes signatures (argtypes, restype), as declared in
@@ -46,6 +46,8 @@ SIGNATURES = {
     "qmc_system_set_nonlocal": ([_vp, _i, _vp, _vp, _d], _i),
     "qmc_system_set_ewald": ([_vp, _d, _d], _i),
     "qmc_system_set_jastrow3": ([_vp, _i, _i, _d, _vp, _vp], _i),
+    "qmc_dmc_profile_enable": ([_vp, _i], _i),
+    "qmc_dmc_profile_read": ([_vp, _i, _vp, _vp], _i),
     "qmc_system_ewald_count": ([_vp], _i),
     "qmc_get_nonlocal": ([_vp, _vp], _i),
     "qmc_walkers_create": ([_vp, _i, _vp, C.POINTER(_vp)], _i),
@@ -351,6 +353,16 @@ class DMC:
 
     def step(self, n=1, stream=None):
         _check(load().qmc_dmc_step(self.h, int(n), _stream_ptr(stream)))
+
+    def profile(self, enable=True):
+        _check(load().qmc_dmc_profile_enable(self.h, int(bool(enable))))
+
+    def profile_read(self, system):
+        """(ms, launches) per kernel class of one system since the last read."""
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), dtype=np.int64)
+        _check(load().qmc_dmc_profile_read(self.h, int(system), ms.ctypes.data, n.ctypes.data))
+        return ms, n
 
     def set_mode(self, effective_tau=False, reconfigure=False):
         """Effective time step in the branching factor; stochastic reconfiguration at a
