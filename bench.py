@@ -738,6 +738,8 @@ def run_dmc(args, rank, world, local_rank):
             "populations_first_last": r["populations_first_last"],
             "e_mean_last": r["e_mean_last"], "e_trial_last": r["e_trial_last"],
             "gpu_launches": r["gpu_launches"]}
+    if r.get("kernels_ms_per_step"):
+        line["kernels_ms_per_step"] = r["kernels_ms_per_step"]
     print(json.dumps(line), flush=True)
 
 
