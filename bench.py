@@ -538,6 +538,21 @@ def run_ours(args, spec, rank, world, local_rank):
                 "ms_per_step": mse / 10, "steps": 10, "alpha": alpha, "kcut": 8.0 * alpha,
                 "k_vectors": se.ewald_count, "prof": profe}
             se.close()
+        if spec.n_ion > 0:
+            # the same workload with the three-body e-e-I Jastrow factor (r_c = 5 bohr, orders
+            # M_eI = 2, M_ee = 3): every move's ratio and drift, E_L and ln|Psi| carry it
+            from synthetic import jastrow3_coefficients
+            sj = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
+                                      prop_chunk=args.prop_chunk, reinv_period=args.reinv_period,
+                                      logdet_period=logdet_period)
+            gs, go = jastrow3_coefficients(2, 3, J3_RCUT, seed=5)
+            sj.set_jastrow3(gs, go, J3_RCUT)
+            msj, profj, _, _, _ = timed(sj, 10, args.warmup, profile=True)
+            sj.close()
+            extras["jastrow3"] = {
+                "value": whole_job_rate(world, moves_per_step * 10, msj / 1e3), "unit": UNIT,
+                "ms_per_step": msj / 10, "steps": 10, "rcut": J3_RCUT, "orders": [2, 3],
+                "prof": profj}
         extras["dmc"] = dmc_measure(args, rank, world, 10, dist)
 
     if rank != 0:
@@ -571,6 +586,10 @@ def run_ours(args, spec, rank, world, local_rank):
                                       f"per electron-ion pair inside the cutoff"}
         if nl["roofline"]["achieved"]:
             nl["roofline"]["frac"] = nl["roofline"]["achieved"] / nl["roofline"]["peak"]
+    if extras is not None and "jastrow3" in extras:
+        pm, pn = extras["jastrow3"].pop("prof")
+        extras["jastrow3"]["kernels"] = {n: float(pm[i]) / 10
+                                         for i, n in enumerate(qb.KERNEL_CLASSES) if pn[i]}
     if extras is not None and "ewald" in extras:
         pm, pn = extras["ewald"].pop("prof")
         ix = qb.KERNEL_CLASSES.index("ewald")
@@ -618,6 +637,9 @@ DMC_SYSTEMS = ("dmc64", "dmc192", "dmc384")
 
 # synthetic non-local channels of the pseudopotential extra: s and p, Gaussian, cutoff 1.6 bohr
 NL_AMP, NL_WIDTH, NL_RCUT = [1.5, -1.0], [1.0, 0.9], 1.6
+
+# the three-body Jastrow extra's cutoff (bohr): r_c / 2 = 2.5 bohr spheres about the ions
+J3_RCUT = 5.0
 
 
 def nl_pairs(pos, ions, L, rcut):
