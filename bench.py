@@ -213,18 +213,18 @@ def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
 N_SM, FP32_LANES = 152, 128        # GB300: SMs and FP32 lanes per SM
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of each kernel
-# class, from ncu captures of the 512-electron FP32 workload at 200 walkers (the kernel
-# summaries committed beside this file), scaled to a full launch by the units it
-# processes: [(bytes per unit, unit, delay rank of the capture or None where the kernel does
-# not depend on it)]. A k-dependent entry is used only at its own k.
+# class, from ncu captures of the 512-electron FP32 workload at 256 walkers, k = 32 (the kernel
+# summaries committed beside this file), scaled to a full launch by the units it processes:
+# [(bytes per unit, unit, delay rank of the capture or None where the kernel does not depend
+# on it)]. A k-dependent entry is used only at its own k.
 TRAFFIC_SJ512_FP32 = {
-    "vgl": [(2.645e9 / 51200, "move", None)],      # k_vgl_proposals: 51,200 moves per launch
-    "sweep": [(37.585e6 / 6400, "move", 32)],      # k_sweep_win: 32 moves x 200 walkers
-    "flush": [(62.85e6 / 200, "walker", 16),       # k_flush_tc<16>: one spin block of 200 walkers
-              (67.978e6 / 200, "walker", 32)],     # k_flush_tc<32>
-    "refine": [(186.2e6 / 200, "walker", None)],   # k_refine_residual_tc
-    "refine_update": [(174.4e6 / 200, "walker", None)],  # k_refine_update_tc
-    "energy": [(530.1e6 / 200, "walker", None)],   # k_local_energy
+    "vgl": [((3019.3e6 + 363.2e6) / 65536, "move", None)],   # k_vgl_proposals: 65,536 moves
+    "sweep": [((46.3e6 + 7.1e6) / 8192, "move", 32)],         # k_sweep_win: 32 moves x 256 walkers
+    "flush": [((80.9e6 + 6.6e6) / 256, "walker", 32)],        # k_flush_tc<32>: one spin block
+    "refine": [((227.6e6 + 47.8e6) / 256, "walker", None)],   # k_refine_residual_tc
+    "refine_update": [((218.1e6 + 45.4e6) / 256, "walker", None)],   # k_refine_update_tc
+    "energy": [((674.4e6 + 3.3e6) / 256, "walker", None)],    # k_local_energy
+    "logdet": [((234.2e6 + 166.1e6) / 256, "walker", None)],  # k_logdet_anchor
 }
 
 
@@ -316,7 +316,7 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
             per_unit, unit, kcap = t
             units = moves if unit == "move" else spec.n_walkers
             out["traffic"] = per_unit * units
-            out["traffic_note"] = (f"ncu DRAM bytes per {unit} at 200 walkers"
+            out["traffic_note"] = (f"ncu DRAM bytes per {unit} at 256 walkers"
                                    + (f", k = {kcap}" if kcap else "")
                                    + f", scaled to this launch's {units:.0f} {unit}s")
         out["avg_launch_ms"] = sec * 1e3

@@ -23,7 +23,7 @@ def test_sweep_rate_and_traffic_at_the_captured_rank():
     assert r["kernel"] == "k_sweep_win"
     assert r["achieved"] == pytest.approx(per_move * moves_per_launch / launch_s / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / PEAKS["hbm_gbs"])
-    assert r["traffic"] == pytest.approx(37.585e6 / 6400 * moves_per_launch)
+    assert r["traffic"] == pytest.approx((46.3e6 + 7.1e6) / 8192 * moves_per_launch)
     # captured at k = 32 only
     assert _cls("sweep", k=16)["traffic"] is None
 
@@ -31,8 +31,8 @@ def test_sweep_rate_and_traffic_at_the_captured_rank():
 def test_flush_traffic_follows_the_delay_rank():
     t16 = _cls("flush", k=16)["traffic"]
     t32 = _cls("flush", k=32)["traffic"]
-    assert t16 == pytest.approx(62.85e6 / 200 * 256)
-    assert t32 == pytest.approx(67.978e6 / 200 * 256)
+    assert t16 is None                     # captured at k = 32 only
+    assert t32 == pytest.approx((80.9e6 + 6.6e6) / 256 * 256)
     assert _cls("flush", k=8)["traffic"] is None
 
 
