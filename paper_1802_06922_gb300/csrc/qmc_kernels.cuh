@@ -179,8 +179,19 @@ __global__ void __launch_bounds__(256, sizeof(TT) == 8 ? 1 : 2) k_vgl_proposals(
 // FP64 Gauss-Jordan inversion with partial pivoting of M (n x n, row-major, global),
 // in place, by one thread block. Returns false on an exactly zero or non-finite pivot.
 // ln|det M| and its sign are accumulated from the pivots and row interchanges.
+//
+// The pivots are taken b at a time. Within a panel of b pivot columns, those columns are kept
+// current in shared memory (Cur) and updated by every step as in plain Gauss-Jordan; each
+// other element is left in M and represented as M[i][j] - sum_s F[i][s] H[s][j], with F[i][s]
+// the multiplier of row i at step s (its panel column value then) and H[s] the pivot row of
+// step s divided by its pivot. A pivot row's stored values become its H row and its earlier
+// multipliers zero, so the one formula holds for every row. One pass per panel then applies
+// the rank-b update, instead of one pass over the whole matrix per pivot: the matrix crosses
+// L2 n/b times instead of n times, and the FP64 arithmetic becomes the bound.
 // =============================================================================
-static __device__ bool gj_invert_fp64(double* __restrict__ M, int n, double* colk, int* perm,
+// One pivot per pass, with O(n) shared memory: the form the sweep kernel's in-kernel
+// re-inversion uses inside its own shared-memory budget.
+static __device__ bool gj_invert_fp64_plain(double* __restrict__ M, int n, double* colk, int* perm,
                                double* redv, int* redi, double& logdet, double& sign) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -253,12 +264,149 @@ static __device__ bool gj_invert_fp64(double* __restrict__ M, int n, double* col
   return ok;
 }
 
+__host__ __device__ inline int gj_panel_width(int n) { return n <= 512 ? 8 : 4; }
+__host__ __device__ inline size_t gj_smem_bytes(int n) {
+  const size_t b = gj_panel_width(n);
+  return sizeof(double) * (32 + 3 * (size_t)n * b) + sizeof(int) * ((size_t)n + 32);
+}
+
+static __device__ bool gj_invert_fp64(double* __restrict__ M, int n, char* smem, double& logdet,
+                                      double& sign) {
+  const int b = gj_panel_width(n);
+  double* redv = reinterpret_cast<double*>(smem);    // [32] pivot search, one per warp
+  double* Cur = redv + 32;                            // [n][b] the panel's columns, current
+  double* F = Cur + (size_t)n * b;                    // [n][b] multipliers of the panel's steps
+  double* H = F + (size_t)n * b;                      // [b][n] scaled pivot rows
+  int* perm = reinterpret_cast<int*>(H + (size_t)b * n);   // [n] pivot row of each step
+  int* redi = perm + n;                               // [32]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double ld = 0.0, sg = 1.0;
+  bool ok = true;
+  for (int k0 = 0; k0 < n && ok; k0 += b) {
+    const int bb = min(b, n - k0);
+    for (int i = tid; i < n * bb; i += nt) {
+      const int r = i / bb, t = i - r * bb;
+      Cur[r * b + t] = M[(size_t)r * n + k0 + t];
+      F[r * b + t] = 0.0;
+    }
+    __syncthreads();
+    for (int s = 0; s < bb; ++s) {
+      const int k = k0 + s;
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + tid; i < n; i += nt) {
+        const double a = fabs(Cur[i * b + s]);
+        if (a > best) { best = a; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+      __syncthreads();
+      best = redv[0];
+      bi = redi[0];
+      for (int w = 1; w < nw; ++w)
+        if (redv[w] > best || (redv[w] == best && redi[w] < bi)) { best = redv[w]; bi = redi[w]; }
+      const double pv = Cur[bi * b + s];
+      __syncthreads();
+      if (!(pv != 0.0) || !isfinite(pv)) { ok = false; break; }   // uniform across the block
+      if (bi != k) {
+        for (int j = tid; j < n; j += nt) {
+          const double a = M[(size_t)k * n + j];
+          M[(size_t)k * n + j] = M[(size_t)bi * n + j];
+          M[(size_t)bi * n + j] = a;
+        }
+        if (tid < bb) {
+          double a = Cur[k * b + tid];
+          Cur[k * b + tid] = Cur[bi * b + tid];
+          Cur[bi * b + tid] = a;
+          a = F[k * b + tid];
+          F[k * b + tid] = F[bi * b + tid];
+          F[bi * b + tid] = a;
+        }
+        sg = -sg;
+      }
+      if (tid == 0) {
+        perm[k] = bi;
+        ld += log(fabs(pv));
+      }
+      if (pv < 0) sg = -sg;
+      __syncthreads();
+      // the pivot row, current and divided by the pivot
+      const double pinv = 1.0 / pv;
+      for (int j = tid; j < n; j += nt) {
+        double v;
+        if (j >= k0 && j < k0 + bb) {
+          v = Cur[k * b + (j - k0)];
+        } else {
+          v = M[(size_t)k * n + j];
+          for (int u = 0; u < s; ++u) v -= F[k * b + u] * H[(size_t)u * n + j];
+        }
+        H[(size_t)s * n + j] = v * pinv;
+      }
+      __syncthreads();
+      // the panel's columns: one plain Gauss-Jordan step; the multipliers of this step
+      for (int i = tid; i < n; i += nt) {
+        if (i == k) continue;
+        const double f = Cur[i * b + s];
+        for (int t = 0; t < bb; ++t)
+          Cur[i * b + t] = (t == s) ? -f * pinv : Cur[i * b + t] - f * H[(size_t)s * n + k0 + t];
+        F[i * b + s] = f;
+      }
+      if (tid < bb) Cur[k * b + tid] = (tid == s) ? pinv : H[(size_t)s * n + k0 + tid];
+      if (tid <= s) F[k * b + tid] = 0.0;
+      for (int j = tid; j < n; j += nt)
+        if (j < k0 || j >= k0 + bb) M[(size_t)k * n + j] = H[(size_t)s * n + j];
+      __syncthreads();
+    }
+    if (!ok) break;
+    // the rank-bb update of every other column, and the panel's columns written back
+    for (int i = warp; i < n; i += nw) {
+      double f[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) f[t] = t < bb ? F[i * b + t] : 0.0;
+      double* row = M + (size_t)i * n;
+      for (int j = lane; j < n; j += 32) {
+        if (j >= k0 && j < k0 + bb) {
+          row[j] = Cur[i * b + (j - k0)];
+        } else {
+          double v = row[j];
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            if (t < bb) v -= f[t] * H[(size_t)t * n + j];
+          row[j] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = perm[k];
+      if (p != k)
+        for (int i = tid; i < n; i += nt) {
+          const double a = M[(size_t)i * n + k];
+          M[(size_t)i * n + k] = M[(size_t)i * n + p];
+          M[(size_t)i * n + p] = a;
+        }
+      __syncthreads();
+    }
+  }
+  logdet = ld;   // valid in thread 0
+  sign = sg;
+  return ok;
+}
+
 // Re-inversion of one spin block of walker w from the orbital values at the current
 // positions: M = A^T (M[j][e] = phi_j(r_e)), so M^-1 = (A^-1)^T = Binv. Writes Binv in
 // working precision, ln|det A| and its sign. Called by one whole block.
 template <class TW>
 __device__ void reinvert_block(const SysParams& S, const WalkParams& Wk, int w, int spin,
-                               double* colk, int* perm, double* redv, int* redi) {
+                               char* smem) {
   const int ns = spin ? S.n_dn : S.n_up;
   if (ns == 0) return;
   const int first = spin ? S.n_up : 0;
@@ -271,7 +419,7 @@ __device__ void reinvert_block(const SysParams& S, const WalkParams& Wk, int w, 
   }
   __syncthreads();
   double ld, sg;
-  const bool ok = gj_invert_fp64(M, ns, colk, perm, redv, redi, ld, sg);
+  const bool ok = gj_invert_fp64(M, ns, smem, ld, sg);
   TW* B = binv_block<TW>(S, Wk, w, spin);
   if (ok)
     for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) B[i] = (TW)M[i];
@@ -286,19 +434,45 @@ __device__ void reinvert_block(const SysParams& S, const WalkParams& Wk, int w, 
   __syncthreads();
 }
 
-__host__ __device__ inline size_t reinvert_smem_bytes(int ld_v) {
-  return sizeof(double) * (ld_v + 32) + sizeof(int) * (ld_v + 32);
+// The same with the one-pivot-per-pass inversion in the caller's small work arrays (the sweep
+// kernel's in-kernel re-inversion).
+template <class TW>
+__device__ void reinvert_block_plain(const SysParams& S, const WalkParams& Wk, int w, int spin,
+                                     double* colk, int* perm, double* redv, int* redi) {
+  const int ns = spin ? S.n_dn : S.n_up;
+  if (ns == 0) return;
+  const int first = spin ? S.n_up : 0;
+  const size_t msz = (size_t)Wk.ld_v * Wk.ld_v;
+  double* M = Wk.scratch64 + (size_t)(2 * w + spin) * msz;   // one work matrix per (walker, spin)
+  const TW* VG = static_cast<const TW*>(Wk.vgl) + (size_t)w * S.n_e * 5 * Wk.ld_v;
+  for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) {
+    const int j = i / ns, e = i % ns;
+    M[i] = (double)VG[(size_t)(first + e) * 5 * Wk.ld_v + j];
+  }
+  __syncthreads();
+  double ld, sg;
+  const bool ok = gj_invert_fp64_plain(M, ns, colk, perm, redv, redi, ld, sg);
+  TW* B = binv_block<TW>(S, Wk, w, spin);
+  if (ok)
+    for (int i = threadIdx.x; i < ns * ns; i += blockDim.x) B[i] = (TW)M[i];
+  if (threadIdx.x == 0) {
+    if (ok) {
+      Wk.logdet[2 * w + spin] = ld;
+      Wk.sgn[2 * w + spin] = sg;
+    } else {
+      atomicOr(Wk.err, kErrSingular);
+    }
+  }
+  __syncthreads();
 }
+
+__host__ __device__ inline size_t reinvert_smem_bytes(int ld_v) { return gj_smem_bytes(ld_v); }
 
 template <class TW>
 __global__ void __launch_bounds__(256) k_reinvert(SysParams S, WalkParams Wk) {
   extern __shared__ __align__(16) char smem_r[];
   const int w = blockIdx.x >> 1, spin = blockIdx.x & 1;
-  double* colk = reinterpret_cast<double*>(smem_r);
-  double* redv = colk + Wk.ld_v;
-  int* perm = reinterpret_cast<int*>(redv + 32);
-  int* redi = perm + Wk.ld_v;
-  reinvert_block<TW>(S, Wk, w, spin, colk, perm, redv, redi);
+  reinvert_block<TW>(S, Wk, w, spin, smem_r);
 }
 
 // Batched FP64 re-inversion of caller-supplied Slater matrices (one block per matrix):
@@ -311,10 +485,6 @@ __global__ void __launch_bounds__(256) k_invert_batch(const T* __restrict__ A, T
                                                      double* __restrict__ sign, int n,
                                                      double* __restrict__ work) {
   extern __shared__ __align__(16) char smem_i[];
-  double* colk = reinterpret_cast<double*>(smem_i);
-  double* redv = colk + n;
-  int* perm = reinterpret_cast<int*>(redv + 32);
-  int* redi = perm + n;
   const size_t nn = (size_t)n * n;
   const int b = blockIdx.x;
   double* M = work + (size_t)b * nn;
@@ -325,7 +495,7 @@ __global__ void __launch_bounds__(256) k_invert_batch(const T* __restrict__ A, T
   }
   __syncthreads();
   double ld, sg;
-  const bool ok = gj_invert_fp64(M, n, colk, perm, redv, redi, ld, sg);
+  const bool ok = gj_invert_fp64(M, n, smem_i, ld, sg);
   T* Bb = Binv + (size_t)b * nn;
   for (size_t i = threadIdx.x; i < nn; i += blockDim.x) Bb[i] = ok ? (T)M[i] : T(0);
   if (threadIdx.x == 0) {
@@ -334,9 +504,7 @@ __global__ void __launch_bounds__(256) k_invert_batch(const T* __restrict__ A, T
   }
 }
 
-__host__ __device__ inline size_t invert_batch_smem_bytes(int n) {
-  return sizeof(double) * (n + 32) + sizeof(int) * (n + 32);
-}
+__host__ __device__ inline size_t invert_batch_smem_bytes(int n) { return gj_smem_bytes(n); }
 
 // =============================================================================
 // Re-inversion of the single-precision forms by one Newton step with an accurate residual.
@@ -1233,7 +1401,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
           full = !(refine_inverse(S, Wk, w, spin, sm.tile, reinterpret_cast<float*>(sm.red)) <= kRefineMax);
         }
         if (full) {
-          reinvert_block<TW>(S, Wk, w, spin, sm.colk, sm.perm, sm.redv, sm.redi);
+          reinvert_block_plain<TW>(S, Wk, w, spin, sm.colk, sm.perm, sm.redv, sm.redi);
           if (tid == 0) {
             logdet = Wk.logdet[2 * w + spin];
             sgn = Wk.sgn[2 * w + spin];
@@ -1401,13 +1569,7 @@ __global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
   const float rm = Wk.refine_max[2 * w + spin];
-  if (!(rm <= kRefineMax)) {
-    double* colk = reinterpret_cast<double*>(smem_c);
-    double* redv = colk + Wk.ld_v;
-    int* perm = reinterpret_cast<int*>(redv + 32);
-    int* redi = perm + Wk.ld_v;
-    reinvert_block<TW>(S, Wk, w, spin, colk, perm, redv, redi);
-  }
+  if (!(rm <= kRefineMax)) reinvert_block<TW>(S, Wk, w, spin, smem_c);
   if (threadIdx.x == 0) {
     Wk.refine_last[2 * w + spin] = rm;
     Wk.refine_max[2 * w + spin] = 0.f;

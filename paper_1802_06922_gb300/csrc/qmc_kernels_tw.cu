@@ -12,7 +12,10 @@ namespace {
 
 template <class TW>
 cudaError_t reinvert(const SysParams& S, const WalkParams& W, cudaStream_t st) {
-  k_reinvert<TW><<<2 * W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W);
+  const size_t smem = reinvert_smem_bytes(W.ld_v);
+  cudaError_t e = cudaFuncSetAttribute(k_reinvert<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_reinvert<TW><<<2 * W.n_w, kThreads, smem, st>>>(S, W);
   return cudaGetLastError();
 }
 
@@ -91,7 +94,10 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
     }
     if (part == 2) {
       // after the buffer swap: FP64 re-inversion of the walkers whose residual was too large
-      k_refine_fallback<TW><<<W.n_w, kThreads, reinvert_smem_bytes(W.ld_v), st>>>(S, W, spin);
+      const size_t smem = reinvert_smem_bytes(W.ld_v);
+      cudaError_t e = cudaFuncSetAttribute(k_refine_fallback<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_refine_fallback<TW><<<W.n_w, kThreads, smem, st>>>(S, W, spin);
       return cudaGetLastError();
     }
     if (ns > kRsMaxK) {
@@ -144,7 +150,10 @@ cudaError_t local_energy(const SysParams& S, const WalkParams& W, cudaStream_t s
 template <class TW>
 cudaError_t invert_batch(const void* A, void* Binv, double* logdet, double* sign, int n,
                          int batch, double* work, cudaStream_t st) {
-  k_invert_batch<TW><<<batch, kThreads, invert_batch_smem_bytes(n), st>>>(
+  const size_t smem = invert_batch_smem_bytes(n);
+  cudaError_t e = cudaFuncSetAttribute(k_invert_batch<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_invert_batch<TW><<<batch, kThreads, smem, st>>>(
       static_cast<const TW*>(A), static_cast<TW*>(Binv), logdet, sign, n, work);
   return cudaGetLastError();
 }

@@ -11,7 +11,7 @@ if not torch.cuda.is_available():
 from paper_1802_06922_gb300 import qmcgb as q   # noqa: E402
 
 
-@pytest.mark.parametrize("n", [1, 7, 70, 257])
+@pytest.mark.parametrize("n", [1, 7, 8, 9, 70, 257, 520])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_invert_matches_lapack(n, dtype):
     rng = np.random.default_rng(n)
