@@ -46,6 +46,10 @@ def parse_args():
     p.add_argument("--prop-chunk", type=int, default=None,
                    help="Metropolis moves per proposal batch (0 = the whole spin block); "
                         "tuned with the delay rank when --delay-k is auto")
+    p.add_argument("--prop-blocks", type=int, default=None,
+                   help="grid cap of the proposal gather that runs beside the other spin "
+                        "block's moves (0 = a full grid); tuned with the delay rank when "
+                        "--delay-k is auto")
     p.add_argument("--reinv-period", type=int, default=128)
     p.add_argument("--logdet-period", type=int, default=1024,
                    help="moves of a spin block between log-determinant anchors (a multiple of "
@@ -85,11 +89,14 @@ def system_desc(spec):
 
 
 def workload(spec, precision, delay_k, reinv_period, on_accepted=False, logdet_period=0,
-             prop_chunk=0):
+             prop_chunk=0, prop_blocks=0):
     tab = {"fp32": "FP32", "bf16": "BF16", "fp64": "FP64"}[precision]
     upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
     if prop_chunk:
         upd += f" (proposals in batches of {prop_chunk} moves)"
+    elif delay_k >= 4 and precision != "fp64" and not on_accepted:
+        upd += (" (each spin block's proposals formed beside the other block's moves"
+                + (f" by a {prop_blocks}-block gather)" if prop_blocks else ")"))
     what = "accepted moves" if on_accepted else "moves"
     re = (("FP64 re-inversion" if precision == "fp64" else "re-inversion (error-free Newton step)")
           + f" every {reinv_period} {what}") if reinv_period else "no re-inversion"
@@ -370,7 +377,9 @@ def run_ours(args, spec, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     moves_per_step = spec.n_walkers * spec.n_elec
 
-    def timed(system, n_steps, n_warm, profile=False):
+    def timed(system, n_steps, n_warm, profile=False, sample_clocks=False):
+        """ms of n_steps sweeps after n_warm. Without `profile`, every sweep is one CUDA-graph
+        replay; with it, direct launches each bracketed by CUDA events (per-class times)."""
         w = q.Walkers(system, pos)
         for _ in range(n_warm):
             w.sweep(1, stream)
@@ -378,8 +387,8 @@ def run_ours(args, spec, rank, world, local_rank):
         l0 = w.launch_count()
         if profile:
             w.profile(True)
-        sampler = ClockSampler(local_rank) if profile else None
-        time.sleep(0.3 if profile else 0.0)
+        sampler = ClockSampler(local_rank) if sample_clocks else None
+        time.sleep(0.3 if sample_clocks else 0.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -397,30 +406,45 @@ def run_ours(args, spec, rank, world, local_rank):
         ms = max_over_ranks(ms, dist)
         return ms, prof, launches, clocks, e_loc
 
+    def timed_extra(system, n_steps, n_warm):
+        """ms of graph-replayed sweeps, then the per-class times of a profiled pass."""
+        ms_g = timed(system, n_steps, n_warm)[0]
+        return ms_g, timed(system, n_steps, n_warm, profile=True)[1]
+
     tuning = None
     if args.delay_k == "auto":
-        (k_best, c_best), t_times = q.tune_launch(inputs, pos, delays=(8, 16, 32),
-                                                  precision=args.precision,
-                                                  reinv_period=args.reinv_period,
-                                                  reinv_on_accepted=args.reinv_on_accepted)
+        (k_best, c_best, g_best), t_times = q.tune_launch(inputs, pos, delays=(8, 16, 32),
+                                                          precision=args.precision,
+                                                          reinv_period=args.reinv_period,
+                                                          reinv_on_accepted=args.reinv_on_accepted)
         args.delay_k = k_best
         if args.prop_chunk is None:
             args.prop_chunk = c_best
-        tuning = {"candidates_ms_per_sweep": {f"k={k},batch={c or 'block'}": round(v, 3)
-                                              for (k, c), v in t_times.items()},
-                  "chosen": {"delay_k": k_best, "proposal_batch": c_best}}
+            if args.prop_blocks is None:
+                args.prop_blocks = g_best
+        tuning = {"candidates_ms_per_sweep": {
+                      f"k={k},batch={c or 'block'}" + (f",gather_blocks={g}" if g else ""): round(v, 3)
+                      for (k, c, g), v in t_times.items()},
+                  "chosen": {"delay_k": k_best, "proposal_batch": c_best,
+                             "gather_blocks": g_best}}
     else:
         args.delay_k = int(args.delay_k)
     if args.prop_chunk is None:
         args.prop_chunk = 0
+    if args.prop_blocks is None:
+        args.prop_blocks = 0
     logdet_period = 0 if (args.reinv_on_accepted or args.precision == "fp64") else args.logdet_period
     sysm = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                prop_chunk=args.prop_chunk,
+                                prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
                                 reinv_period=args.reinv_period,
                                 reinv_on_accepted=args.reinv_on_accepted,
                                 logdet_period=logdet_period)
-    ms, prof, launches, clocks, e_loc = timed(sysm, args.steps, args.warmup, profile=True)
+    # the headline: every sweep one CUDA-graph replay, no per-kernel events
+    ms, _, launches, clocks, e_loc = timed(sysm, args.steps, args.warmup, sample_clocks=True)
     value = whole_job_rate(world, moves_per_step * args.steps, ms / 1e3)
+    # the per-class breakdown behind the roofline fields: the same sweeps by direct launches,
+    # each bracketed by CUDA events on the launching stream
+    ms_prof, prof, _, _, _ = timed(sysm, args.steps, args.warmup, profile=True)
 
     # end to end through the public API with pinned host buffers: walker creation from
     # host positions, every sweep followed by a device->host read of E_L and ln|Psi|,
@@ -484,23 +508,24 @@ def run_ours(args, spec, rank, world, local_rank):
     if not args.no_extras and world == 1:
         extras = {}
         sb = q.system_from_inputs(inputs, precision="bf16", delay_k=args.delay_k,
-                                  prop_chunk=args.prop_chunk,
+                                  prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
                                   reinv_period=args.reinv_period, logdet_period=logdet_period)
-        msb, profb, _, _, _ = timed(sb, 10, args.warmup, profile=True)
+        msb, profb = timed_extra(sb, 10, args.warmup)
         sb.close()
         vb = whole_job_rate(world, moves_per_step * 10, msb / 1e3)
         extras["bf16_table"] = {"value": vb, "unit": UNIT, "ms_per_step": msb / 10, "steps": 10,
                                 "workload": workload(spec, "bf16", args.delay_k, args.reinv_period,
-                                                     logdet_period=logdet_period, prop_chunk=args.prop_chunk),
+                                                     logdet_period=logdet_period, prop_chunk=args.prop_chunk,
+                                                     prop_blocks=args.prop_blocks),
                                 "prof": profb}
         if args.reinv_period > 0 and logdet_period != args.reinv_period and args.precision != "fp64":
             # the log-determinant anchor at every re-inversion (the 128-move cadence the
             # 512-electron workload names for re-inversion and log-det)
             sa = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk,
+                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
                                       reinv_period=args.reinv_period,
                                       logdet_period=args.reinv_period)
-            msa, profa, _, _, _ = timed(sa, 10, args.warmup, profile=True)
+            msa, profa = timed_extra(sa, 10, args.warmup)
             sa.close()
             extras["anchor_every_reinversion"] = {
                 "value": whole_job_rate(world, moves_per_step * 10, msa / 1e3), "unit": UNIT,
@@ -510,10 +535,10 @@ def run_ours(args, spec, rank, world, local_rank):
             # the same workload with non-local pseudopotential channels on every ion: the
             # 12-point quadrature's virtual moves are measured after every sweep
             sn = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk,
+                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
                                       reinv_period=args.reinv_period, logdet_period=logdet_period)
             sn.set_nonlocal(NL_AMP, NL_WIDTH, NL_RCUT)
-            msn, profn, _, _, _ = timed(sn, 10, args.warmup, profile=True)
+            msn, profn = timed_extra(sn, 10, args.warmup)
             wn = q.Walkers(sn, pos)
             wn.sweep(1)
             pairs = nl_pairs(wn.positions(), inputs["ions"], spec.L, NL_RCUT)
@@ -528,11 +553,11 @@ def run_ours(args, spec, rank, world, local_rank):
             # the same workload with Coulomb interactions by Ewald summation in place of the
             # Yukawa form: erfc(alpha L / 2) = erfc(4) and exp(-kcut^2 / (4 alpha^2)) = e^-16
             se = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk,
+                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
                                       reinv_period=args.reinv_period, logdet_period=logdet_period)
             alpha = 8.0 / spec.L
             se.set_ewald(alpha, 8.0 * alpha)
-            mse, profe, _, _, _ = timed(se, 10, args.warmup, profile=True)
+            mse, profe = timed_extra(se, 10, args.warmup)
             extras["ewald"] = {
                 "value": whole_job_rate(world, moves_per_step * 10, mse / 1e3), "unit": UNIT,
                 "ms_per_step": mse / 10, "steps": 10, "alpha": alpha, "kcut": 8.0 * alpha,
@@ -543,11 +568,11 @@ def run_ours(args, spec, rank, world, local_rank):
             # M_eI = 2, M_ee = 3): every move's ratio and drift, E_L and ln|Psi| carry it
             from synthetic import jastrow3_coefficients
             sj = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk, reinv_period=args.reinv_period,
+                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks, reinv_period=args.reinv_period,
                                       logdet_period=logdet_period)
             gs, go = jastrow3_coefficients(2, 3, J3_RCUT, seed=5)
             sj.set_jastrow3(gs, go, J3_RCUT)
-            msj, profj, _, _, _ = timed(sj, 10, args.warmup, profile=True)
+            msj, profj = timed_extra(sj, 10, args.warmup)
             sj.close()
             extras["jastrow3"] = {
                 "value": whole_job_rate(world, moves_per_step * 10, msj / 1e3), "unit": UNIT,
@@ -618,14 +643,20 @@ def run_ours(args, spec, rank, world, local_rank):
             "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload(spec, args.precision, args.delay_k, args.reinv_period,
-                                            args.reinv_on_accepted, logdet_period, args.prop_chunk),
+                                            args.reinv_on_accepted, logdet_period, args.prop_chunk,
+                                            args.prop_blocks),
                        "walkers_per_gpu": spec.n_walkers, "electrons": spec.n_elec,
                        "moves_per_step": moves_per_step * world,
                        "l2": f"inputs larger than L2: {table_bytes(spec, args.precision) / 1e6:.0f} MB "
                              f"coefficient table gathered at random",
                        "parallelism": f"replicas x{world}",
                        "delay_k_autotune": tuning},
-            "roofline": roof, "gpu_launches": launches, "kernels": kernels, "clocks": clocks,
+            "roofline": roof, "gpu_launches": launches, "kernels": kernels,
+            "kernels_note": "per-class times from a second timed pass of the same sweeps by "
+                            "direct launches bracketed by CUDA events ("
+                            f"{ms_prof / args.steps:.3f} ms per step); the headline pass "
+                            "replays each sweep as one CUDA graph",
+            "clocks": clocks,
             "e2e": e2e, "e2e_steady": e2e_steady, "cpu_baseline": cpu, "fp64_form": fp64,
             "measured_rates": rates, "extras": extras,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
@@ -656,9 +687,9 @@ def nl_pairs(pos, ions, L, rcut):
 def dmc_measure(args, rank, world, n_steps, dist=None):
     """Batched uneven DMC: three systems advance together each step (drift-diffusion sweep
     with the drift rescaled near nodes, local energy, branching with the effective time step,
-    compaction; one stream per system). moves/s counts sum_s N_e(s) * N_w(s, step) over the
-    timed steps, each step bracketed by CUDA events on the caller's stream (the systems'
-    streams join it). Returns the measurement as a dictionary (every rank)."""
+    compaction), each step one CUDA graph over the systems. moves/s counts
+    sum_s N_e(s) * N_w(s, step) over the timed steps, each step bracketed by CUDA events on
+    the caller's stream. Returns the measurement as a dictionary (every rank)."""
     import numpy as np
     import torch
     import paper_1802_06922_gb300 as q
@@ -731,8 +762,8 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
             + f"; drift-diffusion tau={specs[0].step} with nodal drift rescaling (a = 1), "
               f"branching with the effective time step, E_T feedback, delayed rank-{dmc_k}, "
               f"re-inversion every {args.reinv_period} moves; walkers equilibrated by "
-              f"{args.dmc_vmc_sweeps} VMC sweeps, E_T from their median E_L; systems on "
-              f"concurrent streams",
+              f"{args.dmc_vmc_sweeps} VMC sweeps, E_T from their median E_L; each step one "
+              f"CUDA graph over the three systems (captured on one stream per system)",
             "populations_first_last": [pops[0], pops[-1]],
             "kernels_ms_per_step": prof,
             "e_mean_last": [float(x["e_mean"]) for x in final],

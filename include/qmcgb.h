@@ -118,12 +118,19 @@ typedef struct {
                               one launch pair, per spin block (0 = the whole block); smaller
                               batches keep the rows in L2 until the sweep reads them. A
                               launch parameter only: the chain does not depend on it. */
+  int prop_blocks;         /* With whole-block batches of Metropolis moves in the batched
+                              delayed update (delay_k >= 4, windows flushed between launches),
+                              one spin block's proposal rows are formed on a second stream
+                              while the other block moves; prop_blocks > 0 caps
+                              that gather's grid (thread blocks of 256 threads that loop over
+                              the work), so that it shares HBM with the moves instead of
+                              saturating it; 0 = a full grid. A launch parameter only. */
 } qmc_system_desc;
 
 /* Creates a system. Fails with QMC_EINVAL for n_up or n_dn outside [0, 1024], n_up+n_dn
  * = 0, L <= 0, step < 0, delay_k outside [1, 64], an unknown precision/move, a
  * logdet_period that is negative or not a multiple of a positive reinv_period, or a negative
- * prop_chunk. */
+ * prop_chunk or prop_blocks. */
 qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out);
 
 /* Sets the B-spline orbital table (Sec. "B-spline basis sets"). coef is host memory
@@ -416,6 +423,27 @@ qmc_status qmc_profile_read(qmc_walkers_t w, double* ms, int64_t* launches);
 
 /* Number of kernel launches the library enqueued since the walker set was created. */
 int64_t qmc_launch_count(qmc_walkers_t w);
+
+/* CUDA-graph replay of sweeps (no counterpart in the paper, which launches per move or per
+ * batch; the persistent-launch batching of many walkers it motivates). On by default. With
+ * it on, each sweep of qmc_sweep (and each step of qmc_dmc_step, over all of the driver's
+ * systems) that is neither traced, replayed from decisions nor profiled runs as one CUDA
+ * graph launched on the caller's stream, after one kernel that writes the sweep index to a
+ * device word the graph's kernels read. A graph is captured, without running, the first time
+ * a sweep starts from a given host state (system parameters, launch configuration, the walker
+ * set's buffer assignment and its move counts since the last re-inversion and log-det
+ * anchor) and is kept, up to 16 per walker set or driver, least recently used replaced;
+ * a change of the Hamiltonian or of the launch configuration changes that state. The results
+ * are identical bit for bit to those of direct launches. qmc_launch_count counts the graphs'
+ * kernels and the index-setting kernel.
+ *   qmc_graph_enable / qmc_dmc_graph_enable: enable != 0 turns replay on, 0 off (the kept
+ *       graphs stay until destroy).
+ *   qmc_graph_stats / qmc_dmc_graph_stats: captures and replays so far (either may be NULL).
+ * QMC_EINVAL for a NULL handle. */
+qmc_status qmc_graph_enable(qmc_walkers_t w, int enable);
+qmc_status qmc_graph_stats(qmc_walkers_t w, int64_t* captures, int64_t* replays);
+qmc_status qmc_dmc_graph_enable(qmc_dmc_t d, int enable);
+qmc_status qmc_dmc_graph_stats(qmc_dmc_t d, int64_t* captures, int64_t* replays);
 
 void qmc_walkers_destroy(qmc_walkers_t w);
 void qmc_system_destroy(qmc_system_t sys);

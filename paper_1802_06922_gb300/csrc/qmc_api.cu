@@ -75,6 +75,7 @@ struct qmc_system_s {
   double* d_ions = nullptr;
   float* d_ionsf = nullptr;
   uint64_t ham_version = 0;    // bumped by every change of the Hamiltonian's terms
+  uint64_t table_version = 0;  // bumped by every new orbital table
   double* d_j3 = nullptr;      // three-body Jastrow coefficients [2][n_coef]
   int4* d_ew_n = nullptr;      // Ewald half set of integer k vectors
   double* d_ew = nullptr;      // c_k [n_k], the ions' rho_k [2][n_k], constant [1]
@@ -83,6 +84,65 @@ struct qmc_system_s {
   const TtLaunch* tt = nullptr;
 };
 
+namespace {
+// Sweeps (and DMC steps) replayed as CUDA graphs. The launches of a sweep follow from host
+// state alone: the system's parameters, the launch configuration, the walker set's device
+// pointers (which the refinements' buffer swaps permute) and its counts of moves since the
+// last re-inversion and log-det anchor. That state, byte for byte, keys a captured graph;
+// `post` holds the state the captured sweep leaves, which a replay installs. The sweep index
+// of the Philox counters reaches the graph's kernels through a device word set before each
+// replay, so one graph serves every sweep that starts from the same state.
+using Bytes = std::vector<unsigned char>;
+
+template <class T>
+void put(Bytes& b, const T& v) {
+  const auto* p = reinterpret_cast<const unsigned char*>(&v);
+  b.insert(b.end(), p, p + sizeof(T));
+}
+
+template <class T>
+void take(const unsigned char*& p, T& v) {
+  std::memcpy(&v, p, sizeof(T));
+  p += sizeof(T);
+}
+
+struct GraphEntry {
+  Bytes key, post;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> launches;   // kernels of the graph, per walker set
+  uint64_t used = 0;
+};
+
+struct GraphCache {
+  static constexpr size_t kMaxEntries = 16;
+  std::vector<GraphEntry> entries;
+  uint64_t clock = 0;
+  int64_t captures = 0, replays = 0;
+  bool enabled = true;
+
+  GraphEntry* find(const Bytes& key) {
+    for (auto& g : entries)
+      if (g.key == key) return &g;
+    return nullptr;
+  }
+  // a free entry, or the least recently used one with its graph destroyed
+  GraphEntry& slot() {
+    if (entries.size() < kMaxEntries) return entries.emplace_back();
+    GraphEntry* lru = &entries[0];
+    for (auto& g : entries)
+      if (g.used < lru->used) lru = &g;
+    if (lru->exec) cudaGraphExecDestroy(lru->exec);
+    *lru = GraphEntry{};
+    return *lru;
+  }
+  void clear() {
+    for (auto& g : entries)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    entries.clear();
+  }
+};
+}  // namespace
+
 struct qmc_walkers_s {
   qmc_system_s* sys = nullptr;
   WalkParams W{};
@@ -90,6 +150,11 @@ struct qmc_walkers_s {
   int chunk = 0;               // moves per launch of a spin block
   void* d_P = nullptr;         // proposal orbital values [W][chunk][5][ld_v]
   Prop* d_prop = nullptr;      // [W][chunk]
+  void* d_P2 = nullptr;        // the down block's, when proposals are pipelined (whole-block
+  Prop* d_prop2 = nullptr;     // batches): formed beside the up block's moves
+  bool pf_ready = false;       // d_P / d_prop hold the up block's proposals of sweep pf_sweep
+  uint32_t pf_sweep = 0;
+  uint64_t pf_table = 0;       // the system's table version they were evaluated with
   double* d_out = nullptr;     // [8] accumulate output
   long long* d_nacc = nullptr;
   long long proposed = 0;      // since the last accumulate
@@ -104,8 +169,12 @@ struct qmc_walkers_s {
   void* d_j3vgl = nullptr;     // three-body Jastrow terms per electron [W][n_e][5] (working precision)
   cudaStream_t side = nullptr; // the up block's last refinement of a sweep runs here, beside
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // the down block's moves
+  cudaEvent_t ev_prop = nullptr;  // the down block's pipelined proposals are ready
   int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
   int since_anchor[2] = {0, 0};// proposed moves per spin since the last log-det anchor
+  GraphCache graphs;
+  cudaStream_t cap = nullptr;  // capture stream of the graphs
+  uint32_t* d_t = nullptr;     // device sweep index read by replayed graphs
   bool profiling = false;
   struct Ev { int kind; cudaEvent_t a, b; };
   std::vector<Ev> events;
@@ -168,6 +237,7 @@ extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_
   if (!(d.step >= 0.0)) return fail(QMC_EINVAL, "step must be >= 0");
   if (!(d.drift_a >= 0.0) || !std::isfinite(d.drift_a)) return fail(QMC_EINVAL, "drift_a must be >= 0");
   if (d.prop_chunk < 0) return fail(QMC_EINVAL, "prop_chunk must be >= 0");
+  if (d.prop_blocks < 0) return fail(QMC_EINVAL, "prop_blocks must be >= 0");
   if (d.delay_k < 1 || d.delay_k > kMaxDelay) return fail(QMC_EINVAL, "delay_k must be in [1, %d]", kMaxDelay);
   if (d.prec < QMC_FP64 || d.prec > QMC_FP32_BF16TAB) return fail(QMC_EINVAL, "unknown precision");
   if (d.move != QMC_MOVE_METROPOLIS && d.move != QMC_MOVE_DRIFT) return fail(QMC_EINVAL, "unknown move");
@@ -283,6 +353,7 @@ extern "C" qmc_status qmc_system_set_spline(qmc_system_t s, int nx, int ny, int 
     P.inv_deltaf[c] = (float)P.inv_delta[c];
   }
   s->has_spline = true;
+  ++s->table_version;
   return QMC_OK;
 }
 
@@ -474,7 +545,7 @@ qmc_status measure_energy(qmc_walkers_s* w, const WalkParams& W0, uint32_t t, cu
   if (s->P.nl_nch > 0 && s->P.n_ion > 0) {
     Bracket b(w, st, QMC_K_NLPP);
     QMC_CUDA(s->tt->nlpp(s->P, W, t, st));
-    w->launches += 1;
+    w->launches += 2;   // pair list, virtual moves, per-walker sums
   }
   return QMC_OK;
 }
@@ -487,6 +558,7 @@ qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
   w->since_moves[0] = w->since_moves[1] = 0;
   w->since_anchor[0] = w->since_anchor[1] = 0;
+  w->pf_ready = false;
   w->energy_valid = true;
   w->energy_version = s->ham_version;
   return check_err(w, st);
@@ -496,12 +568,18 @@ void free_walkers(qmc_walkers_s* w) {
   WalkParams& W = w->W;
   void* ptrs[] = {W.pos, W.binv[0], W.binv[1], W.binv_alt[0], W.binv_alt[1], W.vgl, W.logdet,
                   W.sgn, W.wid, W.weight, W.e_loc, W.log_psi, W.n_acc, W.acc_since, W.scratch64,
-                  W.err, w->d_P, w->d_prop, w->d_out, w->d_nacc, w->d_forced, W.win_phi,
+                  W.err, w->d_P, w->d_prop, w->d_P2, w->d_prop2, w->d_out, w->d_nacc,
+                  w->d_forced, W.win_phi,
                   W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
-                  W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count, w->d_j3vgl};
+                  W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count, W.nl_val,
+                  w->d_j3vgl};
   for (void* p : ptrs) cudaFree(p);
+  w->graphs.clear();
+  cudaFree(w->d_t);
+  if (w->cap) cudaStreamDestroy(w->cap);
   if (w->ev_fork) cudaEventDestroy(w->ev_fork);
   if (w->ev_join) cudaEventDestroy(w->ev_join);
+  if (w->ev_prop) cudaEventDestroy(w->ev_prop);
   if (w->side) cudaStreamDestroy(w->side);
 }
 
@@ -544,6 +622,9 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
   while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
   const size_t np = proposals ? nw * (size_t)w->chunk : 1;
+  // whole-block proposal batches of both spin blocks: a second buffer lets the proposals of
+  // one block be formed while the other block moves
+  const bool pipe = proposals && w->chunk >= ns_max && P.n_up > 0 && P.n_dn > 0;
   const size_t nb_up = (size_t)std::max(P.n_up, 1) * std::max(P.n_up, 1);
   const size_t nb_dn = (size_t)std::max(P.n_dn, 1) * std::max(P.n_dn, 1);
   // the second inverse buffers serve the batched single-precision re-inversion
@@ -567,6 +648,8 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.err, sizeof(int)},
       {(void**)&w->d_P, np * 5 * W.ld_v * tw},
       {(void**)&w->d_prop, np * sizeof(Prop)},
+      {(void**)&w->d_P2, pipe ? np * 5 * W.ld_v * tw : 0},
+      {(void**)&w->d_prop2, pipe ? np * sizeof(Prop) : 0},
       {(void**)&w->d_out, 8 * sizeof(double)},
       {(void**)&w->d_nacc, sizeof(long long)},
       {(void**)&W.win_phi, nw * (size_t)s->d.delay_k * W.ld_v * tw},
@@ -581,6 +664,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.vnl, nw * sizeof(double)},
       {(void**)&W.nl_pairs, nw * (size_t)std::max(64, 2 * (int)ne) * sizeof(int)},
       {(void**)&W.nl_count, nw * sizeof(int)},
+      {(void**)&W.nl_val, nw * (size_t)std::max(64, 2 * (int)ne) * sizeof(double)},
       {(void**)&W.rscale, nw * 4 * (size_t)W.ld_v * sizeof(int)},
       {(void**)&w->d_j3vgl, nw * (size_t)ne * 5 * tw},
   };
@@ -595,9 +679,17 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
                   cudaGetErrorString(e));
     }
   }
+  if (cudaMalloc(&w->d_t, sizeof(uint32_t)) != cudaSuccess) {
+    w->d_t = nullptr;
+    free_walkers(w);
+    delete w;
+    return fail(QMC_ENOMEM, "cannot allocate the walker set's sweep index");
+  }
   if (cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ev_prop, cudaEventDisableTiming) != cudaSuccess) {
     free_walkers(w);
     delete w;
     return fail(QMC_ECUDA, "cannot create the walker set's side stream");
@@ -659,31 +751,69 @@ extern "C" qmc_status qmc_walkers_create(qmc_system_t s, int n_walkers, const do
 namespace {
 // The sweeps of one walker set: Metropolis moves from batched proposals, or drift moves
 // with in-kernel orbital evaluation; windows flushed in batches every k moves unless the
-// re-inversion cadence counts accepted moves.
-qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStream_t st) {
+// re-inversion cadence counts accepted moves. t: the sweep index of the Philox counters (an
+// offset from *W.t_base when that is set).
+qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_node, cudaStream_t st) {
   qmc_system_s* s = w->sys;
   const SysParams& P = s->P;
   const int kc = s->d.delay_k, period = s->d.reinv_period;
   const bool drift = s->d.move == QMC_MOVE_DRIFT;
   const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
                    !(period > 0 && s->d.prec == QMC_FP64);
+  // Pipelined proposals (whole-block batches of Metropolis moves): a block's proposals and
+  // their orbital rows depend only on that block's positions, which the other block's moves
+  // leave alone. So the down block's are formed on the side stream while the up block moves,
+  // and once the up block's moves are done, the next sweep's up-block proposals are formed
+  // there while the down block moves. Both are gathers bound by HBM; the moves are bound by
+  // latency.
+  const bool pipe = !drift && ext && w->d_P2 != nullptr;
+  const bool have_pf = pipe && w->pf_ready;
+  w->pf_ready = false;
+  auto propose_block = [&](int e0, int e1, uint32_t tt, void* Pbuf, Prop* prbuf,
+                           cudaStream_t ps) -> qmc_status {
+    const int cap = ps == w->side ? s->d.prop_blocks : 0;
+    { Bracket b(w, ps, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, tt, e0, e1, prbuf, ps)); }
+    {
+      Bracket b(w, ps, QMC_K_VGL);
+      QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, prbuf, Pbuf, cap, ps));
+    }
+    return QMC_OK;
+  };
   bool joined = true;             // the side stream's work has been joined back into st
   for (int spin = 0; spin < 2; ++spin) {
     const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
     const int pchunk = drift ? std::max(b1 - b0, 1) : w->chunk;
+    void* Pbuf = pipe && spin ? w->d_P2 : w->d_P;
+    Prop* prbuf = pipe && spin ? w->d_prop2 : w->d_prop;
     for (int pc0 = b0; pc0 < b1; pc0 += pchunk) {
       const int pc1 = std::min(b1, pc0 + pchunk);
-      if (!drift) {
-        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, w->sweep, pc0, pc1, w->d_prop, st)); }
-        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, pc0, pc1, w->d_prop, w->d_P, st)); }
+      if (pipe) {
+        if (spin == 0) {
+          if (!have_pf) {
+            qmc_status r = propose_block(pc0, pc1, t, Pbuf, prbuf, st);
+            if (r != QMC_OK) return r;
+          }
+          QMC_CUDA(cudaEventRecord(w->ev_fork, st));
+          QMC_CUDA(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
+          qmc_status r = propose_block(P.n_up, P.n_e, t, w->d_P2, w->d_prop2, w->side);
+          if (r != QMC_OK) return r;
+          QMC_CUDA(cudaEventRecord(w->ev_prop, w->side));
+          QMC_CUDA(cudaEventRecord(w->ev_join, w->side));
+          joined = false;
+        } else {
+          QMC_CUDA(cudaStreamWaitEvent(st, w->ev_prop, 0));
+        }
+      } else if (!drift) {
+        qmc_status r = propose_block(pc0, pc1, t, Pbuf, prbuf, st);
+        if (r != QMC_OK) return r;
       }
       if (!ext) {
         Bracket b(w, st, QMC_K_SWEEP);
         if (drift)
-          QMC_CUDA(s->tt->sweep_drift(P, W, w->sweep, pc0, pc1, kc, period, s->d.reinv_on_accepted,
+          QMC_CUDA(s->tt->sweep_drift(P, W, t, pc0, pc1, kc, period, s->d.reinv_on_accepted,
                                       0, fixed_node, st));
         else
-          QMC_CUDA(s->tw->sweep(P, W, w->sweep, pc0, pc1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
+          QMC_CUDA(s->tw->sweep(P, W, t, pc0, pc1, kc, Pbuf, prbuf, pc0, pc1 - pc0,
                                 period, s->d.reinv_on_accepted, 0, fixed_node, st));
         continue;
       }
@@ -693,9 +823,9 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStre
         {
           Bracket b(w, st, QMC_K_SWEEP);
           if (drift)
-            QMC_CUDA(s->tt->sweep_drift(P, W, w->sweep, e0, e1, kc, 0, 0, 1, fixed_node, st));
+            QMC_CUDA(s->tt->sweep_drift(P, W, t, e0, e1, kc, 0, 0, 1, fixed_node, st));
           else
-            QMC_CUDA(s->tw->sweep(P, W, w->sweep, e0, e1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
+            QMC_CUDA(s->tw->sweep(P, W, t, e0, e1, kc, Pbuf, prbuf, pc0, pc1 - pc0,
                                   0, 0, 1, fixed_node, st));
         }
         { Bracket b(w, st, QMC_K_FLUSH); QMC_CUDA(s->tw->flush(P, W, spin, st)); }
@@ -739,8 +869,105 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, bool fixed_node, cudaStre
         e0 = e1;
       }
     }
+    if (pipe && spin == 0) {
+      // the up block's positions are final for this sweep: its proposals of the next one
+      QMC_CUDA(cudaEventRecord(w->ev_fork, st));
+      QMC_CUDA(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
+      qmc_status r = propose_block(0, P.n_up, t + 1, w->d_P, w->d_prop, w->side);
+      if (r != QMC_OK) return r;
+      QMC_CUDA(cudaEventRecord(w->ev_join, w->side));
+      joined = false;
+      w->pf_ready = true;
+    }
   }
   if (!joined) QMC_CUDA(cudaStreamWaitEvent(st, w->ev_join, 0));
+  return QMC_OK;
+}
+
+// The host state a sweep of walker set w changes: its device pointers (the refinements swap
+// the two inverse buffers of a spin block) and its move counts.
+void put_state(Bytes& b, const qmc_walkers_s* w) {
+  put(b, w->W);
+  put(b, w->since_moves);
+  put(b, w->since_anchor);
+  put(b, w->pf_ready);
+}
+
+void take_state(const unsigned char*& p, qmc_walkers_s* w) {
+  take(p, w->W);
+  take(p, w->since_moves);
+  take(p, w->since_anchor);
+  take(p, w->pf_ready);
+}
+
+// Everything the launches of walker set w's sweep depend on besides the sweep index.
+void put_walker_key(Bytes& b, const qmc_walkers_s* w) {
+  put(b, w->sys->P);
+  put(b, w->sys->d);
+  put(b, w->chunk);
+  put(b, w->d_P);
+  put(b, w->d_prop);
+  put(b, w->d_j3vgl);
+  put_state(b, w);
+}
+
+// Ends a capture begun on `cap` and instantiates it; on any failure (of the capture's own
+// launches, r, or of the capture) no graph is kept.
+qmc_status end_capture(cudaStream_t cap, qmc_status r, cudaGraphExec_t* exec) {
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cap, &graph);
+  cudaError_t ei = cudaSuccess;
+  if (r == QMC_OK && e == cudaSuccess) ei = cudaGraphInstantiate(exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (r != QMC_OK) return r;
+  if (e != cudaSuccess || ei != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QMC_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : ei));
+  }
+  return QMC_OK;
+}
+
+// One Metropolis or drift sweep of w and its measurement, as a graph on stream st: captured
+// (on w's capture stream; nothing runs) the first time its starting state is met, then
+// replayed behind one launch that sets the device sweep index to w->sweep.
+qmc_status sweep_graph(qmc_walkers_s* w, cudaStream_t st) {
+  Bytes key;
+  put_walker_key(key, w);
+  GraphEntry* g = w->graphs.find(key);
+  if (!g) {
+    Bytes pre;
+    put_state(pre, w);
+    const int64_t l0 = w->launches;
+    QMC_CUDA(cudaStreamBeginCapture(w->cap, cudaStreamCaptureModeRelaxed));
+    WalkParams W = w->W;
+    W.trace = nullptr;
+    W.forced = nullptr;
+    W.t_base = w->d_t;
+    qmc_status r = sweep_once(w, W, 0u, false, w->cap);
+    if (r == QMC_OK) r = measure_energy(w, W, 1u, w->cap);
+    cudaGraphExec_t exec = nullptr;
+    r = end_capture(w->cap, r, &exec);
+    const int64_t n = w->launches - l0;
+    Bytes post;
+    put_state(post, w);
+    const unsigned char* p = pre.data();
+    take_state(p, w);
+    w->launches = l0;
+    if (r != QMC_OK) return r;
+    g = &w->graphs.slot();
+    g->key = std::move(key);
+    g->post = std::move(post);
+    g->exec = exec;
+    g->launches = {n};
+    ++w->graphs.captures;
+  }
+  QMC_CUDA(launch_set_word(w->d_t, w->sweep, st));
+  QMC_CUDA(cudaGraphLaunch(g->exec, st));
+  const unsigned char* p = g->post.data();
+  take_state(p, w);
+  w->launches += g->launches[0] + 1;
+  g->used = ++w->graphs.clock;
+  ++w->graphs.replays;
   return QMC_OK;
 }
 }  // namespace
@@ -759,13 +986,24 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
       W.trace = w->trace + w->traced * (size_t)W.n_w * P.n_e * 8;
     if (w->d_forced && sw < w->forced_sweeps)
       W.forced = w->d_forced + (size_t)sw * W.n_w * P.n_e;
-    qmc_status r = sweep_once(w, W, false, st);
-    if (r != QMC_OK) return r;
-    r = measure_energy(w, W, w->sweep + 1, st);
-    if (r != QMC_OK) return r;
+    // proposals formed ahead by the previous sweep serve only the sweep and table they were
+    // made for
+    if (w->pf_ready && (w->pf_sweep != w->sweep || w->pf_table != s->table_version))
+      w->pf_ready = false;
+    if (w->graphs.enabled && !w->profiling && !W.trace && !W.forced) {
+      qmc_status r = sweep_graph(w, st);
+      if (r != QMC_OK) return r;
+    } else {
+      qmc_status r = sweep_once(w, W, w->sweep, false, st);
+      if (r != QMC_OK) return r;
+      r = measure_energy(w, W, w->sweep + 1, st);
+      if (r != QMC_OK) return r;
+    }
     if (W.trace) ++w->traced;
     ++w->sweep;
     w->proposed += (long long)W.n_w * P.n_e;
+    w->pf_sweep = w->sweep;
+    w->pf_table = s->table_version;
   }
   if (w->d_forced) {
     QMC_CUDA(cudaStreamSynchronize(st));
@@ -1015,6 +1253,19 @@ extern "C" qmc_status qmc_check_errors(qmc_walkers_t w, void* stream) {
 
 extern "C" int64_t qmc_launch_count(qmc_walkers_t w) { return w ? w->launches : 0; }
 
+extern "C" qmc_status qmc_graph_enable(qmc_walkers_t w, int enable) {
+  if (!w) return fail(QMC_EINVAL, "qmc_graph_enable: NULL walkers");
+  w->graphs.enabled = enable != 0;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_graph_stats(qmc_walkers_t w, int64_t* captures, int64_t* replays) {
+  if (!w) return fail(QMC_EINVAL, "qmc_graph_stats: NULL walkers");
+  if (captures) *captures = w->graphs.captures;
+  if (replays) *replays = w->graphs.replays;
+  return QMC_OK;
+}
+
 extern "C" qmc_status qmc_profile_enable(qmc_walkers_t w, int enable) {
   if (!w) return fail(QMC_EINVAL, "qmc_profile_enable: NULL walkers");
   w->profiling = enable != 0;
@@ -1075,8 +1326,11 @@ struct qmc_dmc_s {
   };
   std::vector<Sys> sys;
   uint32_t step = 0;
-  cudaEvent_t ev_in = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_done = nullptr;
   std::vector<cudaEvent_t> ev_out;
+  GraphCache graphs;
+  cudaStream_t cap = nullptr;  // capture stream of the step graphs
+  uint32_t* d_t = nullptr;     // device step index read by replayed graphs
 };
 
 namespace {
@@ -1095,7 +1349,11 @@ void free_dmc(qmc_dmc_s* d) {
     if (y.st) cudaStreamDestroy(y.st);
   }
   if (d->ev_in) cudaEventDestroy(d->ev_in);
+  if (d->ev_done) cudaEventDestroy(d->ev_done);
   for (auto e : d->ev_out) cudaEventDestroy(e);
+  d->graphs.clear();
+  cudaFree(d->d_t);
+  if (d->cap) cudaStreamDestroy(d->cap);
   delete d;
 }
 }  // namespace
@@ -1151,44 +1409,161 @@ extern "C" qmc_status qmc_dmc_create(qmc_system_t const* systems, const int* n_w
       y.w[b]->W.n_live = D.n_live + b;
     }
   }
-  cudaEventCreateWithFlags(&d->ev_in, cudaEventDisableTiming);
   d->ev_out.resize(n_systems);
-  for (auto& e : d->ev_out) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  cudaError_t e = cudaEventCreateWithFlags(&d->ev_in, cudaEventDisableTiming);
+  e = e ? e : cudaEventCreateWithFlags(&d->ev_done, cudaEventDisableTiming);
+  for (auto& v : d->ev_out) e = e ? e : cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+  e = e ? e : cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking);
+  e = e ? e : cudaMalloc(&d->d_t, sizeof(uint32_t));
+  if (e != cudaSuccess) { free_dmc(d); return fail(QMC_ECUDA, "qmc_dmc_create: %s", cudaGetErrorString(e)); }
   *out = d;
   return QMC_OK;
 }
+
+namespace {
+// One DMC step of every system, each on its own stream: drift-diffusion sweep, local energy,
+// branching weights and copy counts, copies into the other slot buffer. t: the step index of
+// the Philox counters (an offset from *t_base when that is set).
+qmc_status dmc_step_once(qmc_dmc_s* d, uint32_t t, const uint32_t* t_base) {
+  for (auto& y : d->sys) {
+    qmc_walkers_s* w = y.w[y.parity];
+    qmc_walkers_s* w2 = y.w[y.parity ^ 1];
+    WalkParams W = w->W;
+    W.trace = nullptr;
+    W.forced = nullptr;
+    W.t_base = t_base;
+    QMC_CUDA(cudaMemsetAsync(W.r2, 0, sizeof(double) * 2 * (size_t)W.n_w, y.st));
+    qmc_status r = sweep_once(w, W, t, true, y.st);
+    if (r != QMC_OK) return r;
+    r = measure_energy(w, W, t + 1, y.st);
+    if (r != QMC_OK) return r;
+    DmcParams D = y.D;
+    D.e_old = y.e_old[y.parity];
+    D.e_old_next = y.e_old[y.parity ^ 1];
+    {
+      Bracket b(w, y.st, QMC_K_BRANCH);
+      QMC_CUDA(y.sys->tw->dmc_branch(y.sys->P, W, D, y.parity, t, y.st));
+      QMC_CUDA(y.sys->tw->dmc_copy(y.sys->P, W, w2->W, D, y.parity, y.st));
+    }
+    w->launches += 1;   // the copy kernel after the branching kernel
+    y.parity ^= 1;
+  }
+  return QMC_OK;
+}
+
+// The host state a DMC step changes, and the key of its graph.
+void put_dmc_state(Bytes& b, const qmc_dmc_s* d) {
+  for (auto& y : d->sys) {
+    put(b, y.parity);
+    put_state(b, y.w[0]);
+    put_state(b, y.w[1]);
+  }
+}
+
+void take_dmc_state(const unsigned char*& p, qmc_dmc_s* d) {
+  for (auto& y : d->sys) {
+    take(p, y.parity);
+    take_state(p, y.w[0]);
+    take_state(p, y.w[1]);
+  }
+}
+
+void put_dmc_key(Bytes& b, const qmc_dmc_s* d) {
+  for (auto& y : d->sys) {
+    put(b, y.D);
+    put(b, y.e_old);
+    put_walker_key(b, y.w[0]);
+    put_walker_key(b, y.w[1]);
+  }
+  put_dmc_state(b, d);
+}
+
+// One step of every system as a graph on stream cs (captured on the driver's capture
+// stream the first time its starting state is met, then replayed), its systems' streams
+// made to wait for it so that the per-system reads see its results.
+qmc_status dmc_step_graph(qmc_dmc_s* d, cudaStream_t cs) {
+  Bytes key;
+  put_dmc_key(key, d);
+  GraphEntry* g = d->graphs.find(key);
+  if (!g) {
+    Bytes pre;
+    put_dmc_state(pre, d);
+    std::vector<int64_t> l0;
+    for (auto& y : d->sys) {
+      l0.push_back(y.w[0]->launches);
+      l0.push_back(y.w[1]->launches);
+    }
+    QMC_CUDA(cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeRelaxed));
+    qmc_status r = QMC_OK;
+    if (cudaEventRecord(d->ev_in, d->cap) != cudaSuccess) r = fail(QMC_ECUDA, "qmc_dmc_step: capture fork");
+    for (auto& y : d->sys)
+      if (r == QMC_OK && cudaStreamWaitEvent(y.st, d->ev_in, 0) != cudaSuccess)
+        r = fail(QMC_ECUDA, "qmc_dmc_step: capture fork");
+    if (r == QMC_OK) r = dmc_step_once(d, 0u, d->d_t);
+    for (size_t i = 0; r == QMC_OK && i < d->sys.size(); ++i)
+      if (cudaEventRecord(d->ev_out[i], d->sys[i].st) != cudaSuccess ||
+          cudaStreamWaitEvent(d->cap, d->ev_out[i], 0) != cudaSuccess)
+        r = fail(QMC_ECUDA, "qmc_dmc_step: capture join");
+    cudaGraphExec_t exec = nullptr;
+    r = end_capture(d->cap, r, &exec);
+    std::vector<int64_t> n;
+    size_t k = 0;
+    for (auto& y : d->sys)
+      for (auto* w : y.w) {
+        n.push_back(w->launches - l0[k]);
+        w->launches = l0[k++];
+      }
+    Bytes post;
+    put_dmc_state(post, d);
+    const unsigned char* p = pre.data();
+    take_dmc_state(p, d);
+    if (r != QMC_OK) return r;
+    g = &d->graphs.slot();
+    g->key = std::move(key);
+    g->post = std::move(post);
+    g->exec = exec;
+    g->launches = std::move(n);
+    ++d->graphs.captures;
+  }
+  for (auto& y : d->sys) y.w[y.parity]->sweep = d->step;
+  QMC_CUDA(launch_set_word(d->d_t, d->step, cs));
+  QMC_CUDA(cudaGraphLaunch(g->exec, cs));
+  QMC_CUDA(cudaEventRecord(d->ev_done, cs));
+  for (auto& y : d->sys) QMC_CUDA(cudaStreamWaitEvent(y.st, d->ev_done, 0));
+  const unsigned char* p = g->post.data();
+  take_dmc_state(p, d);
+  size_t k = 0;
+  for (auto& y : d->sys)
+    for (auto* w : y.w) w->launches += g->launches[k++];
+  d->sys[0].w[0]->launches += 1;   // the sweep-index launch
+  g->used = ++d->graphs.clock;
+  ++d->graphs.replays;
+  return QMC_OK;
+}
+}  // namespace
 
 extern "C" qmc_status qmc_dmc_step(qmc_dmc_t d, int n_steps, void* stream) {
   if (!d) return fail(QMC_EINVAL, "qmc_dmc_step: NULL driver");
   if (n_steps < 0) return fail(QMC_EINVAL, "qmc_dmc_step: n_steps < 0");
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  bool graphs = d->graphs.enabled;
+  for (auto& y : d->sys)
+    for (auto* w : y.w) graphs = graphs && !w->profiling;
+  if (graphs) {
+    for (int k = 0; k < n_steps; ++k) {
+      qmc_status r = dmc_step_graph(d, cs);
+      if (r != QMC_OK) return r;
+      ++d->step;
+    }
+    return QMC_OK;
+  }
   QMC_CUDA(cudaEventRecord(d->ev_in, cs));
   for (auto& y : d->sys) QMC_CUDA(cudaStreamWaitEvent(y.st, d->ev_in, 0));
   for (int k = 0; k < n_steps; ++k) {
     // the systems advance concurrently, one stream each
-    for (auto& y : d->sys) {
-      qmc_walkers_s* w = y.w[y.parity];
-      qmc_walkers_s* w2 = y.w[y.parity ^ 1];
-      WalkParams W = w->W;
-      W.trace = nullptr;
-      W.forced = nullptr;
-      w->sweep = d->step;
-      QMC_CUDA(cudaMemsetAsync(W.r2, 0, sizeof(double) * 2 * (size_t)W.n_w, y.st));
-      qmc_status r = sweep_once(w, W, true, y.st);
-      if (r != QMC_OK) return r;
-      r = measure_energy(w, W, d->step + 1, y.st);
-      if (r != QMC_OK) return r;
-      DmcParams D = y.D;
-      D.e_old = y.e_old[y.parity];
-      D.e_old_next = y.e_old[y.parity ^ 1];
-      {
-        Bracket b(w, y.st, QMC_K_BRANCH);
-        QMC_CUDA(y.sys->tw->dmc_branch(y.sys->P, W, D, y.parity, d->step, y.st));
-        QMC_CUDA(y.sys->tw->dmc_copy(y.sys->P, W, w2->W, D, y.parity, y.st));
-      }
-      w->launches += 1;   // the copy kernel after the branching kernel
-      y.parity ^= 1;
-    }
+    for (auto& y : d->sys) y.w[y.parity]->sweep = d->step;
+    qmc_status r = dmc_step_once(d, d->step, nullptr);
+    if (r != QMC_OK) return r;
     ++d->step;
   }
   for (size_t i = 0; i < d->sys.size(); ++i) {
@@ -1279,6 +1654,19 @@ extern "C" qmc_status qmc_dmc_walkers(qmc_dmc_t d, int system, int max_walkers, 
   }
   if (ids) QMC_CUDA(cudaMemcpy(ids, w->W.wid, n * sizeof(uint32_t), cudaMemcpyDefault));
   if (e_local) QMC_CUDA(cudaMemcpy(e_local, w->W.e_loc, n * sizeof(double), cudaMemcpyDefault));
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_graph_enable(qmc_dmc_t d, int enable) {
+  if (!d) return fail(QMC_EINVAL, "qmc_dmc_graph_enable: NULL driver");
+  d->graphs.enabled = enable != 0;
+  return QMC_OK;
+}
+
+extern "C" qmc_status qmc_dmc_graph_stats(qmc_dmc_t d, int64_t* captures, int64_t* replays) {
+  if (!d) return fail(QMC_EINVAL, "qmc_dmc_graph_stats: NULL driver");
+  if (captures) *captures = d->graphs.captures;
+  if (replays) *replays = d->graphs.replays;
   return QMC_OK;
 }
 

@@ -35,7 +35,8 @@ __device__ __forceinline__ int comb_teeth_below(double c, double W, int n, doubl
 // `cap`, and E_T <- E_w - ln(N / N_target) / (10 tau) with E_w the weighted mean E_L of
 // this step.
 __global__ void __launch_bounds__(1024) k_dmc_branch(SysParams S, WalkParams Wk, DmcParams D,
-                                                    int parity, uint32_t step) {
+                                                    int parity, uint32_t step0) {
+  const uint32_t step = sweep_index(Wk, step0);
   __shared__ int scan[1024];
   __shared__ int scan2[1024];
   __shared__ double red[2 * 32];

@@ -113,10 +113,19 @@ struct WalkParams {
   double* vnl;         // [W]    non-local pseudopotential energy of the last measurement
   int* nl_pairs;       // [W][nl_cap] electron * n_ion + ion of the pairs inside the cutoff
   int* nl_count;       // [W]
+  double* nl_val;      // [W][nl_cap] V_NL of each listed pair
   int nl_cap;
   void* j3vgl;         // working precision [W][n_e][5]: grad_i J3, lap_i J3 and electron i's
                        // share of J3 for the next local energy; nullptr without that term
+  const uint32_t* t_base;  // optional device sweep index added to the kernels' sweep argument
+                           // (a replayed graph passes offsets and reads the index here)
 };
+
+// Sweep index of the Philox counters: the launch argument, plus the device word when the
+// launch belongs to a replayed graph.
+__device__ __forceinline__ uint32_t sweep_index(const WalkParams& W, uint32_t t) {
+  return W.t_base ? t + *W.t_base : t;
+}
 
 // Inverse of walker w's spin block: Binv[e][j] = (A^-1)[j][e], N_s x N_s, row-major.
 template <class T>

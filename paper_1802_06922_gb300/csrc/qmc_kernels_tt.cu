@@ -18,12 +18,13 @@ cudaError_t vgl_current(const SysParams& S, const WalkParams& W, cudaStream_t st
 
 template <class TT, class TW>
 cudaError_t vgl_proposals(const SysParams& S, const WalkParams& W, int e0, int e1,
-                          const void* prop, void* out, cudaStream_t st) {
+                          const void* prop, void* out, int max_blocks, cudaStream_t st) {
   constexpr int V = TabVec<TT>::V;
   const int ns = e0 < S.n_up ? S.n_up : S.n_dn;
   const long long chunks = (ns + 32 * V - 1) / (32 * V);
   const long long warps = (long long)W.n_w * (e1 - e0) * chunks;
-  const long long blocks = (warps * 32 + 255) / 256;
+  long long blocks = (warps * 32 + 255) / 256;
+  if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
   k_vgl_proposals<TT, TW><<<(unsigned)blocks, 256, 0, st>>>(
       S, W, e0, e1, static_cast<const Prop*>(prop), static_cast<TW*>(out));
   return cudaGetLastError();
@@ -48,13 +49,16 @@ cudaError_t nlpp(const SysParams& S, const WalkParams& W, uint32_t t, cudaStream
   cudaError_t e = cudaMemsetAsync(W.nl_count, 0, sizeof(int) * W.n_w, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(W.vnl, 0, sizeof(double) * W.n_w, st);
   if (e != cudaSuccess) return e;
-  const long long n1 = (long long)W.n_w * S.n_e;
-  k_nlpp_pairs<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(S, W, W.nl_pairs, W.nl_count, W.nl_cap);
+  k_nlpp_pairs<<<W.n_w, 256, 0, st>>>(S, W, W.nl_pairs, W.nl_count, W.nl_cap);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long warps = (long long)W.n_w * W.nl_cap;
   k_nlpp_eval<TT, TW><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-      S, W, W.nl_pairs, W.nl_count, W.nl_cap, t, W.vnl);
+      S, W, W.nl_pairs, W.nl_count, W.nl_cap, t, W.nl_val);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_nlpp_sum<<<(unsigned)(((long long)W.n_w * 32 + 255) / 256), 256, 0, st>>>(
+      W, W.nl_val, W.nl_count, W.nl_cap, W.vnl);
   return cudaGetLastError();
 }
 

@@ -215,6 +215,13 @@ cudaError_t launch_proposals(const SysParams& S, const WalkParams& W, uint32_t t
   return cudaGetLastError();
 }
 
+static __global__ void k_set_word(uint32_t* p, uint32_t v) { *p = v; }
+
+cudaError_t launch_set_word(uint32_t* p, uint32_t v, cudaStream_t st) {
+  k_set_word<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_accumulate(const WalkParams& W, double* out, long long* nacc, cudaStream_t st) {
   k_accumulate<<<1, 256, 0, st>>>(W, out, nacc);
   return cudaGetLastError();

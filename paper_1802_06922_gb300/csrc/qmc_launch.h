@@ -40,8 +40,9 @@ const TwLaunch& tw_launch_f32();
 struct TtLaunch {
   int vec;   // orbitals per 16-byte load
   cudaError_t (*vgl_current)(const SysParams&, const WalkParams&, cudaStream_t);
+  // (max_blocks > 0 caps the grid; the kernel then loops over its work)
   cudaError_t (*vgl_proposals)(const SysParams&, const WalkParams&, int e0, int e1,
-                               const void* prop, void* out, cudaStream_t);
+                               const void* prop, void* out, int max_blocks, cudaStream_t);
   // drift-diffusion sweep of electrons [e0, e1) with in-kernel orbital evaluation
   cudaError_t (*sweep_drift)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
                              int k, int reinv_period, int reinv_on_acc, int ext_flush,
@@ -57,6 +58,8 @@ const TtLaunch& tt_launch_bf16();
 cudaError_t launch_proposals(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
                              void* prop, cudaStream_t);
 cudaError_t launch_accumulate(const WalkParams&, double* out, long long* nacc, cudaStream_t);
+// *p = v on the stream (the sweep index of a replayed graph).
+cudaError_t launch_set_word(uint32_t* p, uint32_t v, cudaStream_t);
 // Ewald setup from the ions: c_k, the ions' rho_k and the constant terms (FP64).
 cudaError_t launch_ewald_setup(const SysParams&, double* ck, double* rho, double* cst, cudaStream_t);
 

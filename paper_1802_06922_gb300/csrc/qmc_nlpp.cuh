@@ -8,9 +8,9 @@
 // the determinant ratio phi(r') . Binv[i] (value-only tricubic gather of the spin block's
 // orbitals dotted with the inverse row) times exp(dJ), with no update of anything.
 //
-// Two kernels: k_nlpp_pairs lists the (walker, electron, ion) pairs inside the cutoff; then
-// k_nlpp_eval gives one warp to each pair, which evaluates its 12 points and adds the
-// pair's energy to E_L and to the walker's V_NL.
+// Three kernels: k_nlpp_pairs lists the (walker, electron, ion) pairs inside the cutoff;
+// k_nlpp_eval gives one warp to each pair, which evaluates its 12 points; k_nlpp_sum adds
+// each walker's pair energies in list order to E_L and to the walker's V_NL.
 #pragma once
 #include "qmc_kernels.cuh"
 
@@ -57,29 +57,64 @@ __device__ __forceinline__ void val_dot_lane(const SysParams& S, const int (&idx
     if (o0 + v < n_eval) comp_fma(s, c, (TW)acc[v], brow[o0 + v]);
 }
 
-// Pairs (electron, ion) of each walker within the cutoff: pairs[w][k] = e * n_ion + I,
-// count[w] = k. One thread per (walker, electron).
-static __global__ void k_nlpp_pairs(SysParams S, WalkParams Wk, int* __restrict__ pairs,
-                                    int* __restrict__ count, int cap) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)Wk.n_w * S.n_e) return;
-  const int w = (int)(g / S.n_e), e = (int)(g % S.n_e);
+// Pairs (electron, ion) of each walker within the cutoff: pairs[w][k] = e * n_ion + I in
+// electron-major, ion-minor order, count[w] = k. One block per walker: each thread counts
+// the pairs of one electron per pass, a block scan gives the offsets, then the thread writes
+// them, so the list (and every sum over it) is the same from run to run.
+static __global__ void __launch_bounds__(256) k_nlpp_pairs(SysParams S, WalkParams Wk,
+                                                           int* __restrict__ pairs,
+                                                           int* __restrict__ count, int cap) {
+  __shared__ int part[256 / 32];
+  const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (Wk.n_live && w >= *Wk.n_live) return;
   const double* P = Wk.pos + (size_t)w * 3 * S.n_e;
-  const double x[3] = {P[e], P[S.n_e + e], P[2 * S.n_e + e]};
   const double rc2 = S.nl_rcut * S.nl_rcut;
-  for (int I = 0; I < S.n_ion; ++I) {
+  auto inside = [&](const double (&x)[3], int I) {
     double r2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const double d = min_image<double>(x[c] - S.ions[c * S.n_ion + I], S.L);
       r2 += d * d;
     }
-    if (r2 < rc2 && r2 > 0.0) {
-      const int k = atomicAdd(&count[w], 1);
-      if (k < cap) pairs[(size_t)w * cap + k] = e * S.n_ion + I;
-      else atomicOr(Wk.err, kErrOverflow);
+    return r2 < rc2 && r2 > 0.0;
+  };
+  int base = 0;
+  for (int e0 = 0; e0 < S.n_e; e0 += blockDim.x) {
+    const int e = e0 + tid;
+    double x[3] = {0.0, 0.0, 0.0};
+    int c = 0;
+    if (e < S.n_e) {
+      x[0] = P[e]; x[1] = P[S.n_e + e]; x[2] = P[2 * S.n_e + e];
+      for (int I = 0; I < S.n_ion; ++I) c += inside(x, I);
     }
+    // exclusive block scan of the counts
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) part[warp] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      before += q < warp ? part[q] : 0;
+      total += part[q];
+    }
+    __syncthreads();
+    if (c > 0) {
+      int k = base + before + incl - c;
+      for (int I = 0; I < S.n_ion; ++I)
+        if (inside(x, I)) {
+          if (k < cap) pairs[(size_t)w * cap + k] = e * S.n_ion + I;
+          ++k;
+        }
+    }
+    base += total;
+  }
+  if (tid == 0) {
+    count[w] = base;
+    if (base > cap) atomicOr(Wk.err, kErrOverflow);
   }
 }
 
@@ -112,11 +147,11 @@ __device__ __forceinline__ void nlpp_rotation(const SysParams& S, uint32_t t, ui
 }
 
 // One warp per listed pair: the 12 virtual moves of electron e about ion I; the pair's
-// V_NL (FP64) is added to E_L and to vnl[w].
+// V_NL (FP64) goes to vals[w][k].
 template <class TT, class TW>
 __global__ void __launch_bounds__(256, 2) k_nlpp_eval(SysParams S, WalkParams Wk, const int* __restrict__ pairs,
                                                    const int* __restrict__ count, int cap,
-                                                   uint32_t t, double* __restrict__ vnl) {
+                                                   uint32_t t, double* __restrict__ vals) {
   using A = typename AccOf<TT>::type;
   constexpr int V = TabVec<TT>::V;
   __shared__ JastrowTab<TW> jt;
@@ -147,7 +182,7 @@ __global__ void __launch_bounds__(256, 2) k_nlpp_eval(SysParams S, WalkParams Wk
   if (lane < 12) {
     const double r = sqrt(r2);
     double O[3][3], v[3], p[3];
-    nlpp_rotation(S, t, Wk.wid[w], O);
+    nlpp_rotation(S, sweep_index(Wk, t), Wk.wid[w], O);
     ico_vertex(lane, v);
     double ct = 0.0;
 #pragma unroll
@@ -233,9 +268,26 @@ __global__ void __launch_bounds__(256, 2) k_nlpp_eval(SysParams S, WalkParams Wk
     const double wqq = __shfl_sync(0xffffffffu, wq, q);
     total += wqq * ((double)s + (double)sc) * exp((double)dj);
   }
+  if (lane == 0) vals[(size_t)w * cap + k] = total;
+}
+
+// V_NL of each walker: the sum of its pairs' values in list order (one warp per walker, a
+// fixed reduction tree), stored to vnl[w] and added to E_L.
+static __global__ void k_nlpp_sum(WalkParams Wk, const double* __restrict__ vals,
+                                  const int* __restrict__ count, int cap, double* __restrict__ vnl) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= Wk.n_w) return;
+  const int w = (int)gw;
+  if (Wk.n_live && w >= *Wk.n_live) return;
+  const int n = min(count[w], cap);
+  double v = 0.0;
+  for (int k = lane; k < n; k += 32) v += vals[(size_t)w * cap + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) {
-    atomicAdd(&Wk.e_loc[w], total);
-    atomicAdd(&vnl[w], total);
+    vnl[w] = v;
+    Wk.e_loc[w] += v;
   }
 }
 

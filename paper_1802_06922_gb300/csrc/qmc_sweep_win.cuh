@@ -498,7 +498,12 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     gc[i] = (a < m && b < m) ? ci[a * kWinP + b] : TW(0);
   }
   for (int i = tid; i < m; i += nt) Wk.win_row[(size_t)w * kc + i] = e0 + sm.wt[i] - first;
-  for (int i = tid; i < 3 * n_e; i += nt) gpos[i] = sm.posd[i];
+  // positions of this launch's electrons only: the other spin block's proposals may be
+  // reading theirs meanwhile
+  for (int i = tid; i < 3 * (e1 - e0); i += nt) {
+    const int c = i / (e1 - e0), j = c * n_e + e0 + (i - c * (e1 - e0));
+    gpos[j] = sm.posd[j];
+  }
   if (tid == 0) Wk.win_m[w] = m;
   if (tid == kBook) {
     Wk.logdet[2 * w + spin] = logdet + log(lprod) + (double)lexp * 0.69314718055994530942;

@@ -35,7 +35,7 @@ class SystemDesc(C.Structure):
                 ("move", C.c_int), ("step", C.c_double), ("delay_k", C.c_int),
                 ("reinv_period", C.c_int), ("reinv_on_accepted", C.c_int),
                 ("seed", C.c_uint64), ("logdet_period", C.c_int), ("drift_a", C.c_double),
-                ("prop_chunk", C.c_int)]
+                ("prop_chunk", C.c_int), ("prop_blocks", C.c_int)]
 
 
 _vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
@@ -65,6 +65,10 @@ SIGNATURES = {
     "qmc_get_logdet": ([_vp, _vp, _vp], _i),
     "qmc_get_precision_report": ([_vp, _vp, _vp], _i),
     "qmc_launch_count": ([_vp], C.c_int64),
+    "qmc_graph_enable": ([_vp, _i], _i),
+    "qmc_graph_stats": ([_vp, _vp, _vp], _i),
+    "qmc_dmc_graph_enable": ([_vp, _i], _i),
+    "qmc_dmc_graph_stats": ([_vp, _vp, _vp], _i),
     "qmc_profile_enable": ([_vp, _i], _i),
     "qmc_profile_read": ([_vp, _vp, _vp], _i),
     "qmc_walkers_destroy": ([_vp], None),
@@ -139,7 +143,8 @@ class System:
 
     def __init__(self, n_up, n_dn, L, ions, precision="fp64", move="metropolis", step=0.3,
                  delay_k=1, reinv_period=0, reinv_on_accepted=False, seed=0, ion_Z=4.0,
-                 kappa=1.0, with_potential=True, logdet_period=0, drift_a=0.0, prop_chunk=0):
+                 kappa=1.0, with_potential=True, logdet_period=0, drift_a=0.0, prop_chunk=0,
+                 prop_blocks=0):
         lib = load()
         ions = np.ascontiguousarray(np.asarray(ions, dtype=np.float64).reshape(-1, 3))
         self._ions = ions
@@ -148,7 +153,7 @@ class System:
                        int(bool(with_potential)), PRECISIONS[precision], MOVES[move],
                        float(step), int(delay_k), int(reinv_period), int(bool(reinv_on_accepted)),
                        int(seed) & 0xFFFFFFFFFFFFFFFF, int(logdet_period), float(drift_a),
-                       int(prop_chunk))
+                       int(prop_chunk), int(prop_blocks))
         h = C.c_void_p()
         _check(lib.qmc_system_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -322,6 +327,16 @@ class Walkers:
     def launch_count(self) -> int:
         return int(load().qmc_launch_count(self.h))
 
+    def graphs(self, enable: bool = True):
+        """Sweeps replayed as CUDA graphs (on by default)."""
+        _check(load().qmc_graph_enable(self.h, int(bool(enable))))
+
+    def graph_stats(self):
+        """(captures, replays) of sweep graphs so far."""
+        c, r = C.c_int64(0), C.c_int64(0)
+        _check(load().qmc_graph_stats(self.h, C.byref(c), C.byref(r)))
+        return c.value, r.value
+
     def close(self):
         if getattr(self, "h", None):
             load().qmc_walkers_destroy(self.h)
@@ -393,6 +408,16 @@ class DMC:
     def launch_count(self) -> int:
         return int(load().qmc_dmc_launch_count(self.h))
 
+    def graphs(self, enable: bool = True):
+        """Steps (all systems) replayed as CUDA graphs (on by default)."""
+        _check(load().qmc_dmc_graph_enable(self.h, int(bool(enable))))
+
+    def graph_stats(self):
+        """(captures, replays) of step graphs so far."""
+        c, r = C.c_int64(0), C.c_int64(0)
+        _check(load().qmc_dmc_graph_stats(self.h, C.byref(c), C.byref(r)))
+        return c.value, r.value
+
     def close(self):
         if getattr(self, "h", None):
             load().qmc_dmc_destroy(self.h)
@@ -458,7 +483,7 @@ def slater_invert_noalloc(A, Binv, logdet=None, sign=None, stream=None):
 
 def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0,
                        reinv_on_accepted=False, step=None, move=None,
-                       logdet_period=0, drift_a=0.0, prop_chunk=0) -> System:
+                       logdet_period=0, drift_a=0.0, prop_chunk=0, prop_blocks=0) -> System:
     """System (with spline table and Jastrow functors) from a ``synthetic.build_inputs``
     dictionary, or any dictionary with the same keys."""
     spec = inputs["spec"]
@@ -467,7 +492,8 @@ def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0
                delay_k=delay_k, reinv_period=reinv_period,
                reinv_on_accepted=reinv_on_accepted, seed=inputs["seed"], ion_Z=spec.ion_Z,
                kappa=spec.kappa, with_potential=spec.with_potential,
-               logdet_period=logdet_period, drift_a=drift_a, prop_chunk=prop_chunk)
+               logdet_period=logdet_period, drift_a=drift_a, prop_chunk=prop_chunk,
+               prop_blocks=prop_blocks)
     s.set_spline(inputs["coef"])
     j = inputs["jastrow"]
     for which, key in enumerate(("eI", "same", "opp")):
