@@ -46,10 +46,6 @@ def parse_args():
     p.add_argument("--prop-chunk", type=int, default=None,
                    help="Metropolis moves per proposal batch (0 = the whole spin block); "
                         "tuned with the delay rank when --delay-k is auto")
-    p.add_argument("--prop-blocks", type=int, default=None,
-                   help="grid cap of the proposal gather that runs beside the other spin "
-                        "block's moves (0 = a full grid); tuned with the delay rank when "
-                        "--delay-k is auto")
     p.add_argument("--reinv-period", type=int, default=128)
     p.add_argument("--logdet-period", type=int, default=1024,
                    help="moves of a spin block between log-determinant anchors (a multiple of "
@@ -89,14 +85,13 @@ def system_desc(spec):
 
 
 def workload(spec, precision, delay_k, reinv_period, on_accepted=False, logdet_period=0,
-             prop_chunk=0, prop_blocks=0):
+             prop_chunk=0):
     tab = {"fp32": "FP32", "bf16": "BF16", "fp64": "FP64"}[precision]
     upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
     if prop_chunk:
         upd += f" (proposals in batches of {prop_chunk} moves)"
     elif delay_k >= 4 and precision != "fp64" and not on_accepted:
-        upd += (" (each spin block's proposals formed beside the other block's moves"
-                + (f" by a {prop_blocks}-block gather)" if prop_blocks else ")"))
+        upd += " (each spin block's proposals formed beside the other block's moves)"
     what = "accepted moves" if on_accepted else "moves"
     re = (("FP64 re-inversion" if precision == "fp64" else "re-inversion (error-free Newton step)")
           + f" every {reinv_period} {what}") if reinv_period else "no re-inversion"
@@ -413,29 +408,23 @@ def run_ours(args, spec, rank, world, local_rank):
 
     tuning = None
     if args.delay_k == "auto":
-        (k_best, c_best, g_best), t_times = q.tune_launch(inputs, pos, delays=(8, 16, 32),
-                                                          precision=args.precision,
-                                                          reinv_period=args.reinv_period,
-                                                          reinv_on_accepted=args.reinv_on_accepted)
+        (k_best, c_best), t_times = q.tune_launch(inputs, pos, delays=(8, 16, 32),
+                                                  precision=args.precision,
+                                                  reinv_period=args.reinv_period,
+                                                  reinv_on_accepted=args.reinv_on_accepted)
         args.delay_k = k_best
         if args.prop_chunk is None:
             args.prop_chunk = c_best
-            if args.prop_blocks is None:
-                args.prop_blocks = g_best
-        tuning = {"candidates_ms_per_sweep": {
-                      f"k={k},batch={c or 'block'}" + (f",gather_blocks={g}" if g else ""): round(v, 3)
-                      for (k, c, g), v in t_times.items()},
-                  "chosen": {"delay_k": k_best, "proposal_batch": c_best,
-                             "gather_blocks": g_best}}
+        tuning = {"candidates_ms_per_sweep": {f"k={k},batch={c or 'block'}": round(v, 3)
+                                              for (k, c), v in t_times.items()},
+                  "chosen": {"delay_k": k_best, "proposal_batch": c_best}}
     else:
         args.delay_k = int(args.delay_k)
     if args.prop_chunk is None:
         args.prop_chunk = 0
-    if args.prop_blocks is None:
-        args.prop_blocks = 0
     logdet_period = 0 if (args.reinv_on_accepted or args.precision == "fp64") else args.logdet_period
     sysm = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
+                                prop_chunk=args.prop_chunk,
                                 reinv_period=args.reinv_period,
                                 reinv_on_accepted=args.reinv_on_accepted,
                                 logdet_period=logdet_period)
@@ -508,21 +497,20 @@ def run_ours(args, spec, rank, world, local_rank):
     if not args.no_extras and world == 1:
         extras = {}
         sb = q.system_from_inputs(inputs, precision="bf16", delay_k=args.delay_k,
-                                  prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
+                                  prop_chunk=args.prop_chunk,
                                   reinv_period=args.reinv_period, logdet_period=logdet_period)
         msb, profb = timed_extra(sb, 10, args.warmup)
         sb.close()
         vb = whole_job_rate(world, moves_per_step * 10, msb / 1e3)
         extras["bf16_table"] = {"value": vb, "unit": UNIT, "ms_per_step": msb / 10, "steps": 10,
                                 "workload": workload(spec, "bf16", args.delay_k, args.reinv_period,
-                                                     logdet_period=logdet_period, prop_chunk=args.prop_chunk,
-                                                     prop_blocks=args.prop_blocks),
+                                                     logdet_period=logdet_period, prop_chunk=args.prop_chunk),
                                 "prof": profb}
         if args.reinv_period > 0 and logdet_period != args.reinv_period and args.precision != "fp64":
             # the log-determinant anchor at every re-inversion (the 128-move cadence the
             # 512-electron workload names for re-inversion and log-det)
             sa = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
+                                      prop_chunk=args.prop_chunk,
                                       reinv_period=args.reinv_period,
                                       logdet_period=args.reinv_period)
             msa, profa = timed_extra(sa, 10, args.warmup)
@@ -535,7 +523,7 @@ def run_ours(args, spec, rank, world, local_rank):
             # the same workload with non-local pseudopotential channels on every ion: the
             # 12-point quadrature's virtual moves are measured after every sweep
             sn = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
+                                      prop_chunk=args.prop_chunk,
                                       reinv_period=args.reinv_period, logdet_period=logdet_period)
             sn.set_nonlocal(NL_AMP, NL_WIDTH, NL_RCUT)
             msn, profn = timed_extra(sn, 10, args.warmup)
@@ -553,7 +541,7 @@ def run_ours(args, spec, rank, world, local_rank):
             # the same workload with Coulomb interactions by Ewald summation in place of the
             # Yukawa form: erfc(alpha L / 2) = erfc(4) and exp(-kcut^2 / (4 alpha^2)) = e^-16
             se = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks,
+                                      prop_chunk=args.prop_chunk,
                                       reinv_period=args.reinv_period, logdet_period=logdet_period)
             alpha = 8.0 / spec.L
             se.set_ewald(alpha, 8.0 * alpha)
@@ -568,7 +556,7 @@ def run_ours(args, spec, rank, world, local_rank):
             # M_eI = 2, M_ee = 3): every move's ratio and drift, E_L and ln|Psi| carry it
             from synthetic import jastrow3_coefficients
             sj = q.system_from_inputs(inputs, precision=args.precision, delay_k=args.delay_k,
-                                      prop_chunk=args.prop_chunk, prop_blocks=args.prop_blocks, reinv_period=args.reinv_period,
+                                      prop_chunk=args.prop_chunk, reinv_period=args.reinv_period,
                                       logdet_period=logdet_period)
             gs, go = jastrow3_coefficients(2, 3, J3_RCUT, seed=5)
             sj.set_jastrow3(gs, go, J3_RCUT)
@@ -643,8 +631,7 @@ def run_ours(args, spec, rank, world, local_rank):
             "dtype": {"fp32": "f32", "bf16": "bf16-table/f32", "fp64": "f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload(spec, args.precision, args.delay_k, args.reinv_period,
-                                            args.reinv_on_accepted, logdet_period, args.prop_chunk,
-                                            args.prop_blocks),
+                                            args.reinv_on_accepted, logdet_period, args.prop_chunk),
                        "walkers_per_gpu": spec.n_walkers, "electrons": spec.n_elec,
                        "moves_per_step": moves_per_step * world,
                        "l2": f"inputs larger than L2: {table_bytes(spec, args.precision) / 1e6:.0f} MB "

@@ -118,19 +118,12 @@ typedef struct {
                               one launch pair, per spin block (0 = the whole block); smaller
                               batches keep the rows in L2 until the sweep reads them. A
                               launch parameter only: the chain does not depend on it. */
-  int prop_blocks;         /* With whole-block batches of Metropolis moves in the batched
-                              delayed update (delay_k >= 4, windows flushed between launches),
-                              one spin block's proposal rows are formed on a second stream
-                              while the other block moves; prop_blocks > 0 caps
-                              that gather's grid (thread blocks of 256 threads that loop over
-                              the work), so that it shares HBM with the moves instead of
-                              saturating it; 0 = a full grid. A launch parameter only. */
 } qmc_system_desc;
 
 /* Creates a system. Fails with QMC_EINVAL for n_up or n_dn outside [0, 1024], n_up+n_dn
  * = 0, L <= 0, step < 0, delay_k outside [1, 64], an unknown precision/move, a
  * logdet_period that is negative or not a multiple of a positive reinv_period, or a negative
- * prop_chunk or prop_blocks. */
+ * prop_chunk. */
 qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_t* out);
 
 /* Sets the B-spline orbital table (Sec. "B-spline basis sets"). coef is host memory

@@ -18,11 +18,10 @@ from .qmcgb import Walkers, system_from_inputs
 
 
 def _time_sweeps(inputs, pos, precision, k, chunk, reinv_period, reinv_on_accepted,
-                 warm_sweeps, timed_sweeps, blocks=0) -> float:
+                 warm_sweeps, timed_sweeps) -> float:
     import torch
     s = system_from_inputs(inputs, precision=precision, delay_k=int(k), prop_chunk=int(chunk),
-                           reinv_period=reinv_period, reinv_on_accepted=reinv_on_accepted,
-                           prop_blocks=int(blocks))
+                           reinv_period=reinv_period, reinv_on_accepted=reinv_on_accepted)
     w = Walkers(s, pos)
     stream = torch.cuda.current_stream()
     try:
@@ -56,30 +55,18 @@ def tune_delay(inputs: dict, positions=None, candidates: Iterable[int] = (8, 16,
 
 
 def tune_launch(inputs: dict, positions=None, delays: Iterable[int] = (8, 16, 32),
-                chunks: Optional[Iterable[int]] = None, blocks: Optional[Iterable[int]] = None,
-                precision: str = "fp32", reinv_period: int = 0, reinv_on_accepted: bool = False,
-                warm_sweeps: int = 3, timed_sweeps: int = 2
-                ) -> Tuple[Tuple[int, int, int], Dict[Tuple[int, int, int], float]]:
-    """Returns ((best k, best proposal batch, best gather grid), {(k, batch, grid): device ms
-    per sweep}). Batches default to 2k, 4k and the whole spin block (0); a batch is always a
-    multiple of k so that no window is cut short. The grid (`prop_blocks`) caps the gather
-    that forms one spin block's proposal rows beside the other block's moves, which only
-    whole-block batches in the batched delayed update do: it defaults to a full grid (0) and
-    2, 1 and 1/2 blocks per SM there, and to 0 elsewhere."""
+                chunks: Optional[Iterable[int]] = None, precision: str = "fp32",
+                reinv_period: int = 0, reinv_on_accepted: bool = False, warm_sweeps: int = 3,
+                timed_sweeps: int = 2) -> Tuple[Tuple[int, int], Dict[Tuple[int, int], float]]:
+    """Returns ((best k, best proposal batch), {(k, batch): device ms per sweep}). Batches
+    default to 2k, 4k and the whole spin block (0); a batch is always a multiple of k so
+    that no window is cut short."""
     pos = inputs["pos"] if positions is None else positions
-    if blocks is None:
-        import torch
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        blocks = (0, 2 * sms, sms, max(1, sms // 2))
-    times: Dict[Tuple[int, int, int], float] = {}
+    times: Dict[Tuple[int, int], float] = {}
     for k in delays:
         cands = [2 * k, 4 * k, 0] if chunks is None else [c for c in chunks if c == 0 or c % k == 0]
         for c in dict.fromkeys(cands):
-            pipelined = (c == 0 and k >= 4 and
-                         not (reinv_period > 0 and (reinv_on_accepted or precision == "fp64")))
-            for g in (dict.fromkeys(blocks) if pipelined else (0,)):
-                times[(int(k), int(c), int(g))] = _time_sweeps(
-                    inputs, pos, precision, k, c, reinv_period, reinv_on_accepted, warm_sweeps,
-                    timed_sweeps, g)
+            times[(int(k), int(c))] = _time_sweeps(inputs, pos, precision, k, c, reinv_period,
+                                                   reinv_on_accepted, warm_sweeps, timed_sweeps)
     best = min(times, key=times.get)
     return best, times

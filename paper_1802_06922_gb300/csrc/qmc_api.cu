@@ -237,7 +237,6 @@ extern "C" qmc_status qmc_system_create(const qmc_system_desc* desc, qmc_system_
   if (!(d.step >= 0.0)) return fail(QMC_EINVAL, "step must be >= 0");
   if (!(d.drift_a >= 0.0) || !std::isfinite(d.drift_a)) return fail(QMC_EINVAL, "drift_a must be >= 0");
   if (d.prop_chunk < 0) return fail(QMC_EINVAL, "prop_chunk must be >= 0");
-  if (d.prop_blocks < 0) return fail(QMC_EINVAL, "prop_blocks must be >= 0");
   if (d.delay_k < 1 || d.delay_k > kMaxDelay) return fail(QMC_EINVAL, "delay_k must be in [1, %d]", kMaxDelay);
   if (d.prec < QMC_FP64 || d.prec > QMC_FP32_BF16TAB) return fail(QMC_EINVAL, "unknown precision");
   if (d.move != QMC_MOVE_METROPOLIS && d.move != QMC_MOVE_DRIFT) return fail(QMC_EINVAL, "unknown move");
@@ -771,12 +770,8 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
   w->pf_ready = false;
   auto propose_block = [&](int e0, int e1, uint32_t tt, void* Pbuf, Prop* prbuf,
                            cudaStream_t ps) -> qmc_status {
-    const int cap = ps == w->side ? s->d.prop_blocks : 0;
     { Bracket b(w, ps, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, tt, e0, e1, prbuf, ps)); }
-    {
-      Bracket b(w, ps, QMC_K_VGL);
-      QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, prbuf, Pbuf, cap, ps));
-    }
+    { Bracket b(w, ps, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, prbuf, Pbuf, ps)); }
     return QMC_OK;
   };
   bool joined = true;             // the side stream's work has been joined back into st

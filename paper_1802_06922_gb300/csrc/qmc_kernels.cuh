@@ -156,26 +156,22 @@ __global__ void __launch_bounds__(256, sizeof(TT) == 8 ? 1 : 2) k_vgl_proposals(
   constexpr int V = TabVec<TT>::V;
   const int ns = e0 < S.n_up ? S.n_up : S.n_dn;
   const int chunks = (ns + 32 * V - 1) / (32 * V);
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nmov = (long long)Wk.n_w * (e1 - e0);
-  const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
-  // a full grid gives each warp one (move, orbital chunk) item; a smaller grid (the gather
-  // that runs beside the other spin block's moves) loops over them
-  for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-       gw < nmov * chunks; gw += stride) {
-    const int ch = (int)(gw % chunks);
-    const long long mv = gw / chunks;
-    const Prop p = prop[mv];
-    const double r[3] = {p.x, p.y, p.z};
-    TW* o = out + (size_t)mv * 5 * Wk.ld_v;
-    vgl_warp<TT, TW>(S, r, ch * 32 * V, ns, o, Wk.ld_v);
-    // the padding columns N_s..ld_v-1 of the five rows are zero, as in the current rows that
-    // an accepted move's rows replace whole (the buffer also serves the other block's moves)
-    if (ch == chunks - 1) {
-      const int lane = threadIdx.x & 31;
-      for (int j = ns + lane; j < Wk.ld_v; j += 32)
+  if (gw >= nmov * chunks) return;
+  const int ch = (int)(gw % chunks);
+  const long long mv = gw / chunks;
+  const Prop p = prop[mv];
+  const double r[3] = {p.x, p.y, p.z};
+  TW* o = out + (size_t)mv * 5 * Wk.ld_v;
+  vgl_warp<TT, TW>(S, r, ch * 32 * V, ns, o, Wk.ld_v);
+  // the padding columns N_s..ld_v-1 of the five rows are zero, as in the current rows that an
+  // accepted move's rows replace whole (the buffer also serves the other spin block's moves)
+  if (ch == chunks - 1) {
+    const int lane = threadIdx.x & 31;
+    for (int j = ns + lane; j < Wk.ld_v; j += 32)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) o[(size_t)q * Wk.ld_v + j] = TW(0);
-    }
+      for (int q = 0; q < 5; ++q) o[(size_t)q * Wk.ld_v + j] = TW(0);
   }
 }
 

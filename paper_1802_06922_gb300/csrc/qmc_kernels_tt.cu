@@ -18,13 +18,12 @@ cudaError_t vgl_current(const SysParams& S, const WalkParams& W, cudaStream_t st
 
 template <class TT, class TW>
 cudaError_t vgl_proposals(const SysParams& S, const WalkParams& W, int e0, int e1,
-                          const void* prop, void* out, int max_blocks, cudaStream_t st) {
+                          const void* prop, void* out, cudaStream_t st) {
   constexpr int V = TabVec<TT>::V;
   const int ns = e0 < S.n_up ? S.n_up : S.n_dn;
   const long long chunks = (ns + 32 * V - 1) / (32 * V);
   const long long warps = (long long)W.n_w * (e1 - e0) * chunks;
-  long long blocks = (warps * 32 + 255) / 256;
-  if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+  const long long blocks = (warps * 32 + 255) / 256;
   k_vgl_proposals<TT, TW><<<(unsigned)blocks, 256, 0, st>>>(
       S, W, e0, e1, static_cast<const Prop*>(prop), static_cast<TW*>(out));
   return cudaGetLastError();

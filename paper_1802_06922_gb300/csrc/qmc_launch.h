@@ -40,9 +40,8 @@ const TwLaunch& tw_launch_f32();
 struct TtLaunch {
   int vec;   // orbitals per 16-byte load
   cudaError_t (*vgl_current)(const SysParams&, const WalkParams&, cudaStream_t);
-  // (max_blocks > 0 caps the grid; the kernel then loops over its work)
   cudaError_t (*vgl_proposals)(const SysParams&, const WalkParams&, int e0, int e1,
-                               const void* prop, void* out, int max_blocks, cudaStream_t);
+                               const void* prop, void* out, cudaStream_t);
   // drift-diffusion sweep of electrons [e0, e1) with in-kernel orbital evaluation
   cudaError_t (*sweep_drift)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
                              int k, int reinv_period, int reinv_on_acc, int ext_flush,

@@ -35,7 +35,7 @@ class SystemDesc(C.Structure):
                 ("move", C.c_int), ("step", C.c_double), ("delay_k", C.c_int),
                 ("reinv_period", C.c_int), ("reinv_on_accepted", C.c_int),
                 ("seed", C.c_uint64), ("logdet_period", C.c_int), ("drift_a", C.c_double),
-                ("prop_chunk", C.c_int), ("prop_blocks", C.c_int)]
+                ("prop_chunk", C.c_int)]
 
 
 _vp, _i, _d, _sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
@@ -143,8 +143,7 @@ class System:
 
     def __init__(self, n_up, n_dn, L, ions, precision="fp64", move="metropolis", step=0.3,
                  delay_k=1, reinv_period=0, reinv_on_accepted=False, seed=0, ion_Z=4.0,
-                 kappa=1.0, with_potential=True, logdet_period=0, drift_a=0.0, prop_chunk=0,
-                 prop_blocks=0):
+                 kappa=1.0, with_potential=True, logdet_period=0, drift_a=0.0, prop_chunk=0):
         lib = load()
         ions = np.ascontiguousarray(np.asarray(ions, dtype=np.float64).reshape(-1, 3))
         self._ions = ions
@@ -153,7 +152,7 @@ class System:
                        int(bool(with_potential)), PRECISIONS[precision], MOVES[move],
                        float(step), int(delay_k), int(reinv_period), int(bool(reinv_on_accepted)),
                        int(seed) & 0xFFFFFFFFFFFFFFFF, int(logdet_period), float(drift_a),
-                       int(prop_chunk), int(prop_blocks))
+                       int(prop_chunk))
         h = C.c_void_p()
         _check(lib.qmc_system_create(C.byref(d), C.byref(h)))
         self.h = h
@@ -483,7 +482,7 @@ def slater_invert_noalloc(A, Binv, logdet=None, sign=None, stream=None):
 
 def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0,
                        reinv_on_accepted=False, step=None, move=None,
-                       logdet_period=0, drift_a=0.0, prop_chunk=0, prop_blocks=0) -> System:
+                       logdet_period=0, drift_a=0.0, prop_chunk=0) -> System:
     """System (with spline table and Jastrow functors) from a ``synthetic.build_inputs``
     dictionary, or any dictionary with the same keys."""
     spec = inputs["spec"]
@@ -492,8 +491,7 @@ def system_from_inputs(inputs: dict, precision="fp64", delay_k=1, reinv_period=0
                delay_k=delay_k, reinv_period=reinv_period,
                reinv_on_accepted=reinv_on_accepted, seed=inputs["seed"], ion_Z=spec.ion_Z,
                kappa=spec.kappa, with_potential=spec.with_potential,
-               logdet_period=logdet_period, drift_a=drift_a, prop_chunk=prop_chunk,
-               prop_blocks=prop_blocks)
+               logdet_period=logdet_period, drift_a=drift_a, prop_chunk=prop_chunk)
     s.set_spline(inputs["coef"])
     j = inputs["jastrow"]
     for which, key in enumerate(("eI", "same", "opp")):

@@ -228,8 +228,7 @@ def test_refinement_beyond_the_exact_slice_bound_falls_back_to_fp64():
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_proposal_batch_does_not_change_the_chain(precision):
     """The proposal batch (moves whose proposals and orbital rows one launch pair forms) is a
-    launch parameter: batches of 8 and 24 moves and the whole block (with a full or a capped
-    gather grid) give identical chains.
+    launch parameter: batches of 8 and 24 moves and the whole block give identical chains.
     Delay windows end at batch ends, so bit-identical single-precision results need window
     ends that do not depend on the batch: spin blocks and the re-inversion period are
     multiples of k here, as at the benched workload (with other sizes the chains still make
@@ -237,10 +236,9 @@ def test_proposal_batch_does_not_change_the_chain(precision):
     inputs = build_inputs(small_spec(40, 32, grid=12), n_walkers=3)
     out = []
     # whole-block batches form one block's proposals beside the other block's moves and the
-    # next sweep's ahead, by a full grid or by 3 looping thread blocks
-    for chunk, blocks in ((0, 0), (0, 3), (8, 0), (24, 0)):
+    # next sweep's up-block proposals ahead
+    for chunk in (0, 8, 24):
         s = q.system_from_inputs(inputs, precision=precision, delay_k=8, prop_chunk=chunk,
-                                 prop_blocks=blocks,
                                  reinv_period=16 if precision == "fp32" else 0,
                                  logdet_period=16 if precision == "fp32" else 0)
         w = q.Walkers(s, inputs["pos"])
