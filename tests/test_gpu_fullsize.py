@@ -96,12 +96,14 @@ def test_full_size_sampled_parity(preset, precision, k, period, on_acc, sample, 
 
 @pytest.mark.parametrize("precision,anchor", [("fp32", 128), ("bf16", 128), ("fp32", 1024)])
 def test_logpsi_over_many_sweeps(precision, anchor):
-    """ln|Psi| of the single-precision forms stays tied to the FP64 oracle over 56 sweeps of
-    the 512-electron workload (k = 32, re-inversion every 128 moves, log-determinant anchor
-    every `anchor` moves; 1024 is the bench's cadence): the oracle recomputes ln|Psi| from
-    scratch at the GPU's final positions of sampled walkers. 56 sweeps (14336 moves per spin
-    block) end right after an anchor for both cadences, so the gate is the single-precision
-    floor; the drift the anchors removed along the way (their shifts) is reported."""
+    """ln|Psi| and E_L of the single-precision forms stay tied to the FP64 oracle over 56
+    sweeps of the 512-electron workload in the bench's launch form (k = 32, whole-block
+    proposal batches formed beside the other block's moves, every sweep a CUDA-graph replay,
+    re-inversion every 128 moves, log-determinant anchor every `anchor` moves; 1024 is the
+    bench's cadence): the oracle recomputes both from scratch at the GPU's final positions of
+    sampled walkers. 56 sweeps (14336 moves per spin block) end right after an anchor for both
+    cadences, so the ln|Psi| gate is the single-precision floor; the drift the anchors removed
+    along the way (their shifts) is reported."""
     spec = spec_for("sj512")
     inputs = build_inputs(spec)
     coef = inputs["coef"]
@@ -117,10 +119,14 @@ def test_logpsi_over_many_sweeps(precision, anchor):
         res, shift = w.precision_report()
         shifts.append(shift.ravel())
         resid.append(res.ravel())
-    _, lp = w.measure()
+    assert w.graph_stats()[1] == 56                   # every sweep replayed, as in the bench
+    e_gpu, lp = w.measure()
     final = w.positions()
     osys = OracleSystem(inputs, coef=coef)
     errs = [lp[wid] - osys.wf.log_psi(final[wid])[0] for wid in (0, 101, 255)]
+    for wid in (0, 101, 255):
+        e_ref = osys.measure(osys.walker(final[wid], wid))[0]
+        assert abs(e_gpu[wid] - e_ref) / spec.n_elec < 1e-5, (wid, e_gpu[wid], e_ref)
     sh = np.abs(np.concatenate(shifts))
     sh = sh[np.isfinite(sh)]                      # NaN before a walker's first anchor
     print(f"{precision} anchor {anchor}: ln|Psi| error after 56 sweeps {np.round(errs, 7)}; anchor "
