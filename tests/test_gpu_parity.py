@@ -62,10 +62,11 @@ def test_plane_wave_fp64_parity_and_zero_variance():
     assert np.all(np.abs(e_gpu - e_ref) / e_ref < ((2 * np.pi / 10) * (10 / 32)) ** 2)
 
 
-@pytest.mark.parametrize("delay_k", [1, 3, 8])
+@pytest.mark.parametrize("delay_k", [1, 3, 8, 32])
 def test_slater_jastrow_fp64_parity_ragged(delay_k):
     # 70 up / 66 down electrons: two 64-orbital chunks per FP64 warp with a ragged tail,
-    # a delay window that does not divide the block
+    # a delay window that does not divide the block; k = 32 fills the window to the pair
+    # matrix's full 32 rows
     inputs = build_inputs(small_spec(70, 66, grid=12, n_orb=72), n_walkers=2)
     ids = np.arange(2)
     tr, en, _ = _gpu_run(inputs, ids, 1, delay_k=delay_k)
