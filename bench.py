@@ -271,8 +271,10 @@ def class_roofline(name, ms, n, spec, precision, moves_per_step, steps, peaks, d
                "per_unit": f"Binv0 read + write 2*N_s^2*{tw} B + window rows Phi, U "
                            f"2*k*N_s*{tw} B = {per} B per walker and spin block"}
     elif name == "refine":
-        # error-free residual: 21 BF16 slice-pair products of N_s x N_s x N_s on tcgen05
-        pairs = sum(1 for i in range(1, 7) for j in range(1, 7) if i + j <= 7)
+        # error-free residual: BF16 slice-pair products of N_s x N_s x N_s on tcgen05, 15
+        # with 8-bit slices (N_s <= 256) and 21 with 7-bit slices (N_s <= 512)
+        slices, top = (5, 6) if ns <= 256 else (6, 7)
+        pairs = sum(1 for i in range(1, slices + 1) for j in range(1, slices + 1) if i + j <= top)
         per = pairs * 2 * ns ** 3
         peak = peaks.get("bf16_tflops", 1899.6)
         out = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,

@@ -110,11 +110,14 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
     k_refine_scales<TW><<<dim3(W.n_w, 2), kThreads, 0, st>>>(S, W, spin);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = refine_tc_smem_bytes();
-    e = cudaFuncSetAttribute(k_refine_residual_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // 8-bit slices where K = N_s allows them (15 slice pairs), 7-bit ones up to K = 512
+    const bool b8 = ns <= RsSlicing<8>::kMaxK;
+    const size_t smem = refine_tc_smem_bytes(b8 ? RsSlicing<8>::kSlices : RsSlicing<7>::kSlices);
+    auto kern = b8 ? k_refine_residual_tc<8> : k_refine_residual_tc<7>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nt = (ns + kRsRows - 1) / kRsRows;
-    k_refine_residual_tc<<<dim3(W.n_w, nt * nt), kThreads, smem, st>>>(S, W, spin);
+    kern<<<dim3(W.n_w, nt * nt), kThreads, smem, st>>>(S, W, spin);
     return cudaGetLastError();
   } else {
     // double precision needs no refinement: FP64 Gauss-Jordan of that spin block

@@ -417,13 +417,17 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
 // run through terms up to ~10^4 times larger than their result (random plane-wave
 // Slater matrices have condition numbers 10^3..10^5), so FP32 or 3xTF32 products are not
 // enough. Here each row of A (electron e) and each row of Binv (f; Binv[f][j] = X[j][f])
-// is scaled by a power of two 2^E so that |x| < 1 and cut into kRsSlices slices of
-// kRsBits bits (RN splitting; slice i holds an integer times 2^(-kRsBits i), exact in
-// BF16). The product of slice i of A with slice j of X is a sum of K products that are
-// integers in units of 2^(-kRsBits (i+j)) and bounded by K 2^(2 kRsBits) <= 2^23 for K <= 512,
-// so an FP32 accumulator sums it without rounding. The pairs of level i+j = 2 and 3 carry
-// the cancellation and get one exact accumulator each; the pairs of levels 4..kRsMaxLevel
-// (magnitude below 2^-14 of the first) share a third, ordinary FP32 accumulator. The
+// is scaled by a power of two 2^E so that |x| < 1 and cut into S slices of b bits (RN
+// splitting; slice i holds an integer times 2^(-b i), |integer| <= 2^b for the first slice
+// and 2^(b-1) for the others, exact in BF16). The product of slice i of A with slice j of X
+// is a sum of K products that are integers in units of 2^(-b (i+j)); the level-2 sum and
+// the two level-3 sums together are bounded by K 2^(2b), and K 2^(2b) <= 2^24 lets an FP32
+// accumulator sum them without rounding. Two slicings meet that bound: b = 8 with five
+// slices and levels up to 6 (15 slice pairs) for K <= 256, and b = 7 with six slices and
+// levels up to 7 (21 pairs) for K <= 512; both represent each scaled element to 2^-41 or
+// better and drop only pairs below 2^-48. The pairs of level i+j = 2 and 3 carry the
+// cancellation and get one exact accumulator each; the pairs of the higher levels
+// (magnitude below 2^-2b of the first) share a third, ordinary FP32 accumulator. The
 // epilogue forms R = delta - 2^(E_e+F_f) (L2 + L3 + L4+) with error-free (TwoSum) steps.
 // This is an Ozaki-type splitting (Ozaki, Ogita, Oishi, Rump, "Error-free transformations
 // of matrix multiplication by using fast routines of matrix multiplication"), restated
@@ -431,14 +435,15 @@ __global__ void __launch_bounds__(256) k_flush_tc(SysParams S, WalkParams Wk, in
 // =============================================================================
 constexpr int kRsRows = 128;      // M and N of the output tile
 constexpr int kRsK = 32;          // BF16 K elements staged per chunk
-constexpr int kRsSlices = 6;
-constexpr int kRsBits = 7;
-constexpr int kRsMaxLevel = 7;    // slice pairs (i, j) with i + j <= kRsMaxLevel
+// slices of kBits bits: their count, the highest level of the pairs taken, the largest K
+template <int kBits> struct RsSlicing;
+template <> struct RsSlicing<8> { static constexpr int kSlices = 5, kMaxLevel = 6, kMaxK = 256; };
+template <> struct RsSlicing<7> { static constexpr int kSlices = 6, kMaxLevel = 7, kMaxK = 512; };
 constexpr int kRsTile = kRsRows * kRsK;            // BF16 elements of one slice tile
-constexpr int kRsMaxK = 512;      // K <= 512 keeps every exact accumulator below 2^23
+constexpr int kRsMaxK = RsSlicing<7>::kMaxK;       // beyond it the FP64 re-inversion serves
 
-__host__ __device__ inline size_t refine_tc_smem_bytes() {
-  return (size_t)2 * 2 * kRsSlices * kRsTile * 2 + 2 * kRsRows * sizeof(int) + 64;
+__host__ __device__ inline size_t refine_tc_smem_bytes(int slices) {
+  return (size_t)2 * 2 * slices * kRsTile * 2 + 2 * kRsRows * sizeof(int) + 64;
 }
 
 // Power-of-two exponent E of every row of A (operand 0: orbital values of the spin
@@ -477,9 +482,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
-// Splits 16 consecutive K elements of one row into the kRsSlices BF16 slice tiles.
+// Splits 16 consecutive K elements of one row into the BF16 slice tiles of kBits bits.
+template <int kBits>
 __device__ __forceinline__ void stage_slices16(const float (&x)[16], float inv_scale,
                                                __nv_bfloat16* tiles, int r, int k) {
+  constexpr int kRsSlices = RsSlicing<kBits>::kSlices, kRsBits = kBits;
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
     float rem[8];
@@ -512,8 +519,10 @@ __device__ __forceinline__ void stage_slices16(const float (&x)[16], float inv_s
 // w's spin block, stored transposed (Rg[f][e]) in the first N_s^2 floats of the walker's
 // FP64 work area (read by k_refine_update_tc), with max |R| into refine_max[w]. Chunks of 32 K elements are loaded into registers one chunk ahead,
 // split into BF16 slices in one of two shared-memory stages, and multiplied (one thread
-// issues the 21 slice-pair products per 16-wide K step) while the next chunk is split.
+// issues the 15 or 21 slice-pair products per 16-wide K step) while the next chunk is split.
+template <int kBits>
 __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, WalkParams Wk, int spin) {
+  constexpr int kRsSlices = RsSlicing<kBits>::kSlices, kRsMaxLevel = RsSlicing<kBits>::kMaxLevel;
   extern __shared__ __align__(1024) char smem_rt[];
   __shared__ uint64_t bar[2];
   __shared__ uint32_t tbase;
@@ -584,8 +593,8 @@ __global__ void __launch_bounds__(256, 1) k_refine_residual_tc(SysParams S, Walk
     }
     __nv_bfloat16* ta = tiles + (size_t)(st * 2 + 0) * kRsSlices * kRsTile;
     __nv_bfloat16* tb = tiles + (size_t)(st * 2 + 1) * kRsSlices * kRsTile;
-    stage_slices16(xa, inv_a, ta, lr, lk);
-    stage_slices16(xb, inv_b, tb, lr, lk);
+    stage_slices16<kBits>(xa, inv_a, ta, lr, lk);
+    stage_slices16<kBits>(xb, inv_b, tb, lr, lk);
     tc::fence_async_smem();
     ok = __syncthreads_and(ok);
     if (!ok) break;

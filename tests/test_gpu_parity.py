@@ -162,12 +162,13 @@ def test_orbitals_and_inverse_at_setup(precision):
     s.close()
 
 
-def test_fp32_refinement_reaches_storage_accuracy():
+@pytest.mark.parametrize("ns,bound", [(64, 64 * 2.0 ** -24), (256, 1e-5)])
+def test_fp32_refinement_reaches_storage_accuracy(ns, bound):
     """The single-precision re-inversion (one Newton step with the error-free residual
-    computed from BF16 slice products on the tensor cores) leaves an inverse whose error is
-    set by FP32 storage, not by the condition number or the number of rank-k updates since
-    the last re-inversion."""
-    inputs = build_inputs(small_spec(64, 64, grid=12, n_orb=72), n_walkers=2)
+    computed from BF16 slice products on the tensor cores: 8-bit slices at both sizes here)
+    leaves an inverse whose error is set by FP32 storage, not by the condition number or the
+    number of rank-k updates since the last re-inversion."""
+    inputs = build_inputs(small_spec(ns, ns, grid=12, n_orb=ns + 8), n_walkers=2)
     errs = {}
     for period in (0, 16):
         s = q.system_from_inputs(inputs, precision="fp32", delay_k=4, reinv_period=period)
@@ -177,13 +178,14 @@ def test_fp32_refinement_reaches_storage_accuracy():
         for wk in range(2):
             orb = w.orbitals(wk)
             for spin in range(2):
-                A = orb[64 * spin:64 * (spin + 1), 0, :64]
+                A = orb[ns * spin:ns * (spin + 1), 0, :ns]
                 ref = np.linalg.inv(A).T
                 worst = max(worst, np.abs(w.inverse(wk, spin) - ref).max() / np.abs(ref).max())
         errs[period] = worst
         w.close()
         s.close()
-    assert errs[16] < 64 * 2.0 ** -24, errs
+    print(f"N_s = {ns}: max inverse error relative to max |A^-1|: {errs}")
+    assert errs[16] < bound, errs
     assert errs[16] <= errs[0], errs
 
 
