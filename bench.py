@@ -223,7 +223,7 @@ TRAFFIC_SJ512_FP32 = {
     "vgl": [((3019.3e6 + 363.2e6) / 65536, "move", None)],   # k_vgl_proposals: 65,536 moves
     "sweep": [((46.3e6 + 7.1e6) / 8192, "move", 32)],         # k_sweep_win: 32 moves x 256 walkers
     "flush": [((80.9e6 + 6.6e6) / 256, "walker", 32)],        # k_flush_tc<32>: one spin block
-    "refine": [((227.6e6 + 47.8e6) / 256, "walker", None)],   # k_refine_residual_tc
+    "refine": [((228.0e6 + 48.0e6) / 256, "walker", None)],   # k_refine_residual_tc (8-bit slices)
     "refine_update": [((218.1e6 + 45.4e6) / 256, "walker", None)],   # k_refine_update_tc
     "energy": [((674.4e6 + 3.3e6) / 256, "walker", None)],    # k_local_energy
     "logdet": [((234.2e6 + 166.1e6) / 256, "walker", None)],  # k_logdet_anchor
