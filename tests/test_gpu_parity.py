@@ -8,7 +8,7 @@ import pytest
 from synthetic import build_inputs, small_spec, spec_for
 
 from parity_util import (assert_logpsi, assert_ratio_gate, assert_trace_close, bf16_round,
-                         oracle_vmc, rel_err)
+                         logpsi_tol, oracle_vmc, rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -158,6 +158,15 @@ def test_orbitals_and_inverse_at_setup(precision):
             A_gpu = w.orbitals(wk)[first:first + ns, 0, :ns]
             res = np.abs(A_gpu @ Binv.T - np.eye(ns)).max()
             assert res < (1e-11 if precision == "fp64" else 2e-5), res
+    # ln|Psi| at the initial positions (single precision: FP32 Gauss-Jordan, two Newton steps
+    # and the log-det anchor) against the oracle's from-scratch value
+    from oracle.vmc import OracleSystem
+    _, lp = w.measure()
+    osys = OracleSystem(inputs)
+    for wk in range(2):
+        ref = osys.wf.log_psi(inputs["pos"][wk])[0]
+        tol = 1e-10 * max(1.0, abs(ref)) if precision == "fp64" else logpsi_tol(136)
+        assert abs(lp[wk] - ref) <= tol, (wk, lp[wk], ref)
     w.close()
     s.close()
 
