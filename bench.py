@@ -90,8 +90,6 @@ def workload(spec, precision, delay_k, reinv_period, on_accepted=False, logdet_p
     upd = "Sherman-Morrison rank-1" if delay_k == 1 else f"delayed rank-{delay_k}"
     if prop_chunk:
         upd += f" (proposals in batches of {prop_chunk} moves)"
-    elif delay_k >= 4 and precision != "fp64" and not on_accepted:
-        upd += " (each spin block's proposals formed beside the other block's moves)"
     what = "accepted moves" if on_accepted else "moves"
     re = (("FP64 re-inversion" if precision == "fp64" else "re-inversion (error-free Newton step)")
           + f" every {reinv_period} {what}") if reinv_period else "no re-inversion"

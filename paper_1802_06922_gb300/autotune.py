@@ -3,9 +3,8 @@
 A larger delay rank k makes each move's window work (the d, z and x of the delayed update)
 longer and each flush rarer; a smaller proposal batch (moves whose proposals and orbital
 rows one launch pair forms) keeps those rows in L2 until the sweep reads them but adds
-launches, while whole-block batches let one spin block's proposals be formed beside the
-other block's moves. The best pair depends on the system size, the walker count and the GPU,
-so `tune_launch` times whole sweeps for every candidate pair on the caller's own inputs and
+launches. The best pair depends on the system size, the walker count and the GPU, so
+`tune_launch` times whole sweeps for every candidate pair on the caller's own inputs and
 keeps the fastest (`tune_delay` does the same for k alone). A sweep is timed as it runs in
 production, one CUDA-graph replay, by CUDA events on the launching stream, after warm-up
 sweeps that capture its graphs. Neither parameter changes the Markov chain.

@@ -75,7 +75,6 @@ struct qmc_system_s {
   double* d_ions = nullptr;
   float* d_ionsf = nullptr;
   uint64_t ham_version = 0;    // bumped by every change of the Hamiltonian's terms
-  uint64_t table_version = 0;  // bumped by every new orbital table
   double* d_j3 = nullptr;      // three-body Jastrow coefficients [2][n_coef]
   int4* d_ew_n = nullptr;      // Ewald half set of integer k vectors
   double* d_ew = nullptr;      // c_k [n_k], the ions' rho_k [2][n_k], constant [1]
@@ -150,11 +149,6 @@ struct qmc_walkers_s {
   int chunk = 0;               // moves per launch of a spin block
   void* d_P = nullptr;         // proposal orbital values [W][chunk][5][ld_v]
   Prop* d_prop = nullptr;      // [W][chunk]
-  void* d_P2 = nullptr;        // the down block's, when proposals are pipelined (whole-block
-  Prop* d_prop2 = nullptr;     // batches): formed beside the up block's moves
-  bool pf_ready = false;       // d_P / d_prop hold the up block's proposals of sweep pf_sweep
-  uint32_t pf_sweep = 0;
-  uint64_t pf_table = 0;       // the system's table version they were evaluated with
   double* d_out = nullptr;     // [8] accumulate output
   long long* d_nacc = nullptr;
   long long proposed = 0;      // since the last accumulate
@@ -169,7 +163,6 @@ struct qmc_walkers_s {
   void* d_j3vgl = nullptr;     // three-body Jastrow terms per electron [W][n_e][5] (working precision)
   cudaStream_t side = nullptr; // the up block's last refinement of a sweep runs here, beside
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;   // the down block's moves
-  cudaEvent_t ev_prop = nullptr;  // the down block's pipelined proposals are ready
   int since_moves[2] = {0, 0}; // proposed moves per spin since the last re-inversion
   int since_anchor[2] = {0, 0};// proposed moves per spin since the last log-det anchor
   GraphCache graphs;
@@ -352,7 +345,6 @@ extern "C" qmc_status qmc_system_set_spline(qmc_system_t s, int nx, int ny, int 
     P.inv_deltaf[c] = (float)P.inv_delta[c];
   }
   s->has_spline = true;
-  ++s->table_version;
   return QMC_OK;
 }
 
@@ -557,7 +549,6 @@ qmc_status setup_state(qmc_walkers_s* w, cudaStream_t st) {
   QMC_CUDA(cudaMemsetAsync(w->W.acc_since, 0, sizeof(int) * 2 * w->W.n_w, st));
   w->since_moves[0] = w->since_moves[1] = 0;
   w->since_anchor[0] = w->since_anchor[1] = 0;
-  w->pf_ready = false;
   w->energy_valid = true;
   w->energy_version = s->ham_version;
   return check_err(w, st);
@@ -567,8 +558,7 @@ void free_walkers(qmc_walkers_s* w) {
   WalkParams& W = w->W;
   void* ptrs[] = {W.pos, W.binv[0], W.binv[1], W.binv_alt[0], W.binv_alt[1], W.vgl, W.logdet,
                   W.sgn, W.wid, W.weight, W.e_loc, W.log_psi, W.n_acc, W.acc_since, W.scratch64,
-                  W.err, w->d_P, w->d_prop, w->d_P2, w->d_prop2, w->d_out, w->d_nacc,
-                  w->d_forced, W.win_phi,
+                  W.err, w->d_P, w->d_prop, w->d_out, w->d_nacc, w->d_forced, W.win_phi,
                   W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
                   W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count, W.nl_val,
                   w->d_j3vgl};
@@ -578,7 +568,6 @@ void free_walkers(qmc_walkers_s* w) {
   if (w->cap) cudaStreamDestroy(w->cap);
   if (w->ev_fork) cudaEventDestroy(w->ev_fork);
   if (w->ev_join) cudaEventDestroy(w->ev_join);
-  if (w->ev_prop) cudaEventDestroy(w->ev_prop);
   if (w->side) cudaStreamDestroy(w->side);
 }
 
@@ -621,9 +610,6 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
   while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
   const size_t np = proposals ? nw * (size_t)w->chunk : 1;
-  // whole-block proposal batches of both spin blocks: a second buffer lets the proposals of
-  // one block be formed while the other block moves
-  const bool pipe = proposals && w->chunk >= ns_max && P.n_up > 0 && P.n_dn > 0;
   const size_t nb_up = (size_t)std::max(P.n_up, 1) * std::max(P.n_up, 1);
   const size_t nb_dn = (size_t)std::max(P.n_dn, 1) * std::max(P.n_dn, 1);
   // the second inverse buffers serve the batched single-precision re-inversion
@@ -647,8 +633,6 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.err, sizeof(int)},
       {(void**)&w->d_P, np * 5 * W.ld_v * tw},
       {(void**)&w->d_prop, np * sizeof(Prop)},
-      {(void**)&w->d_P2, pipe ? np * 5 * W.ld_v * tw : 0},
-      {(void**)&w->d_prop2, pipe ? np * sizeof(Prop) : 0},
       {(void**)&w->d_out, 8 * sizeof(double)},
       {(void**)&w->d_nacc, sizeof(long long)},
       {(void**)&W.win_phi, nw * (size_t)s->d.delay_k * W.ld_v * tw},
@@ -687,8 +671,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   if (cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ev_prop, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     free_walkers(w);
     delete w;
     return fail(QMC_ECUDA, "cannot create the walker set's side stream");
@@ -759,48 +742,15 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
   const bool drift = s->d.move == QMC_MOVE_DRIFT;
   const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
                    !(period > 0 && s->d.prec == QMC_FP64);
-  // Pipelined proposals (whole-block batches of Metropolis moves): a block's proposals and
-  // their orbital rows depend only on that block's positions, which the other block's moves
-  // leave alone. So the down block's are formed on the side stream while the up block moves,
-  // and once the up block's moves are done, the next sweep's up-block proposals are formed
-  // there while the down block moves. Both are gathers bound by HBM; the moves are bound by
-  // latency.
-  const bool pipe = !drift && ext && w->d_P2 != nullptr;
-  const bool have_pf = pipe && w->pf_ready;
-  w->pf_ready = false;
-  auto propose_block = [&](int e0, int e1, uint32_t tt, void* Pbuf, Prop* prbuf,
-                           cudaStream_t ps) -> qmc_status {
-    { Bracket b(w, ps, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, tt, e0, e1, prbuf, ps)); }
-    { Bracket b(w, ps, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, e0, e1, prbuf, Pbuf, ps)); }
-    return QMC_OK;
-  };
   bool joined = true;             // the side stream's work has been joined back into st
   for (int spin = 0; spin < 2; ++spin) {
     const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
     const int pchunk = drift ? std::max(b1 - b0, 1) : w->chunk;
-    void* Pbuf = pipe && spin ? w->d_P2 : w->d_P;
-    Prop* prbuf = pipe && spin ? w->d_prop2 : w->d_prop;
     for (int pc0 = b0; pc0 < b1; pc0 += pchunk) {
       const int pc1 = std::min(b1, pc0 + pchunk);
-      if (pipe) {
-        if (spin == 0) {
-          if (!have_pf) {
-            qmc_status r = propose_block(pc0, pc1, t, Pbuf, prbuf, st);
-            if (r != QMC_OK) return r;
-          }
-          QMC_CUDA(cudaEventRecord(w->ev_fork, st));
-          QMC_CUDA(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
-          qmc_status r = propose_block(P.n_up, P.n_e, t, w->d_P2, w->d_prop2, w->side);
-          if (r != QMC_OK) return r;
-          QMC_CUDA(cudaEventRecord(w->ev_prop, w->side));
-          QMC_CUDA(cudaEventRecord(w->ev_join, w->side));
-          joined = false;
-        } else {
-          QMC_CUDA(cudaStreamWaitEvent(st, w->ev_prop, 0));
-        }
-      } else if (!drift) {
-        qmc_status r = propose_block(pc0, pc1, t, Pbuf, prbuf, st);
-        if (r != QMC_OK) return r;
+      if (!drift) {
+        { Bracket b(w, st, QMC_K_PROPOSE); QMC_CUDA(launch_proposals(P, W, t, pc0, pc1, w->d_prop, st)); }
+        { Bracket b(w, st, QMC_K_VGL); QMC_CUDA(s->tt->vgl_proposals(P, W, pc0, pc1, w->d_prop, w->d_P, st)); }
       }
       if (!ext) {
         Bracket b(w, st, QMC_K_SWEEP);
@@ -808,7 +758,7 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
           QMC_CUDA(s->tt->sweep_drift(P, W, t, pc0, pc1, kc, period, s->d.reinv_on_accepted,
                                       0, fixed_node, st));
         else
-          QMC_CUDA(s->tw->sweep(P, W, t, pc0, pc1, kc, Pbuf, prbuf, pc0, pc1 - pc0,
+          QMC_CUDA(s->tw->sweep(P, W, t, pc0, pc1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
                                 period, s->d.reinv_on_accepted, 0, fixed_node, st));
         continue;
       }
@@ -820,7 +770,7 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
           if (drift)
             QMC_CUDA(s->tt->sweep_drift(P, W, t, e0, e1, kc, 0, 0, 1, fixed_node, st));
           else
-            QMC_CUDA(s->tw->sweep(P, W, t, e0, e1, kc, Pbuf, prbuf, pc0, pc1 - pc0,
+            QMC_CUDA(s->tw->sweep(P, W, t, e0, e1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
                                   0, 0, 1, fixed_node, st));
         }
         { Bracket b(w, st, QMC_K_FLUSH); QMC_CUDA(s->tw->flush(P, W, spin, st)); }
@@ -864,16 +814,6 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
         e0 = e1;
       }
     }
-    if (pipe && spin == 0) {
-      // the up block's positions are final for this sweep: its proposals of the next one
-      QMC_CUDA(cudaEventRecord(w->ev_fork, st));
-      QMC_CUDA(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
-      qmc_status r = propose_block(0, P.n_up, t + 1, w->d_P, w->d_prop, w->side);
-      if (r != QMC_OK) return r;
-      QMC_CUDA(cudaEventRecord(w->ev_join, w->side));
-      joined = false;
-      w->pf_ready = true;
-    }
   }
   if (!joined) QMC_CUDA(cudaStreamWaitEvent(st, w->ev_join, 0));
   return QMC_OK;
@@ -885,14 +825,12 @@ void put_state(Bytes& b, const qmc_walkers_s* w) {
   put(b, w->W);
   put(b, w->since_moves);
   put(b, w->since_anchor);
-  put(b, w->pf_ready);
 }
 
 void take_state(const unsigned char*& p, qmc_walkers_s* w) {
   take(p, w->W);
   take(p, w->since_moves);
   take(p, w->since_anchor);
-  take(p, w->pf_ready);
 }
 
 // Everything the launches of walker set w's sweep depend on besides the sweep index.
@@ -981,10 +919,6 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
       W.trace = w->trace + w->traced * (size_t)W.n_w * P.n_e * 8;
     if (w->d_forced && sw < w->forced_sweeps)
       W.forced = w->d_forced + (size_t)sw * W.n_w * P.n_e;
-    // proposals formed ahead by the previous sweep serve only the sweep and table they were
-    // made for
-    if (w->pf_ready && (w->pf_sweep != w->sweep || w->pf_table != s->table_version))
-      w->pf_ready = false;
     if (w->graphs.enabled && !w->profiling && !W.trace && !W.forced) {
       qmc_status r = sweep_graph(w, st);
       if (r != QMC_OK) return r;
@@ -997,8 +931,6 @@ extern "C" qmc_status qmc_sweep(qmc_walkers_t w, int n_sweeps, void* stream) {
     if (W.trace) ++w->traced;
     ++w->sweep;
     w->proposed += (long long)W.n_w * P.n_e;
-    w->pf_sweep = w->sweep;
-    w->pf_table = s->table_version;
   }
   if (w->d_forced) {
     QMC_CUDA(cudaStreamSynchronize(st));

@@ -498,8 +498,7 @@ __global__ void __launch_bounds__(kWinThreads, 2)
     gc[i] = (a < m && b < m) ? ci[a * kWinP + b] : TW(0);
   }
   for (int i = tid; i < m; i += nt) Wk.win_row[(size_t)w * kc + i] = e0 + sm.wt[i] - first;
-  // positions of this launch's electrons only: the other spin block's proposals may be
-  // reading theirs meanwhile
+  // positions of this launch's electrons (the only ones it can move)
   for (int i = tid; i < 3 * (e1 - e0); i += nt) {
     const int c = i / (e1 - e0), j = c * n_e + e0 + (i - c * (e1 - e0));
     gpos[j] = sm.posd[j];

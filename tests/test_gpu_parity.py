@@ -247,8 +247,6 @@ def test_proposal_batch_does_not_change_the_chain(precision):
     the same decisions, and the flushes round differently)."""
     inputs = build_inputs(small_spec(40, 32, grid=12), n_walkers=3)
     out = []
-    # whole-block batches form one block's proposals beside the other block's moves and the
-    # next sweep's up-block proposals ahead
     for chunk in (0, 8, 24):
         s = q.system_from_inputs(inputs, precision=precision, delay_k=8, prop_chunk=chunk,
                                  reinv_period=16 if precision == "fp32" else 0,
