@@ -69,7 +69,19 @@ static __global__ void __launch_bounds__(256) k_nlpp_pairs(SysParams S, WalkPara
   if (Wk.n_live && w >= *Wk.n_live) return;
   const double* P = Wk.pos + (size_t)w * 3 * S.n_e;
   const double rc2 = S.nl_rcut * S.nl_rcut;
-  auto inside = [&](const double (&x)[3], int I) {
+  // The test in single precision decides every pair whose r^2 is farther than a margin from
+  // rc^2 (the single-precision distance is off by far less: a few ulp of L per component);
+  // the few within it are decided in FP64, so the list is the FP64 one.
+  const float rc2f = (float)rc2, marg = 1e-4f * rc2f + 64.f * 1.2e-7f * S.Lf * S.Lf;
+  auto inside = [&](const double (&x)[3], const float (&xf)[3], int I) {
+    float r2f = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float d = min_image<float>(xf[c] - S.ionsf[c * S.n_ion + I], S.Lf, S.invLf);
+      r2f += d * d;
+    }
+    if (r2f > rc2f + marg) return false;
+    if (r2f < rc2f - marg && r2f > marg) return true;
     double r2 = 0.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -82,10 +94,12 @@ static __global__ void __launch_bounds__(256) k_nlpp_pairs(SysParams S, WalkPara
   for (int e0 = 0; e0 < S.n_e; e0 += blockDim.x) {
     const int e = e0 + tid;
     double x[3] = {0.0, 0.0, 0.0};
+    float xf[3] = {0.f, 0.f, 0.f};
     int c = 0;
     if (e < S.n_e) {
       x[0] = P[e]; x[1] = P[S.n_e + e]; x[2] = P[2 * S.n_e + e];
-      for (int I = 0; I < S.n_ion; ++I) c += inside(x, I);
+      xf[0] = (float)x[0]; xf[1] = (float)x[1]; xf[2] = (float)x[2];
+      for (int I = 0; I < S.n_ion; ++I) c += inside(x, xf, I);
     }
     // exclusive block scan of the counts
     int incl = c;
@@ -105,7 +119,7 @@ static __global__ void __launch_bounds__(256) k_nlpp_pairs(SysParams S, WalkPara
     if (c > 0) {
       int k = base + before + incl - c;
       for (int I = 0; I < S.n_ion; ++I)
-        if (inside(x, I)) {
+        if (inside(x, xf, I)) {
           if (k < cap) pairs[(size_t)w * cap + k] = e * S.n_ion + I;
           ++k;
         }
