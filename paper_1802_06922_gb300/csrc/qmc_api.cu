@@ -560,7 +560,8 @@ void free_walkers(qmc_walkers_s* w) {
                   W.sgn, W.wid, W.weight, W.e_loc, W.log_psi, W.n_acc, W.acc_since, W.scratch64,
                   W.err, w->d_P, w->d_prop, w->d_out, w->d_nacc, w->d_forced, W.win_phi,
                   W.win_u, W.win_cinv, W.win_row, W.win_m, W.refine_max, W.refine_last,
-                  W.logdet_shift, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count, W.nl_val,
+                  W.logdet_shift, W.refine_fb, W.rscale, W.r2, W.vnl, W.nl_pairs, W.nl_count,
+                  W.nl_val,
                   w->d_j3vgl};
   for (void* p : ptrs) cudaFree(p);
   w->graphs.clear();
@@ -643,6 +644,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.refine_max, nw * 2 * sizeof(float)},
       {(void**)&W.refine_last, nw * 2 * sizeof(float)},
       {(void**)&W.logdet_shift, nw * 2 * sizeof(float)},
+      {(void**)&W.refine_fb, nw * 2 * sizeof(int)},
       {(void**)&W.r2, nw * 2 * sizeof(double)},
       {(void**)&W.vnl, nw * sizeof(double)},
       {(void**)&W.nl_pairs, nw * (size_t)std::max(64, 2 * (int)ne) * sizeof(int)},
@@ -685,6 +687,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   cudaMemset(W.refine_max, 0, nw * 2 * sizeof(float));
   cudaMemset(W.refine_last, 0xFF, nw * 2 * sizeof(float));   // NaN: no refinement yet
   cudaMemset(W.logdet_shift, 0xFF, nw * 2 * sizeof(float));  // NaN: no anchor yet
+  cudaMemset(W.refine_fb, 0, nw * 2 * sizeof(int));
   cudaMemset(W.r2, 0, nw * 2 * sizeof(double));
   cudaMemset(W.vnl, 0, nw * sizeof(double));
   W.nl_cap = std::max(64, 2 * (int)ne);

@@ -104,6 +104,7 @@ struct WalkParams {
                        //               spin block (the two blocks' refinements may overlap)
   float* refine_last;  // [W][2]        max |I - A X| measured by the last refinement of each
                        //               spin block (before its Newton step); NaN if none yet
+  int* refine_fb;      // [W][2]        1 if the last refinement re-inverted in FP64
   float* logdet_shift; // [W][2]        change of ln|det A| made by the last log-det anchor
                        //               (anchor value minus the accumulated one); NaN if none
   int* rscale;         // [W][2][2][ld_v] power-of-two exponents of the rows of A and X

@@ -521,6 +521,11 @@ __host__ __device__ inline size_t invert_batch_smem_bytes(int n) { return gj_sme
 // step; the caller then falls back to the FP64 Gauss-Jordan re-inversion.
 // =============================================================================
 constexpr float kRefineMax = 1e-2f;
+// The batched refinement takes the Newton step up to kRefineTwoStep; above kRefineMax the
+// re-inversion's FP64 stage adds a second, compensated step in the walker's block
+// (0.05 -> 2.5e-3 -> 6e-6), and only a residual beyond that (or not finite) takes the FP64
+// Gauss-Jordan re-inversion.
+constexpr float kRefineTwoStep = 5e-2f;
 constexpr int kTileElems = 2 * 32 * 64;      // two 32 x 64 single-precision tiles
 
 __device__ __forceinline__ void dot2_step(float a, float b, float& P, float& E) {
@@ -1569,10 +1574,20 @@ __global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
   const float rm = Wk.refine_max[2 * w + spin];
-  if (!(rm <= kRefineMax)) reinvert_block<TW>(S, Wk, w, spin, smem_c);
+  bool fp64 = !(rm <= kRefineTwoStep);
+  if constexpr (sizeof(TW) == 4) {
+    if (!fp64 && rm > kRefineMax) {
+      // the batched step left about rm^2: a second step here; FP64 if even that is too far
+      float* tile = reinterpret_cast<float*>(smem_c);
+      const float r2 = refine_inverse(S, Wk, w, spin, tile, tile + kTileElems);
+      fp64 = !(r2 <= kRefineMax);
+    }
+  }
+  if (fp64) reinvert_block<TW>(S, Wk, w, spin, smem_c);
   if (threadIdx.x == 0) {
     Wk.refine_last[2 * w + spin] = rm;
     Wk.refine_max[2 * w + spin] = 0.f;
+    Wk.refine_fb[2 * w + spin] = fp64 ? 1 : 0;
   }
 }
 

@@ -93,8 +93,9 @@ cudaError_t refine(const SysParams& S, const WalkParams& W, int spin, int part, 
       return cudaGetLastError();
     }
     if (part == 2) {
-      // after the buffer swap: FP64 re-inversion of the walkers whose residual was too large
-      const size_t smem = reinvert_smem_bytes(W.ld_v);
+      // after the buffer swap: a second Newton step or the FP64 re-inversion of the walkers
+      // whose residual was too large for one step
+      const size_t smem = std::max(reinvert_smem_bytes(W.ld_v), sizeof(float) * (kTileElems + 32));
       cudaError_t e = cudaFuncSetAttribute(k_refine_fallback<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
       k_refine_fallback<TW><<<W.n_w, kThreads, smem, st>>>(S, W, spin);

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kLdThreads, 2) k_logdet_anchor(SysParams S, Wa
   extern __shared__ __align__(16) char smem_ld[];
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;                    // empty DMC slot
-  if (!(Wk.refine_last[2 * w + spin] <= kRefineMax)) return;  // re-inverted in FP64: exact
+  if (Wk.refine_fb[2 * w + spin]) return;                   // re-inverted in FP64: exact
   const int n = spin ? S.n_dn : S.n_up;
   if (n == 0 || n > kLdMaxN) return;
   const int first = spin ? S.n_up : 0;
