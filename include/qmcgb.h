@@ -95,10 +95,11 @@ typedef struct {
                               QMC_FP64 by FP64 Gauss-Jordan; the single-precision forms by one
                               Newton step X <- X + X R whose residual R = I - A X is computed
                               error-free on the tensor cores; a walker whose |R| is above 1e-2
-                              gets a second, compensated Newton step, and above 5e-2 (or when
-                              the second step's own residual is above 1e-2) FP64 Gauss-Jordan,
-                              as do spin blocks above 512 electrons (the in-sweep variant used
-                              with reinv_on_accepted sums R with compensated arithmetic) */
+                              gets up to two more, compensated Newton steps while its residual
+                              contracts, and above 0.2 (or without contraction) FP64
+                              Gauss-Jordan, as do spin blocks above 512 electrons (the in-sweep
+                              variant used with reinv_on_accepted sums R with compensated
+                              arithmetic) */
   int reinv_on_accepted;   /* 1: count accepted moves of the determinant; 0: proposed moves */
   uint64_t seed;           /* Philox4x32-10 key of every draw */
   int logdet_period;       /* single-precision forms with batched re-inversion (delay_k >= 4,
@@ -279,8 +280,8 @@ qmc_status qmc_get_logdet(qmc_walkers_t w, double* logdet, double* sign);
 /* Numerical health of the single-precision forms, per walker and spin block ([n_walkers][2]
  * doubles each, host or device, either may be NULL):
  *   residual      max |I - A X| measured by the block's last batched re-inversion before
- *                 its Newton step (X the inverse it corrected); above 1e-2 means a second
- *                 Newton step followed, above 5e-2 (or infinite) an FP64 Gauss-Jordan;
+ *                 its Newton step (X the inverse it corrected); above 1e-2 means further
+ *                 Newton steps followed, above 0.2 (or infinite) an FP64 Gauss-Jordan;
  *   logdet_shift  the change the last log-determinant anchor made to ln|det A| (anchored
  *                 value minus the accumulated one): the drift of the accumulated sum since
  *                 the previous FP64-class value.

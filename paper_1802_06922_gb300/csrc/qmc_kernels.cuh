@@ -521,11 +521,11 @@ __host__ __device__ inline size_t invert_batch_smem_bytes(int n) { return gj_sme
 // step; the caller then falls back to the FP64 Gauss-Jordan re-inversion.
 // =============================================================================
 constexpr float kRefineMax = 1e-2f;
-// The batched refinement takes the Newton step up to kRefineTwoStep; above kRefineMax the
-// re-inversion's FP64 stage adds a second, compensated step in the walker's block
-// (0.05 -> 2.5e-3 -> 6e-6), and only a residual beyond that (or not finite) takes the FP64
-// Gauss-Jordan re-inversion.
-constexpr float kRefineTwoStep = 5e-2f;
+// The batched refinement takes the Newton step up to kRefineSteps; above kRefineMax the
+// re-inversion's FP64 stage adds compensated steps in the walker's block until the residual
+// is within kRefineMax (0.2 -> 0.04 -> 1.6e-3 -> 2.6e-6), and only a residual beyond
+// kRefineSteps, or one that does not contract, takes the FP64 Gauss-Jordan re-inversion.
+constexpr float kRefineSteps = 0.2f;
 constexpr int kTileElems = 2 * 32 * 64;      // two 32 x 64 single-precision tiles
 
 __device__ __forceinline__ void dot2_step(float a, float b, float& P, float& E) {
@@ -539,8 +539,9 @@ __device__ __forceinline__ void dot2_step(float a, float b, float& P, float& E) 
 }
 
 // Returns max |R| over the matrix (identical in every thread).
+// One Newton step X <- X + X R when max |R| <= max_r; returns max |R| (before the step).
 static __device__ float refine_inverse(const SysParams& S, const WalkParams& Wk, int w, int spin,
-                                float* tile, float* redf) {
+                                float* tile, float* redf, float max_r = kRefineMax) {
   const int ns = spin ? S.n_dn : S.n_up;
   const int first = spin ? S.n_up : 0;
   const int ld5 = 5 * Wk.ld_v;
@@ -603,7 +604,7 @@ static __device__ float refine_inverse(const SysParams& S, const WalkParams& Wk,
   __syncthreads();
   rmax = 0.f;
   for (int q = 0; q < (int)(blockDim.x >> 5); ++q) rmax = fmaxf(rmax, redf[q]);
-  if (!(rmax <= kRefineMax)) return rmax;
+  if (!(rmax <= max_r)) return rmax;
   // Bn[e][j] = Binv[e][j] + sum_f R[f][e] Binv[f][j]
   for (int te = 0; te < ns; te += 64)
     for (int tj = 0; tj < ns; tj += 64) {
@@ -1574,13 +1575,20 @@ __global__ void __launch_bounds__(256) k_refine_fallback(SysParams S, WalkParams
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;          // empty DMC slot
   const float rm = Wk.refine_max[2 * w + spin];
-  bool fp64 = !(rm <= kRefineTwoStep);
+  bool fp64 = !(rm <= kRefineSteps);
   if constexpr (sizeof(TW) == 4) {
     if (!fp64 && rm > kRefineMax) {
-      // the batched step left about rm^2: a second step here; FP64 if even that is too far
+      // the batched step left about rm^2: up to two more steps here, each taken only if the
+      // residual contracted (to at most a quarter of the last one), each leaving about the
+      // square of the residual it started from; FP64 if that does not reach kRefineMax
       float* tile = reinterpret_cast<float*>(smem_c);
-      const float r2 = refine_inverse(S, Wk, w, spin, tile, tile + kTileElems);
-      fp64 = !(r2 <= kRefineMax);
+      float r = rm;
+      for (int it = 0; it < 2 && r > kRefineMax; ++it) {
+        const float rn = refine_inverse(S, Wk, w, spin, tile, tile + kTileElems, 0.25f * r);
+        if (!(rn <= 0.25f * r)) { r = INFINITY; break; }   // no contraction: no step taken
+        r = rn * rn;
+      }
+      fp64 = !(r <= kRefineMax);
     }
   }
   if (fp64) reinvert_block<TW>(S, Wk, w, spin, smem_c);

@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(256, 1) k_refine_update_tc(SysParams S, WalkPa
   __shared__ uint32_t tbase;
   const int w = blockIdx.x;
   if (Wk.n_live && w >= *Wk.n_live) return;
-  if (!(Wk.refine_max[2 * w + spin] <= kRefineTwoStep)) return;   // FP64 re-inversion instead
+  if (!(Wk.refine_max[2 * w + spin] <= kRefineSteps)) return;   // FP64 re-inversion instead
   const int ns = spin ? S.n_dn : S.n_up;
   const int nt = (ns + kTcRows - 1) / kTcRows;
   const int e0 = (blockIdx.y / nt) * kTcRows, j0 = (blockIdx.y % nt) * kTcRows;
