@@ -39,6 +39,9 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--preset", default="sj512")
+    p.add_argument("--no-graphs", action="store_true",
+                   help="launch every sweep's (and DMC step's) kernels directly instead of "
+                        "replaying them as one CUDA graph")
     p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     p.add_argument("--delay-k", default="auto",
                    help="delay rank k, or 'auto': the fastest of 8, 16, 32 on this workload "
@@ -376,6 +379,7 @@ def run_ours(args, spec, rank, world, local_rank):
         """ms of n_steps sweeps after n_warm. Without `profile`, every sweep is one CUDA-graph
         replay; with it, direct launches each bracketed by CUDA events (per-class times)."""
         w = q.Walkers(system, pos)
+        w.graphs(not args.no_graphs)
         for _ in range(n_warm):
             w.sweep(1, stream)
         barrier()
@@ -706,6 +710,7 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
         et.append(float(np.median(e)))
         specs.append(spec)
     d = q.DMC(systems, pos, et, capacity_factor=2)
+    d.graphs(not args.no_graphs)
     d.set_mode(effective_tau=True, reconfigure=False)
     d.step(args.warmup, stream)
     torch.cuda.synchronize()
@@ -749,8 +754,10 @@ def dmc_measure(args, rank, world, n_steps, dist=None):
             + f"; drift-diffusion tau={specs[0].step} with nodal drift rescaling (a = 1), "
               f"branching with the effective time step, E_T feedback, delayed rank-{dmc_k}, "
               f"re-inversion every {args.reinv_period} moves; walkers equilibrated by "
-              f"{args.dmc_vmc_sweeps} VMC sweeps, E_T from their median E_L; each step one "
-              f"CUDA graph over the three systems (captured on one stream per system)",
+              f"{args.dmc_vmc_sweeps} VMC sweeps, E_T from their median E_L; "
+            + ("each step's kernels launched directly, one stream per system" if args.no_graphs
+               else "each step one CUDA graph over the three systems (captured on one stream "
+                    "per system)"),
             "populations_first_last": [pops[0], pops[-1]],
             "kernels_ms_per_step": prof,
             "e_mean_last": [float(x["e_mean"]) for x in final],
