@@ -611,6 +611,8 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
   // keep the proposal buffer below 2 GiB by splitting spin blocks into chunks
   while (w->chunk > 32 && nw * w->chunk * 5 * W.ld_v * tw > (size_t(2) << 30)) w->chunk = (w->chunk + 1) / 2;
   const size_t np = proposals ? nw * (size_t)w->chunk : 1;
+  // Metropolis proposals of a chunk, or the draws of every move of a drift sweep
+  const size_t nprop = proposals ? np : s->d.move == QMC_MOVE_DRIFT ? nw * ne : 1;
   const size_t nb_up = (size_t)std::max(P.n_up, 1) * std::max(P.n_up, 1);
   const size_t nb_dn = (size_t)std::max(P.n_dn, 1) * std::max(P.n_dn, 1);
   // the second inverse buffers serve the batched single-precision re-inversion
@@ -633,7 +635,7 @@ qmc_status alloc_walkers(qmc_system_s* s, int cap, bool proposals, qmc_walkers_s
       {(void**)&W.scratch64, 2 * nw * (size_t)W.ld_v * W.ld_v * sizeof(double)},
       {(void**)&W.err, sizeof(int)},
       {(void**)&w->d_P, np * 5 * W.ld_v * tw},
-      {(void**)&w->d_prop, np * sizeof(Prop)},
+      {(void**)&w->d_prop, nprop * sizeof(Prop)},
       {(void**)&w->d_out, 8 * sizeof(double)},
       {(void**)&w->d_nacc, sizeof(long long)},
       {(void**)&W.win_phi, nw * (size_t)s->d.delay_k * W.ld_v * tw},
@@ -746,6 +748,10 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
   const bool ext = kc >= 4 && !(period > 0 && s->d.reinv_on_accepted) &&
                    !(period > 0 && s->d.prec == QMC_FP64);
   bool joined = true;             // the side stream's work has been joined back into st
+  if (drift) {
+    Bracket b(w, st, QMC_K_PROPOSE);
+    QMC_CUDA(launch_drift_draws(P, W, t, w->d_prop, st));
+  }
   for (int spin = 0; spin < 2; ++spin) {
     const int b0 = spin ? P.n_up : 0, b1 = spin ? P.n_e : P.n_up;
     const int pchunk = drift ? std::max(b1 - b0, 1) : w->chunk;
@@ -758,8 +764,8 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
       if (!ext) {
         Bracket b(w, st, QMC_K_SWEEP);
         if (drift)
-          QMC_CUDA(s->tt->sweep_drift(P, W, t, pc0, pc1, kc, period, s->d.reinv_on_accepted,
-                                      0, fixed_node, st));
+          QMC_CUDA(s->tt->sweep_drift(P, W, t, pc0, pc1, kc, w->d_prop, period,
+                                      s->d.reinv_on_accepted, 0, fixed_node, st));
         else
           QMC_CUDA(s->tw->sweep(P, W, t, pc0, pc1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
                                 period, s->d.reinv_on_accepted, 0, fixed_node, st));
@@ -771,7 +777,7 @@ qmc_status sweep_once(qmc_walkers_s* w, WalkParams& W, uint32_t t, bool fixed_no
         {
           Bracket b(w, st, QMC_K_SWEEP);
           if (drift)
-            QMC_CUDA(s->tt->sweep_drift(P, W, t, e0, e1, kc, 0, 0, 1, fixed_node, st));
+            QMC_CUDA(s->tt->sweep_drift(P, W, t, e0, e1, kc, w->d_prop, 0, 0, 1, fixed_node, st));
           else
             QMC_CUDA(s->tw->sweep(P, W, t, e0, e1, kc, w->d_P, w->d_prop, pc0, pc1 - pc0,
                                   0, 0, 1, fixed_node, st));

@@ -32,6 +32,12 @@ __device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
 // Word -> open interval (0, 1): (w + 0.5) 2^-32, exact in double.
 __device__ __forceinline__ double unit_open(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
 
+// Acceptance variate of the move of electron e of walker `wid` in sweep t (counter
+// (t, e, wid, 1), first word).
+__device__ __forceinline__ double move_u(const SysParams& S, uint32_t t, uint32_t e, uint32_t wid) {
+  return unit_open(philox4x32_10(t, e, wid, 1u, S.seed_lo, S.seed_hi).v[0]);
+}
+
 // Gaussian displacement (Box-Muller on word pairs (0,1) and (2,3)) and acceptance
 // variate of the move of electron e of walker `wid` in sweep t (trial move of
 // Sec. "Trial Moves"; counter layout (t, e, wid, 0|1)).
@@ -44,8 +50,7 @@ __device__ __forceinline__ void move_draws(const SysParams& S, uint32_t t, uint3
   xi[1] = r1 * sin(g1);
   const double r2 = sqrt(-2.0 * log(unit_open(a.v[2])));
   xi[2] = r2 * cos(2.0 * M_PI * unit_open(a.v[3]));
-  const U32x4 b = philox4x32_10(t, e, wid, 1u, S.seed_lo, S.seed_hi);
-  u = unit_open(b.v[0]);
+  u = move_u(S, t, e, wid);
 }
 
 // Drift part of a drift-diffusion step for drift velocity v = grad_e ln|Psi|: tau v, or with
@@ -393,6 +398,13 @@ template <> struct TabVec<__nv_bfloat16> {
     }
   }
 };
+
+// One table element (the V = 1 form of TabVec::load): into f, or into d for a double table.
+__device__ __forceinline__ void tab_load1(const double* p, float&, double& d) { d = __ldg(p); }
+__device__ __forceinline__ void tab_load1(const float* p, float& f, double&) { f = __ldg(p); }
+__device__ __forceinline__ void tab_load1(const __nv_bfloat16* p, float& f, double&) {
+  f = __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p)) << 16);
+}
 
 // Working-precision accumulator type of a table type.
 template <class TT> struct AccOf { using type = float; };

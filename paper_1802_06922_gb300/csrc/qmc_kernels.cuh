@@ -17,13 +17,14 @@ namespace qmcgb {
 // Orbital evaluation: value, gradient and Laplacian of orbitals [o_begin, o_begin+32V)
 // at point r, by one warp (Sec. "B-spline basis sets": 64 coefficient rows per point,
 // each a contiguous run of orbital coefficients). Lane l owns V consecutive orbitals and
-// reads them with one 16-byte load per row. r must be the same in every lane.
+// reads them with one 16-byte load per row (V = 1: one orbital per lane, which spreads a
+// small orbital set over more warps). r must be the same in every lane.
 // =============================================================================
-template <class TT, class TW>
+template <class TT, class TW, int V = TabVec<TT>::V>
 __device__ __forceinline__ void vgl_warp(const SysParams& S, const double r[3], int o_begin,
                                          int n_eval, TW* __restrict__ out, int ld_out) {
   using A = typename AccOf<TT>::type;
-  constexpr int V = TabVec<TT>::V;
+  static_assert(V == TabVec<TT>::V || V == 1, "vector width: the table's or 1");
   const int lane = threadIdx.x & 31;
   // grid cell and fractional offset per axis, computed in double by lanes 0..2
   A tl = A(0);
@@ -69,9 +70,12 @@ __device__ __forceinline__ void vgl_warp(const SysParams& S, const double r[3], 
       const size_t base = ((size_t)idx[0][a] * S.ny + idx[1][b]) * S.nz;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        float cf[V];
-        double cd[V];
-        TabVec<TT>::load(tab + (base + idx[2][c]) * S.ld + o0, cf, cd);
+        float cf[TabVec<TT>::V];
+        double cd[TabVec<TT>::V];
+        if constexpr (V == 1)
+          tab_load1(tab + (base + idx[2][c]) * S.ld + o0, cf[0], cd[0]);
+        else
+          TabVec<TT>::load(tab + (base + idx[2][c]) * S.ld + o0, cf, cd);
         const A wv = wxy * w[2][0][c], wgx = dxy * w[2][0][c], wgy = xdy * w[2][0][c];
         const A wgz = wxy * w[2][1][c], wl = lxy * w[2][0][c] + wxy * w[2][2][c];
 #pragma unroll
@@ -87,6 +91,12 @@ __device__ __forceinline__ void vgl_warp(const SysParams& S, const double r[3], 
       }
     }
   }
+  if constexpr (V == 1) {
+    if (o0 < n_eval)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) out[k * ld_out + o0] = (TW)acc[k][0];
+    return;
+  } else {
   if (o0 + V <= n_eval) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -106,6 +116,7 @@ __device__ __forceinline__ void vgl_warp(const SysParams& S, const double r[3], 
 #pragma unroll
       for (int v = 0; v < V; ++v)
         if (o0 + v < n_eval) out[k * ld_out + o0 + v] = (TW)acc[k][v];
+  }
   }
 }
 
@@ -146,6 +157,28 @@ static __global__ void k_proposals(SysParams S, WalkParams Wk, uint32_t t, int e
   o.z = wrap_box(P[2 * S.n_e + e] + S.step * xi[2], S.L);
   o.u = u;
   prop[i] = o;
+}
+
+// Draws of the drift-diffusion moves of every electron of every walker in sweep t:
+// draw[w][e] = (xi_x, xi_y, xi_z, ln u). They depend on the Philox counter alone, not on
+// the chain, so they are formed ahead of the sequential moves, one thread per move, and the
+// sweep reads them with its prefetch instead of evaluating Box-Muller in FP64 inside a move;
+// the acceptance u < A is taken as ln u < ln A.
+static __global__ void k_drift_draws(SysParams S, WalkParams Wk, uint32_t t,
+                                     Prop* __restrict__ draw) {
+  const int ne = S.n_e;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)Wk.n_w * ne) return;
+  const int w = (int)(i / ne), e = (int)(i % ne);
+  if (Wk.n_live && w >= *Wk.n_live) return;
+  double xi[3], u;
+  move_draws(S, sweep_index(Wk, t), (uint32_t)e, Wk.wid[w], xi, u);
+  Prop o;
+  o.x = xi[0];
+  o.y = xi[1];
+  o.z = xi[2];
+  o.u = log(u);
+  draw[i] = o;
 }
 
 // VGL at every proposed position of a chunk: out[w][e-e0][5][ld_v].
@@ -913,6 +946,10 @@ __device__ __forceinline__ TW jastrow_delta_grad(const SysParams& S, const Jastr
   return dj;
 }
 
+// ln|x| in the working precision, widened to FP64
+__device__ __forceinline__ double log_abs_w(double x) { return log(fabs(x)); }
+__device__ __forceinline__ double log_abs_w(float x) { return (double)logf(fabsf(x)); }
+
 template <class TW>
 __device__ __forceinline__ TW texp(TW x);
 template <> __device__ __forceinline__ double texp<double>(double x) { return exp(x); }
@@ -946,10 +983,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   TW* B = binv_block<TW>(S, Wk, w, spin);
   TW* VG = static_cast<TW*>(Wk.vgl) + (size_t)w * n_e * 5 * ld_v;
   double* gpos = Wk.pos + (size_t)w * 3 * n_e;
-  // Prefetch of move index e (orbital rows, proposal, inverse row) into buffer b: one
-  // thread hands the contiguous pieces to the bulk-copy unit, which completes them on the
-  // buffer's mbarrier. An inverse row that is not 16-byte aligned (N_s * sizeof(TW) not a
-  // multiple of 16) is fetched element-wise by every thread instead.
+  // Prefetch of move index e (orbital rows, proposal or drift draws, inverse row) into
+  // buffer b: one thread hands the contiguous pieces to the bulk-copy unit, which completes
+  // them on the buffer's mbarrier. An inverse row that is not 16-byte aligned (N_s *
+  // sizeof(TW) not a multiple of 16) is fetched element-wise by every thread instead.
   __shared__ __align__(8) uint64_t pf_bar[2];
   const bool row_bulk = (ns * sizeof(TW)) % 16 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
   auto prefetch = [&](int e, int b) {
@@ -960,10 +997,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       // the block's reads of this buffer (ordered by the barrier before) precede the copies
       tc::fence_async_smem();
       const uint32_t nphi = 5u * ld_v * sizeof(TW), nrow = row_bulk ? ns * sizeof(TW) : 0u;
-      tc::mbar_arrive_expect_tx(&pf_bar[b], nphi + (kDrift ? 0u : (uint32_t)sizeof(Prop)) + nrow);
+      tc::mbar_arrive_expect_tx(&pf_bar[b], nphi + (uint32_t)sizeof(Prop) + nrow);
       tc::bulk_g2s(sm.phib + (size_t)b * 5 * ld_v, kDrift ? VG + (size_t)e * 5 * ld_v : Pv + mvi * 5 * ld_v,
                    nphi, &pf_bar[b]);
-      if (!kDrift) tc::bulk_g2s(sm.propb + 4 * b, prop + mvi, sizeof(Prop), &pf_bar[b]);
+      tc::bulk_g2s(sm.propb + 4 * b, prop + mvi, sizeof(Prop), &pf_bar[b]);
       if (row_bulk && nrow) tc::bulk_g2s(rd, rs, nrow, &pf_bar[b]);
     }
     if (!row_bulk) {
@@ -988,7 +1025,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
     sm.posd[i] = p;
     sm.posw[i] = (TW)p;
   }
-  double logdet = 0.0, sgn = 1.0;        // thread 0
+  // thread 0: ln|det| = logdet + ln lprod + lexp ln 2, the accepted ratios multiplied in FP64
+  // with their binary exponents split off (no logarithm inside a move)
+  double logdet = 0.0, sgn = 1.0, lprod = 1.0;
+  int lexp = 0;
   long long nacc = 0;
   double r2p = 0.0, r2a = 0.0;           // thread 0: squared proposed / accepted displacements
   if (tid == 0) {
@@ -997,6 +1037,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   }
   int since = Wk.acc_since[2 * w + spin];
   int m = 0;
+  const double sq_tau = kDrift ? sqrt(S.step) : 0.0, inv_2tau = kDrift ? 0.5 / S.step : 0.0;
   if (e0 < e1) prefetch(e0, 0);      // every prefetch issued is waited for inside the loop
   for (int e = e0; e < e1; ++e) {
     const int row = e - first;
@@ -1157,25 +1198,30 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
           for (int q = 0; q < nw; ++q) v += sm.red[q * 6 + c] + sm.red[q * 6 + 3 + c];
           go[c] = (double)v;
         }
-        double xi[3], u, dd[3];
-        move_draws(S, sweep_index(Wk, t), (uint32_t)e, Wk.wid[w], xi, u);
-        const double tau = S.step, sq = sqrt(tau);
-        drift_disp(go, tau, S.drift_a, dd);
+        // the move's draws, formed ahead of the sweep (k_drift_draws) and prefetched
+        // (u stays in its slot for the decision)
+        const double xi[3] = {sm.propb[4 * cur], sm.propb[4 * cur + 1], sm.propb[4 * cur + 2]};
+        double dd[3];
+        drift_disp(go, S.step, S.drift_a, dd);
         for (int c = 0; c < 3; ++c) {
-          const double rn = wrap_box(sm.posd[c * n_e + e] + dd[c] + sq * xi[c], S.L);
+          const double rn = wrap_box(sm.posd[c * n_e + e] + dd[c] + sq_tau * xi[c], S.L);
           sm.propb[4 * cur + c] = rn;
           sm.outd[10 + c] = dd[c];               // drift displacement of the forward move
           sm.sc[c] = (TW)rn;
         }
-        sm.propb[4 * cur + 3] = u;
       }
       __syncthreads();
-      // orbital values, gradients and Laplacians at r' (one warp per 32V-orbital chunk)
+      // orbital values, gradients and Laplacians at r' (one warp per 32V-orbital chunk; one
+      // orbital per lane while the block's warps cover the spin block that way)
       {
         constexpr int V = TabVec<TT>::V;
         const double rr[3] = {sm.propb[4 * cur], sm.propb[4 * cur + 1], sm.propb[4 * cur + 2]};
-        const int chunks = (ns + 32 * V - 1) / (32 * V);
-        for (int ch = warp; ch < chunks; ch += nw) vgl_warp<TT, TW>(S, rr, ch * 32 * V, ns, phi, ld_v);
+        if (ns <= 32 * nw) {
+          if (warp < (ns + 31) / 32) vgl_warp<TT, TW, 1>(S, rr, warp * 32, ns, phi, ld_v);
+        } else {
+          const int chunks = (ns + 32 * V - 1) / (32 * V);
+          for (int ch = warp; ch < chunks; ch += nw) vgl_warp<TT, TW>(S, rr, ch * 32 * V, ns, phi, ld_v);
+        }
       }
       __syncthreads();
     }
@@ -1263,9 +1309,10 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
       for (int k = 0; k < 9; ++k) tot[k] = __shfl_sync(0xffffffffu, v, k);
       if (lane == 0) {
       const TW R = kSplit ? sm.sc[6] + sm.sc[7] : tot[0], dJ = tot[5];
-      const double u = sm.propb[4 * cur + 3];
+      const double u = sm.propb[4 * cur + 3];   // ln u for a drift move
       const bool ok = (R != TW(0)) && isfinite(R);
-      TW A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
+      TW A = TW(0);
+      bool accept = false;
       double dr2 = 0.0;                          // |r' - r|^2 of a drift move
       if constexpr (kDrift) {
         // T(R'->R) / T(R->R') with displacement d = r' - r (minimum image) and the drift
@@ -1286,11 +1333,16 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
             f2 += fw * fw;
             b2 += bw * bw;
           }
-          const double lr = 2.0 * log(fabs((double)R)) + 2.0 * (double)dJ + (f2 - b2) / (2.0 * tau);
-          A = (TW)fmin(1.0, exp(lr));
+          // u < min(1, e^lr) decided as ln u < lr: the draws carry ln u, so a move takes no
+          // exponential (A itself is formed for a trace only); ln|R| in working precision
+          const double lr = 2.0 * log_abs_w(R) + 2.0 * (double)dJ + (f2 - b2) * inv_2tau;
+          accept = u < lr;
+          if (Wk.trace) A = (TW)fmin(1.0, exp(lr));
         }
+      } else {
+        A = ok ? fmin(TW(1), R * R * texp<TW>(TW(2) * dJ)) : TW(0);
+        accept = u < (double)A;
       }
-      bool accept = u < (double)A;
       if (kFixedNode && R < TW(0)) accept = false;
       if (Wk.forced) accept = Wk.forced[(size_t)w * n_e + e] != 0;
       if (kDrift) {
@@ -1304,14 +1356,16 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
         tr[2] = (ok ? (double)(tot[1] / R) : 0.0) + (double)tot[6];
         tr[3] = (ok ? (double)(tot[2] / R) : 0.0) + (double)tot[7];
         tr[4] = (ok ? (double)(tot[3] / R) : 0.0) + (double)tot[8];
-        tr[5] = u;
+        tr[5] = kDrift ? move_u(S, sweep_index(Wk, t), (uint32_t)e, Wk.wid[w]) : u;
         tr[6] = (double)A;
         tr[7] = accept ? 1.0 : 0.0;
       }
       sm.flag[0] = accept;
       if (accept) {
         ++nacc;
-        logdet += (double)log(fabs(R));
+        int ex;
+        lprod = frexp(lprod * fabs((double)R), &ex);
+        lexp += ex;
         if (R < TW(0)) sgn = -sgn;
         sm.posd[e] = sm.propb[4 * cur];
         sm.posd[n_e + e] = sm.propb[4 * cur + 1];
@@ -1411,6 +1465,8 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
           if (tid == 0) {
             logdet = Wk.logdet[2 * w + spin];
             sgn = Wk.sgn[2 * w + spin];
+            lprod = 1.0;
+            lexp = 0;
           }
         }
         since = 0;
@@ -1447,7 +1503,7 @@ __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, ui
   __syncthreads();
   for (int i = tid; i < 3 * n_e; i += nt) gpos[i] = sm.posd[i];
   if (tid == 0) {
-    Wk.logdet[2 * w + spin] = logdet;
+    Wk.logdet[2 * w + spin] = logdet + log(lprod) + (double)lexp * 0.69314718055994530942;
     Wk.sgn[2 * w + spin] = sgn;
     Wk.n_acc[w] += nacc;
     Wk.acc_since[2 * w + spin] = since;

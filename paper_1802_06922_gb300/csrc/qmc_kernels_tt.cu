@@ -31,14 +31,14 @@ cudaError_t vgl_proposals(const SysParams& S, const WalkParams& W, int e0, int e
 
 template <class TT, class TW>
 cudaError_t sweep_drift(const SysParams& S, const WalkParams& W, uint32_t t, int e0, int e1,
-                        int k, int reinv_period, int reinv_on_acc, int ext_flush, bool fixed_node,
-                        cudaStream_t st) {
+                        int k, const void* draw, int reinv_period, int reinv_on_acc,
+                        int ext_flush, bool fixed_node, cudaStream_t st) {
   const size_t smem = sweep_smem_bytes<TW>(S.n_e, W.ld_v, k, kThreads / 32, !ext_flush);
   auto kern = fixed_node ? k_sweep<TW, TT, true, true> : k_sweep<TW, TT, false, true>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<W.n_w, kThreads, smem, st>>>(S, W, t, e0, e1, k, nullptr, nullptr, e0, e1 - e0,
-                                      reinv_period, reinv_on_acc, ext_flush);
+  kern<<<W.n_w, kThreads, smem, st>>>(S, W, t, e0, e1, k, nullptr, static_cast<const Prop*>(draw),
+                                      0, S.n_e, reinv_period, reinv_on_acc, ext_flush);
   return cudaGetLastError();
 }
 

@@ -219,6 +219,14 @@ cudaError_t launch_proposals(const SysParams& S, const WalkParams& W, uint32_t t
   return cudaGetLastError();
 }
 
+cudaError_t launch_drift_draws(const SysParams& S, const WalkParams& W, uint32_t t, void* draw,
+                               cudaStream_t st) {
+  const long long n = (long long)W.n_w * S.n_e;
+  if (n == 0) return cudaSuccess;
+  k_drift_draws<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, W, t, static_cast<Prop*>(draw));
+  return cudaGetLastError();
+}
+
 static __global__ void k_set_word(uint32_t* p, uint32_t v) { *p = v; }
 
 cudaError_t launch_set_word(uint32_t* p, uint32_t v, cudaStream_t st) {

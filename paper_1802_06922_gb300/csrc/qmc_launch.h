@@ -42,10 +42,11 @@ struct TtLaunch {
   cudaError_t (*vgl_current)(const SysParams&, const WalkParams&, cudaStream_t);
   cudaError_t (*vgl_proposals)(const SysParams&, const WalkParams&, int e0, int e1,
                                const void* prop, void* out, cudaStream_t);
-  // drift-diffusion sweep of electrons [e0, e1) with in-kernel orbital evaluation
+  // drift-diffusion sweep of electrons [e0, e1) with in-kernel orbital evaluation; draw: the
+  // sweep's draws from launch_drift_draws
   cudaError_t (*sweep_drift)(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
-                             int k, int reinv_period, int reinv_on_acc, int ext_flush,
-                             bool fixed_node, cudaStream_t);
+                             int k, const void* draw, int reinv_period, int reinv_on_acc,
+                             int ext_flush, bool fixed_node, cudaStream_t);
   // non-local pseudopotential energy of every walker (added to E_L), quadrature rotation t
   cudaError_t (*nlpp)(const SysParams&, const WalkParams&, uint32_t t, cudaStream_t);
 };
@@ -56,6 +57,9 @@ const TtLaunch& tt_launch_bf16();
 // Precision-independent kernels.
 cudaError_t launch_proposals(const SysParams&, const WalkParams&, uint32_t t, int e0, int e1,
                              void* prop, cudaStream_t);
+// Draws (xi, u) of every drift-diffusion move of sweep t: draw[w][e], W.n_w x S.n_e entries.
+cudaError_t launch_drift_draws(const SysParams&, const WalkParams&, uint32_t t, void* draw,
+                               cudaStream_t);
 cudaError_t launch_accumulate(const WalkParams&, double* out, long long* nacc, cudaStream_t);
 // *p = v on the stream (the sweep index of a replayed graph).
 cudaError_t launch_set_word(uint32_t* p, uint32_t v, cudaStream_t);
