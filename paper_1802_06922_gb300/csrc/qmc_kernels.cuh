@@ -958,7 +958,8 @@ template <> __device__ __forceinline__ float texp<float>(float x) { return expf(
 // kDrift: drift-diffusion proposals r' = r + tau grad ln|Psi| + sqrt(tau) xi (Eq.
 // pmc:driftdiffusion_step with the adopted lambda = 1/2), whose orbital values are gathered
 // in the kernel (table type TT) because the proposal depends on the current inverse; the
-// acceptance includes the Green's-function ratio of Eq. pmc:g_driftdiffusion.
+// acceptance includes the Green's-function ratio of Eq. pmc:g_driftdiffusion. The draws
+// (xi, ln u) come from k_drift_draws through `prop` ([W][N_e], p_e0 = 0, p_n = N_e).
 template <class TW, class TT, bool kFixedNode, bool kDrift>
 __global__ void __launch_bounds__(256, 2) k_sweep(SysParams S, WalkParams Wk, uint32_t t, int e0,
                                               int e1, int kc, const TW* __restrict__ Pv,
